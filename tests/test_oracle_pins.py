@@ -1,0 +1,334 @@
+"""Pins of the CPU FP64 oracle against what the paper and the mathematics fix.
+
+None of these compares the oracle with itself: each check uses printed values
+(Table 4), closed forms, independent library routines (scipy special
+functions, sympy differentiation), an independent definition of the truncated
+expansion (the total-degree Taylor polynomial, computed by a Cauchy integral),
+or brute force on small inputs.
+"""
+import math
+import os
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+from oracle import tables
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+
+# Table 4 kernels in the oracle's parameterisation (reading R15):
+#   e^{-r}: exponential, l = 1;  (1+r^2)^{-1}: cauchy, l = 1;  e^{-r^2}: gaussian, l = 1/sqrt(2)
+TABLE4_KERNELS = {"exp": ("exponential", 1.0), "cauchy": ("cauchy", 1.0), "gauss": ("gaussian", 1.0 / math.sqrt(2.0))}
+
+
+def _golden_table4():
+    rows = []
+    with open(os.path.join(HERE, "golden", "table4.txt")) as fh:
+        for line in fh:
+            line = line.split("#")[0].strip()
+            if line:
+                k, d, p, e = line.split()
+                rows.append((k, int(d), int(p), float(e)))
+    return rows
+
+
+def _pairs(d, n=1000, seed=0, rr=2.0, rp=1.0):
+    rng = np.random.default_rng(seed)
+    u = rng.standard_normal((n, d))
+    u /= np.linalg.norm(u, axis=1, keepdims=True)
+    v = rng.standard_normal((n, d))
+    v /= np.linalg.norm(v, axis=1, keepdims=True)
+    return rr * u, rp * v
+
+
+# ----------------------------------------------------------------- Table 4
+@pytest.mark.parametrize("row", _golden_table4(), ids=lambda r: f"{r[0]}-d{r[1]}-p{r[2]}")
+def test_table4_max_abs_error(orc, row):
+    """Max |K - K_p| over 1000 random pairs, |r'|=1, |r|=2 (Table 4).
+
+    The paper's value is a maximum over its own random sample, so we accept a
+    factor 1.5 either way (reading R16); dropping the binomial of eq. prelemma
+    (reading R1) makes the error grow with p and fails this by orders of magnitude.
+    """
+    name, d, p, ref = row
+    kname, ell = TABLE4_KERNELS[name]
+    kp = orc.kparams(kname, ell)
+    X, XP = _pairs(d)
+    exact = np.array([orc.kernel_value(kp, np.linalg.norm(a - b)) for a, b in zip(X, XP)])
+    if d <= 4:
+        approx = orc.Basis(d, p).expansion(kp, X, XP)          # factorised s2m/m2t form
+    else:
+        approx = orc.expansion_gegenbauer(d, p, kp, X, XP)     # addition theorem applied
+    err = np.abs(approx - exact).max()
+    assert ref / 1.5 < err < ref * 1.5, (err, ref)
+
+
+# -------------------------------------------------------------- the tables
+def test_num_terms_is_binomial():
+    """P = binom(p+d, d) (Sec. 4.2 and Sec. A.3)."""
+    for d in (3, 4, 5, 6):
+        for p in range(0, 11):
+            assert tables.num_terms(p, d) == math.comb(p + d, d)
+
+
+def test_harmonic_dim_formula():
+    """|H_k| = dimension of degree-k harmonic polynomials = dim P_k - dim P_{k-2} (Sec. A.3)."""
+    for d in (3, 4, 5):
+        for k in range(10):
+            dimP = lambda kk: math.comb(kk + d - 1, d - 1) if kk >= 0 else 0
+            assert tables.harmonic_dim(k, d) == dimP(k) - dimP(k - 2)
+    assert [tables.harmonic_dim(k, 3) for k in range(6)] == [1, 3, 5, 7, 9, 11]
+    assert [tables.harmonic_dim(k, 4) for k in range(6)] == [1, 4, 9, 16, 25, 36]
+
+
+def test_cos_power_identity_against_scipy():
+    """cos^i = sum_k A_{k,i} C_k^alpha(cos) (eq. coschange), C from scipy."""
+    from scipy.special import eval_gegenbauer
+
+    x = np.linspace(-0.97, 0.95, 17)
+    for d in (3, 4, 5, 7):
+        a = d / 2 - 1
+        for i in range(0, 12):
+            rhs = sum(float(tables.A(k, i, d)) * eval_gegenbauer(k, a, x) for k in range(i + 1))
+            np.testing.assert_allclose(rhs, x ** i, rtol=1e-12, atol=1e-13)
+
+
+def test_faa_di_bruno_coefficients_against_sympy():
+    """d^n/de^n K(r sqrt(1+e)) at e=0 = sum_m B_{n,m} K^(m)(r) r^m (Lemma A.2), by symbolic differentiation."""
+    import sympy as sp
+
+    r, e = sp.symbols("r e", positive=True)
+    Kf = sp.Function("K")
+    for n in range(0, 7):
+        lhs = sp.diff(Kf(r * sp.sqrt(1 + e)), e, n).subs(e, 0).doit()
+        rhs = sum(sp.Rational(tables.B(n, m).numerator, tables.B(n, m).denominator) * sp.diff(Kf(r), r, m) * r ** m
+                  for m in range(0, n + 1))
+        assert sp.simplify(lhs - rhs) == 0, n
+
+
+def test_inverse_distance_collapses_to_legendre_multipole():
+    """K = 1/r in d=3: only j = k survives with coefficient 1 (eq. electro, Sec. 3.3).
+
+    K^(m)(r) r^m = (-1)^m m! / r, so sum_m (-1)^m m! Tbar_{k,j,m} must equal delta_{jk} exactly.
+    """
+    for k, j in tables.expansion_terms(10, 3):
+        s = sum(Fraction((-1) ** m * math.factorial(m)) * tables.Tbar(k, j, m, 3) for m in range(j + 1))
+        assert s == (1 if j == k else 0), (k, j, s)
+
+
+def test_tbar_zero_order_and_parity():
+    """Tbar_{0,0,0} = 1 (the n = 0 term of eq. taylor, reading R2); Tbar vanishes unless j = k mod 2."""
+    for d in (3, 4):
+        assert tables.Tbar(0, 0, 0, d) == 1
+        for k in range(6):
+            for j in range(6):
+                for m in range(j + 1):
+                    if (j - k) % 2 or j < k:
+                        assert tables.Tbar(k, j, m, d) == 0
+
+
+# ------------------------------------------------------- special functions
+def test_gegenbauer_against_scipy(orc):
+    from scipy.special import eval_gegenbauer
+
+    for d in (3, 4, 6):
+        a = d / 2 - 1
+        for x in np.linspace(-1, 1, 13):
+            got = orc.gegenbauer(a, 12, x)
+            want = np.array([eval_gegenbauer(n, a, x) for n in range(13)])
+            np.testing.assert_allclose(got, want, rtol=1e-12, atol=1e-12)
+
+
+def test_kernel_values_closed_forms(orc):
+    r = 0.37
+    cases = {
+        ("gaussian", 0.1): math.exp(-r * r / (2 * 0.01)),
+        ("exponential", 0.5): math.exp(-r / 0.5),
+        ("matern32", 0.2): (1 + math.sqrt(3) * r / 0.2) * math.exp(-math.sqrt(3) * r / 0.2),
+        ("matern52", 0.3): (1 + math.sqrt(5) * r / 0.3 + 5 * r * r / (3 * 0.09)) * math.exp(-math.sqrt(5) * r / 0.3),
+        ("cauchy", 0.05): 1 / (1 + r * r / 0.0025),
+        ("laplace", 1.0): 1 / r,
+    }
+    for (k, l), want in cases.items():
+        assert orc.kernel_value(orc.kparams(k, l), r) == pytest.approx(want, rel=1e-14)
+    assert orc.kernel_value(orc.kparams("ratquad", 0.2, alpha=1.0), r) == pytest.approx(1 / (1 + r * r / (2 * 0.04)), rel=1e-14)
+    assert orc.kernel_value(orc.kparams("laplace", 1.0, scale=1 / (4 * math.pi)), r) == pytest.approx(1 / (4 * math.pi * r))
+
+
+def test_jets_closed_forms(orc):
+    """Taylor-mode derivatives K^(m)(r) against closed forms (Sec. B.1 uses AD for these)."""
+    from scipy.special import eval_hermite
+
+    r, p = 0.83, 10
+    # Matern-3/2: K^(m) = (-a)^m e^{-ar} (1 - m + a r), a = sqrt(3)/l
+    l = 0.2
+    a = math.sqrt(3) / l
+    want = [(-a) ** m * math.exp(-a * r) * (1 - m + a * r) for m in range(p + 1)]
+    np.testing.assert_allclose(orc.kernel_derivs(orc.kparams("matern32", l), r, p), want, rtol=1e-11)
+    # 1/r: (-1)^m m! / r^(m+1)
+    want = [(-1) ** m * math.factorial(m) / r ** (m + 1) for m in range(p + 1)]
+    np.testing.assert_allclose(orc.kernel_derivs(orc.kparams("laplace", 1.0), r, p), want, rtol=1e-12)
+    # Gaussian e^{-r^2/(2 l^2)}: (-1/(sqrt2 l))^m H_m(r/(sqrt2 l)) e^{-r^2/(2l^2)}
+    l = 0.5
+    s = math.sqrt(2) * l
+    want = [(-1 / s) ** m * eval_hermite(m, r / s) * math.exp(-r * r / (2 * l * l)) for m in range(p + 1)]
+    np.testing.assert_allclose(orc.kernel_derivs(orc.kparams("gaussian", l), r, p), want, rtol=1e-10)
+
+
+def test_jets_against_sympy(orc):
+    import sympy as sp
+
+    x = sp.symbols("x", positive=True)
+    r, p = 0.61, 8
+    exprs = {
+        ("cauchy", 0.3, 1.0): 1 / (1 + x ** 2 / sp.Rational(9, 100)),
+        ("ratquad", 0.2, 1.0): (1 + x ** 2 / (2 * sp.Rational(4, 100))) ** -1,
+        ("ratquad", 0.4, 0.5): (1 + x ** 2 / (2 * sp.Rational(1, 2) * sp.Rational(16, 100))) ** sp.Rational(-1, 2),
+        ("matern52", 0.3, 1.0): (1 + sp.sqrt(5) * x / sp.Rational(3, 10) + 5 * x ** 2 / (3 * sp.Rational(9, 100)))
+        * sp.exp(-sp.sqrt(5) * x / sp.Rational(3, 10)),
+        ("exponential", 0.7, 1.0): sp.exp(-x / sp.Rational(7, 10)),
+    }
+    for (k, l, al), e in exprs.items():
+        want = [float(sp.diff(e, x, m).subs(x, r)) for m in range(p + 1)]
+        got = orc.kernel_derivs(orc.kparams(k, l, alpha=al), r, p)
+        np.testing.assert_allclose(got, want, rtol=1e-10, err_msg=k)
+
+
+# ---------------------------------------------------------------- harmonics
+@pytest.mark.parametrize("d,p", [(3, 8), (4, 6)])
+def test_addition_theorem(orc, d, p):
+    """sum_h Y_kh(u) Y_kh(v) = C_k^alpha(u.v) for random unit vectors (Sec. A.1, eq. additiontheorem)."""
+    from scipy.special import eval_gegenbauer
+
+    B = orc.Basis(d, p)
+    rng = np.random.default_rng(7)
+    off = np.concatenate([[0], np.cumsum(B.Dk)])
+    for _ in range(20):
+        u, v = rng.standard_normal((2, d))
+        u /= np.linalg.norm(u)
+        v /= np.linalg.norm(v)
+        Yu, Yv = B.harmonics(u), B.harmonics(v)
+        for k in range(p + 1):
+            s = Yu[off[k]:off[k + 1]] @ Yv[off[k]:off[k + 1]]
+            assert s == pytest.approx(eval_gegenbauer(k, d / 2 - 1, u @ v), abs=1e-10)
+
+
+def test_harmonics_d3_are_legendre(orc):
+    """In d=3 the addition theorem reduces to Legendre polynomials (eq. spheradditiontheorem)."""
+    from scipy.special import eval_legendre
+
+    B = orc.Basis(3, 6)
+    rng = np.random.default_rng(3)
+    off = np.concatenate([[0], np.cumsum(B.Dk)])
+    u, v = rng.standard_normal((2, 3))
+    u /= np.linalg.norm(u)
+    v /= np.linalg.norm(v)
+    Yu, Yv = B.harmonics(u), B.harmonics(v)
+    for k in range(7):
+        assert Yu[off[k]:off[k + 1]] @ Yv[off[k]:off[k + 1]] == pytest.approx(eval_legendre(k, u @ v), abs=1e-11)
+
+
+# ---------------------------------------- the truncated expansion, independently
+def _complex_kernel(name, q, ell=1.0, alpha=1.0):
+    """K as a function of q = r^2, continued to complex q near the positive axis."""
+    s = np.sqrt(q)
+    if name == "gaussian":
+        return np.exp(-q / (2 * ell * ell))
+    if name == "exponential":
+        return np.exp(-s / ell)
+    if name == "matern32":
+        t = math.sqrt(3) * s / ell
+        return (1 + t) * np.exp(-t)
+    if name == "matern52":
+        t = math.sqrt(5) * s / ell
+        return (1 + t + t * t / 3) * np.exp(-t)
+    if name == "cauchy":
+        return 1 / (1 + q / (ell * ell))
+    if name == "ratquad":
+        return (1 + q / (2 * alpha * ell * ell)) ** (-alpha)
+    if name == "laplace":
+        return 1 / s
+    raise KeyError(name)
+
+
+def _taylor_poly_in_source(name, x, xp, p, ell, alpha, rad=0.5, nodes=256):
+    """sum_{n<=p} [tau^n] K(|x - tau x'|): the total-degree-p Taylor polynomial of
+    x' -> K(|x - x'|) at 0, evaluated at x'.  Coefficients by the Cauchy integral (FFT)."""
+    tau = rad * np.exp(2j * np.pi * np.arange(nodes) / nodes)
+    q = x @ x - 2 * tau * (x @ xp) + tau * tau * (xp @ xp)
+    f = _complex_kernel(name, q, ell, alpha)
+    c = np.fft.fft(f) / nodes / rad ** np.arange(nodes)
+    return float(np.real(c[: p + 1].sum()))
+
+
+@pytest.mark.parametrize("d", [3, 4])
+@pytest.mark.parametrize("name,ell,alpha", [("gaussian", 0.9, 1.0), ("exponential", 1.3, 1.0), ("matern32", 1.0, 1.0),
+                                            ("matern52", 1.5, 1.0), ("cauchy", 1.2, 1.0), ("ratquad", 1.1, 0.5),
+                                            ("laplace", 1.0, 1.0)])
+def test_truncation_is_total_degree_taylor_polynomial(orc, d, name, ell, alpha):
+    """The order-p truncation (eq. finaltrunc, j <= p) equals the Taylor polynomial of total
+    degree p in the source offset (reading R8), computed here without any of the paper's
+    tables, harmonics or jets.  Catches a dropped term, a wrong sign or index in Tbar,
+    in the jets or in the harmonic basis."""
+    p = 6
+    B = orc.Basis(d, p)
+    kp = orc.kparams(name, ell, alpha=alpha)
+    rng = np.random.default_rng(11)
+    X = rng.standard_normal((8, d))
+    X *= (1.5 + rng.random((8, 1))) / np.linalg.norm(X, axis=1, keepdims=True)
+    XP = rng.standard_normal((8, d))
+    XP *= (0.2 + 0.6 * rng.random((8, 1))) / np.linalg.norm(XP, axis=1, keepdims=True)
+    got = B.expansion(kp, X, XP)
+    want = np.array([_taylor_poly_in_source(name, X[i], XP[i], p, ell, alpha) for i in range(8)])
+    np.testing.assert_allclose(got, want, rtol=1e-9, atol=1e-12)
+
+
+def test_factorised_equals_gegenbauer_form(orc):
+    """s2m/m2t through the harmonic basis equals the addition-theorem form (Theorem 3.1)."""
+    for d, p in ((3, 7), (4, 5)):
+        B = orc.Basis(d, p)
+        kp = orc.kparams("matern32", 0.7)
+        X, XP = _pairs(d, n=50, seed=5, rr=1.7, rp=0.6)
+        np.testing.assert_allclose(B.expansion(kp, X, XP), orc.expansion_gegenbauer(d, p, kp, X, XP), rtol=1e-11,
+                                   atol=1e-13)
+
+
+def test_error_decays_with_p(orc):
+    """Truncation error falls exponentially with p at fixed geometry (Sec. 4.1)."""
+    kp = orc.kparams("cauchy", 1.0)
+    X, XP = _pairs(3, n=200, seed=9)
+    exact = np.array([orc.kernel_value(kp, np.linalg.norm(a - b)) for a, b in zip(X, XP)])
+    errs = [np.abs(orc.Basis(3, p).expansion(kp, X, XP) - exact).max() for p in (2, 4, 6, 8, 10)]
+    assert all(b < a for a, b in zip(errs, errs[1:])), errs
+    assert errs[-1] < errs[0] / 50
+
+
+# --------------------------------------------------------- planted mistakes
+def test_pins_catch_planted_table_mistakes(orc, monkeypatch):
+    """A plausible mistake in the oracle's tables must fail a pin: drop the binomial
+    of eq. prelemma (the printed formula), or flip the sign of (-2)^(2n-j)."""
+    from oracle import oracle as O
+
+    d, p = 3, 6
+    kp = orc.kparams("exponential", 1.0)
+    X, XP = _pairs(d, n=200, seed=0)
+    exact = np.array([orc.kernel_value(kp, np.linalg.norm(a - b)) for a, b in zip(X, XP)])
+
+    def no_binomial(k, j, m, dd):
+        if j < k or (j - k) % 2 or m > j:
+            return Fraction(0)
+        return sum((tables.A(k, 2 * n - j, dd) * Fraction(-2) ** (2 * n - j) * tables.B(n, m) / math.factorial(n)
+                    for n in range(max((j + k) // 2, m), j + 1)), Fraction(0))
+
+    def wrong_sign(k, j, m, dd):
+        if j < k or (j - k) % 2 or m > j:
+            return Fraction(0)
+        return sum((tables.A(k, 2 * n - j, dd) * Fraction(2) ** (2 * n - j) * math.comb(n, 2 * n - j) * tables.B(n, m)
+                    / math.factorial(n) for n in range(max((j + k) // 2, m), j + 1)), Fraction(0))
+
+    for bad in (no_binomial, wrong_sign):
+        monkeypatch.setattr(tables, "Tbar", bad)
+        err = np.abs(O.expansion_gegenbauer(d, p, kp, X, XP) - exact).max()
+        assert err > 1.5 * 7.32e-4, bad.__name__
+    monkeypatch.undo()
