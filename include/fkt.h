@@ -1,0 +1,170 @@
+/*
+ * fkt.h -- C ABI of the GB300-native Fast Kernel Transform (arXiv 2106.04487).
+ *
+ * The library computes the approximate kernel matrix-vector product
+ *
+ *     y = Ktilde(X, X) w,        y_i ~ sum_j K(|x_i - x_j|) w_j          (eq. nbody, Sec. 3)
+ *
+ * for an isotropic kernel K with the paper's tree code (Algorithm 1, Sec. 3.2):
+ * a binary space partitioning tree over the points (Sec. 3.1), dense kernel
+ * blocks between each target and the leaves it is near to, and for every
+ * (target, node) pair that passes the far-field criterion of eq. accparam
+ *
+ *     max_{x' in node} |x' - c_node| / |x - c_node| < theta
+ *
+ * the order-p truncation of the generalized multipole expansion of Theorem 3.1
+ * (eq. finaltrunc, eq. kdef): source-to-multipole (s2m) coefficients per node
+ * and their multipole-to-target (m2t) evaluation.
+ *
+ * Conventions for every entry point:
+ *   - Array pointers are DEVICE pointers unless the name ends in _host.
+ *     The caller owns them; the library never frees or retains them past the call,
+ *     except that fkt_plan copies the points into the plan.
+ *   - Layouts: points row-major [N][d] float32 in the caller's order;
+ *     weights w, results y, right-hand sides b and solutions x are RHS-major
+ *     [nrhs][N] float32, in the caller's original point order.
+ *   - Work is enqueued on the plan's CUDA stream (given at fkt_plan) and is
+ *     asynchronous unless stated otherwise; fkt_plan, fkt_solve and the _host
+ *     calls synchronize that stream before returning.
+ *   - Every call returns an int status (FKT_OK = 0).  No C++ exception crosses
+ *     the ABI.  A plan is not thread-safe: calls on one plan must not overlap.
+ *   - Parameters that the paper leaves open are fixed as follows: the tree
+ *     splits boxes at the midpoint cycling the axes (Sec. 3.1 rules (a),(b)); the
+ *     node centre is the box midpoint and the node radius the largest distance
+ *     from a point of the node to it; the far test is evaluated per target point
+ *     in float64 as rho^2 < theta^2 |x - c|^2; singular kernels (Laplace) skip
+ *     exact r = 0 pairs, all other kernels include K(0) w_i.
+ */
+#ifndef FKT_H
+#define FKT_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---- */
+#define FKT_OK                0
+#define FKT_ERR_INVALID_ARG   1  /* an argument is out of range (see each call) */
+#define FKT_ERR_CUDA          2  /* a CUDA runtime call or kernel launch failed */
+#define FKT_ERR_OOM           3  /* device memory allocation failed */
+#define FKT_ERR_NOT_CONVERGED 4  /* fkt_solve reached max_iter above tol */
+#define FKT_ERR_TIMEOUT       5  /* a bounded device-side wait ran out */
+#define FKT_ERR_UNSUPPORTED   6  /* a valid request this build does not implement */
+#define FKT_ERR_INTERNAL      7  /* an internal consistency check failed (a library bug) */
+
+typedef struct fkt_plan_s* fkt_plan_t;
+
+/* Isotropic kernels.  l = lengthscale, a = alpha, s = scale (a multiplier):
+ *   FKT_GAUSSIAN     s exp(-r^2 / (2 l^2))
+ *   FKT_EXPONENTIAL  s exp(-r / l)                              (Table 1, Matern nu=1/2)
+ *   FKT_MATERN32     s (1 + sqrt3 r/l) exp(-sqrt3 r/l)          (Table 1)
+ *   FKT_MATERN52     s (1 + sqrt5 r/l + 5 r^2/(3 l^2)) exp(-sqrt5 r/l)
+ *   FKT_CAUCHY       s / (1 + r^2 / l^2)                        (Table 1, l = sigma)
+ *   FKT_RATQUAD      s (1 + r^2 / (2 a l^2))^(-a)               (Table 1 has a = 1/2)
+ *   FKT_LAPLACE      s / r      (Green's function: s = 1/(4 pi) in d = 3; r = 0 pairs skipped) */
+typedef enum {
+    FKT_GAUSSIAN = 0,
+    FKT_EXPONENTIAL = 1,
+    FKT_MATERN32 = 2,
+    FKT_MATERN52 = 3,
+    FKT_CAUCHY = 4,
+    FKT_RATQUAD = 5,
+    FKT_LAPLACE = 6
+} fkt_kernel_kind;
+
+typedef struct {
+    int kind;            /* fkt_kernel_kind */
+    double lengthscale;  /* l > 0 */
+    double alpha;        /* a > 0, used by FKT_RATQUAD only */
+    double scale;        /* s, any finite value */
+} fkt_kernel;
+
+/* Plan statistics.  Pair counts are exact and fixed by the method (they count
+ * what Algorithm 1 evaluates for this tree and theta), not by the implementation. */
+typedef struct {
+    int64_t N;
+    int32_t d, p;
+    int32_t nterms;          /* expansion size binom(p+d, d) (Sec. 4.2) */
+    int32_t leaf_size;
+    int32_t depth;           /* deepest level; the root is level 0 */
+    int64_t nodes, leaves;
+    int64_t target_blocks;   /* groups of <= 128 consecutive targets of one leaf */
+    int64_t far_entries, near_entries, masks;
+    int64_t far_pairs;       /* (target, far node) pairs: m2t evaluations */
+    int64_t near_pairs;      /* (target, source) pairs evaluated densely */
+    int64_t s2m_pairs;       /* (source, node) pairs: s2m basis evaluations */
+    int64_t s2m_nodes;       /* nodes whose coefficients some target uses */
+    double plan_ms;          /* wall time of fkt_plan */
+    double last_near_ms, last_far_ms, last_s2m_ms, last_total_ms; /* last fkt_mvm, if timing is on */
+} fkt_stats;
+
+/* Build a plan (Sec. 3.1 tree, far/near sets of Sec. 3.1-3.2, expansion tables of Theorem 3.1).
+ *   points     device [N][d] float32, finite
+ *   N          1 <= N < 2^31
+ *   d          3 or 4
+ *   kernel     see fkt_kernel; lengthscale > 0 (alpha > 0 for FKT_RATQUAD)
+ *   p          truncation order, 0 <= p <= 10 for d = 3, 0 <= p <= 8 for d = 4
+ *   leaf_size  largest number of points in a leaf that may still split, 1 <= leaf_size <= 4096
+ *   theta      far-field parameter of eq. accparam, 0 < theta < 1
+ *   cuda_stream  cudaStream_t to enqueue on, or NULL for the default stream
+ *   out        receives the plan; set to NULL on failure
+ * Errors: FKT_ERR_INVALID_ARG for the ranges above or non-finite points;
+ *         FKT_ERR_OOM / FKT_ERR_CUDA.  Synchronizes the stream. */
+int fkt_plan(const float* points, int64_t N, int d, fkt_kernel kernel, int p, int leaf_size,
+             double theta, void* cuda_stream, fkt_plan_t* out);
+
+/* y = Ktilde w  (Algorithm 1), overwriting y.  w, y device [nrhs][N] float32, 1 <= nrhs <= 64;
+ * w and y must not overlap.  Asynchronous on the plan's stream.
+ * Errors: FKT_ERR_INVALID_ARG (null plan/pointers, nrhs out of range), FKT_ERR_OOM, FKT_ERR_CUDA. */
+int fkt_mvm(fkt_plan_t plan, const float* w, float* y, int nrhs);
+
+/* Same as fkt_mvm with HOST buffers: copies w to the device, runs the MVM and copies y back.
+ * Pinned host memory gives the fastest copies.  Synchronizes the plan's stream. */
+int fkt_mvm_host(fkt_plan_t plan, const float* w_host, float* y_host, int nrhs);
+
+/* Exact dense product y_i = sum_j K(|x_i - x_j|) w_j (eq. nbody) on the GPU in float32 over the
+ * plan's points (same r = 0 rule).  Device [nrhs][N] buffers as for fkt_mvm.  O(N^2) work. */
+int fkt_dense_mvm(fkt_plan_t plan, const float* w, float* y, int nrhs);
+
+/* Options (all take effect on the next call):
+ *   "timing"    "0" | "1"   record per-stage CUDA-event times of fkt_mvm in fkt_stats
+ *   "far_precision"  "fp32" (default) | "tf32" | "bf16" | "bf16x3"  arithmetic of the far field
+ * Errors: FKT_ERR_INVALID_ARG for an unknown key or value. */
+int fkt_set_option(fkt_plan_t plan, const char* key, const char* value);
+
+/* Copy the plan's statistics into *out. */
+int fkt_plan_stats(fkt_plan_t plan, fkt_stats* out);
+
+/* Export the tree (Sec. 3.1), nodes in breadth-first order, host buffers sized from fkt_plan_stats:
+ *   perm [N]           sorted position -> caller's point index
+ *   begin, end [nodes] point range [begin, end) in sorted order
+ *   level, leaf [nodes], child [nodes][2] (-1 = none)
+ *   centre [nodes][d] float64, rho2 [nodes] float64
+ * Any pointer may be NULL to skip that array.  Synchronizes the stream. */
+int fkt_plan_tree(fkt_plan_t plan, int64_t* perm, int64_t* begin, int64_t* end, int32_t* level,
+                  int32_t* leaf, int64_t* child, double* centre, double* rho2);
+
+/* Export the interaction lists per target block (host buffers sized from fkt_plan_stats):
+ *   block_range [blocks][2]  sorted target range [lo, hi) of each block (hi - lo <= 128)
+ *   far_off [blocks+1], far_node [far_entries], far_mask [far_entries]
+ *   near_off [blocks+1], near_leaf [near_entries], near_mask [near_entries]
+ *   masks [masks][4] uint32: bit t of mask m is set when target lo+t takes the entry;
+ *   an entry whose mask index is -1 applies to every target of its block.
+ * Any pointer may be NULL.  Synchronizes the stream. */
+int fkt_plan_lists(fkt_plan_t plan, int64_t* block_range, int64_t* far_off, int32_t* far_node,
+                   int32_t* far_mask, int64_t* near_off, int32_t* near_leaf, int32_t* near_mask,
+                   uint32_t* masks);
+
+/* Release the plan and all device memory it owns.  NULL is ignored. */
+void fkt_destroy(fkt_plan_t plan);
+
+/* Static string for a status code. */
+const char* fkt_error_string(int status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FKT_H */

@@ -1,0 +1,238 @@
+// C ABI entry points (include/fkt.h).
+#include <math.h>
+#include <string.h>
+
+#include <chrono>
+#include <new>
+#include <vector>
+
+#include "fkt_internal.h"
+
+namespace {
+
+bool is_device_pointer(const void* p) {
+    cudaPointerAttributes at{};
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+void free_plan(fkt_plan_s* P) {
+    if (!P) return;
+    void* bufs[] = {P->xs, P->perm, P->codes, P->nd_begin, P->nd_end, P->nd_level, P->nd_leaf, P->nd_child,
+                    P->nd_centre, P->nd_rho2, P->nd_cf, P->nd_scale, P->nd_used, P->blk_range, P->far_off,
+                    P->near_off, P->far_ent, P->near_ent, P->masks, P->s2m_items, P->s2m_node_items,
+                    P->s2m_item_off, P->ws, P->ynear, P->mult, P->s2m_part, P->hbuf_w, P->hbuf_y};
+    for (void* b : bufs)
+        if (b) cudaFree(b);
+    for (auto& e : P->ev)
+        if (e) cudaEventDestroy(e);
+    if (P->stream2) cudaStreamDestroy(P->stream2);
+    delete P;
+}
+
+int valid_kernel(const fkt_kernel& k) {
+    if (k.kind < FKT_GAUSSIAN || k.kind > FKT_LAPLACE) return 0;
+    if (!(k.lengthscale > 0.0) || !isfinite(k.lengthscale)) return 0;
+    if (!isfinite(k.scale)) return 0;
+    if (k.kind == FKT_RATQUAD && (!(k.alpha > 0.0) || !isfinite(k.alpha))) return 0;
+    return 1;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* fkt_error_string(int status) {
+    switch (status) {
+    case FKT_OK: return "ok";
+    case FKT_ERR_INVALID_ARG: return "invalid argument";
+    case FKT_ERR_CUDA: return "CUDA error";
+    case FKT_ERR_OOM: return "out of device memory";
+    case FKT_ERR_NOT_CONVERGED: return "solver did not converge";
+    case FKT_ERR_TIMEOUT: return "device-side wait timed out";
+    case FKT_ERR_UNSUPPORTED: return "unsupported request";
+    case FKT_ERR_INTERNAL: return "internal consistency check failed";
+    default: return "unknown status";
+    }
+}
+
+int fkt_plan(const float* points, int64_t N, int d, fkt_kernel kernel, int p, int leaf_size, double theta,
+             void* cuda_stream, fkt_plan_t* out) {
+    if (out) *out = nullptr;
+    if (!out || !points || N < 1 || N > 0x7fffffffLL || (d != 3 && d != 4) || !valid_kernel(kernel)) return FKT_ERR_INVALID_ARG;
+    if (p < 0 || p > (d == 3 ? fkt::kMaxP3 : fkt::kMaxP4)) return FKT_ERR_INVALID_ARG;
+    if (leaf_size < 1 || leaf_size > 4096 || !(theta > 0.0 && theta < 1.0)) return FKT_ERR_INVALID_ARG;
+    if (!is_device_pointer(points)) return FKT_ERR_INVALID_ARG;
+    auto t0 = std::chrono::steady_clock::now();
+    fkt_plan_s* P = new (std::nothrow) fkt_plan_s();
+    if (!P) return FKT_ERR_OOM;
+    P->N = N;
+    P->d = d;
+    P->p = p;
+    P->leaf_size = leaf_size;
+    P->theta = theta;
+    P->kernel = kernel;
+    P->kp = fkt::make_kernel_params(kernel);
+    P->stream = (cudaStream_t)cuda_stream;
+    int rc = fkt::build_far_tables(d, p, &P->tabs);
+    if (rc) { free_plan(P); return rc; }
+    {
+        long long nt = 1;  // binom(p + d, d)
+        for (int i = 1; i <= d; ++i) nt = nt * (p + i) / i;
+        P->nterms = (int)nt;
+    }
+    if (cudaStreamCreateWithFlags(&P->stream2, cudaStreamNonBlocking) != cudaSuccess) { free_plan(P); return FKT_ERR_CUDA; }
+    for (auto& e : P->ev)
+        if (cudaEventCreate(&e) != cudaSuccess) { free_plan(P); return FKT_ERR_CUDA; }
+    rc = fkt::build_tree(P, points);
+    if (!rc) rc = fkt::build_lists(P);
+    if (!rc && cudaStreamSynchronize(P->stream) != cudaSuccess) rc = FKT_ERR_CUDA;
+    if (rc) { free_plan(P); return rc; }
+    fkt_stats& s = P->stats;
+    s.N = N;
+    s.d = d;
+    s.p = p;
+    s.nterms = P->nterms;
+    s.leaf_size = leaf_size;
+    s.depth = P->depth;
+    s.nodes = P->nnodes;
+    s.leaves = P->nleaves;
+    s.target_blocks = P->nblocks;
+    s.far_entries = P->nfar;
+    s.near_entries = P->nnear;
+    s.masks = P->nmasks;
+    s.plan_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    *out = P;
+    return FKT_OK;
+}
+
+int fkt_mvm(fkt_plan_t plan, const float* w, float* y, int nrhs) {
+    if (!plan || !w || !y || nrhs < 1 || nrhs > fkt::kMaxRhs || w == y) return FKT_ERR_INVALID_ARG;
+    return fkt::launch_mvm(plan, w, y, nrhs);
+}
+
+int fkt_mvm_host(fkt_plan_t plan, const float* w_host, float* y_host, int nrhs) {
+    if (!plan || !w_host || !y_host || nrhs < 1 || nrhs > fkt::kMaxRhs) return FKT_ERR_INVALID_ARG;
+    fkt_plan_s* P = plan;
+    const size_t bytes = sizeof(float) * (size_t)nrhs * P->N;
+    // device staging buffers, sized for the largest nrhs seen so far
+    if (P->hbuf_cap < nrhs) {
+        cudaFree(P->hbuf_w);
+        cudaFree(P->hbuf_y);
+        P->hbuf_w = P->hbuf_y = nullptr;
+        P->hbuf_cap = 0;
+        FKT_CUDA_TRY(cudaMalloc(&P->hbuf_w, bytes));
+        FKT_CUDA_TRY(cudaMalloc(&P->hbuf_y, bytes));
+        P->hbuf_cap = nrhs;
+    }
+    FKT_CUDA_TRY(cudaMemcpyAsync(P->hbuf_w, w_host, bytes, cudaMemcpyHostToDevice, P->stream));
+    int rc = fkt::launch_mvm(P, P->hbuf_w, P->hbuf_y, nrhs);
+    if (rc) return rc;
+    FKT_CUDA_TRY(cudaMemcpyAsync(y_host, P->hbuf_y, bytes, cudaMemcpyDeviceToHost, P->stream));
+    FKT_CUDA_TRY(cudaStreamSynchronize(P->stream));
+    return FKT_OK;
+}
+
+int fkt_dense_mvm(fkt_plan_t plan, const float* w, float* y, int nrhs) {
+    if (!plan || !w || !y || nrhs < 1 || nrhs > fkt::kMaxRhs || w == y) return FKT_ERR_INVALID_ARG;
+    return fkt::launch_dense(plan, w, y, nrhs);
+}
+
+int fkt_set_option(fkt_plan_t plan, const char* key, const char* value) {
+    if (!plan || !key || !value) return FKT_ERR_INVALID_ARG;
+    if (!strcmp(key, "timing")) {
+        if (!strcmp(value, "0")) plan->timing = false;
+        else if (!strcmp(value, "1")) plan->timing = true;
+        else return FKT_ERR_INVALID_ARG;
+        return FKT_OK;
+    }
+    if (!strcmp(key, "far_precision")) {
+        if (!strcmp(value, "fp32")) plan->far_precision = fkt::FAR_FP32;
+        else return !strcmp(value, "tf32") || !strcmp(value, "bf16") || !strcmp(value, "bf16x3") ? FKT_ERR_UNSUPPORTED
+                                                                                                   : FKT_ERR_INVALID_ARG;
+        return FKT_OK;
+    }
+    return FKT_ERR_INVALID_ARG;
+}
+
+int fkt_plan_stats(fkt_plan_t plan, fkt_stats* out) {
+    if (!plan || !out) return FKT_ERR_INVALID_ARG;
+    *out = plan->stats;
+    return FKT_OK;
+}
+
+int fkt_plan_tree(fkt_plan_t plan, int64_t* perm, int64_t* begin, int64_t* end, int32_t* level, int32_t* leaf,
+                  int64_t* child, double* centre, double* rho2) {
+    if (!plan) return FKT_ERR_INVALID_ARG;
+    fkt_plan_s* P = plan;
+    FKT_CUDA_TRY(cudaStreamSynchronize(P->stream));
+    const int64_t nn = P->nnodes, N = P->N;
+    std::vector<int32_t> t32;
+    if (perm) {
+        t32.resize(N);
+        FKT_CUDA_TRY(cudaMemcpy(t32.data(), P->perm, 4 * N, cudaMemcpyDeviceToHost));
+        for (int64_t i = 0; i < N; ++i) perm[i] = t32[i];
+    }
+    auto cp64 = [&](int64_t* dst, const int32_t* src, int64_t n) -> int {
+        t32.resize(n);
+        FKT_CUDA_TRY(cudaMemcpy(t32.data(), src, 4 * n, cudaMemcpyDeviceToHost));
+        for (int64_t i = 0; i < n; ++i) dst[i] = t32[i];
+        return FKT_OK;
+    };
+    int rc;
+    if (begin && (rc = cp64(begin, P->nd_begin, nn))) return rc;
+    if (end && (rc = cp64(end, P->nd_end, nn))) return rc;
+    if (child && (rc = cp64(child, P->nd_child, 2 * nn))) return rc;
+    if (level) FKT_CUDA_TRY(cudaMemcpy(level, P->nd_level, 4 * nn, cudaMemcpyDeviceToHost));
+    if (leaf) FKT_CUDA_TRY(cudaMemcpy(leaf, P->nd_leaf, 4 * nn, cudaMemcpyDeviceToHost));
+    if (rho2) FKT_CUDA_TRY(cudaMemcpy(rho2, P->nd_rho2, 8 * nn, cudaMemcpyDeviceToHost));
+    if (centre) {
+        std::vector<double> c4(4 * nn);
+        FKT_CUDA_TRY(cudaMemcpy(c4.data(), P->nd_centre, 8 * 4 * nn, cudaMemcpyDeviceToHost));
+        for (int64_t i = 0; i < nn; ++i)
+            for (int a = 0; a < P->d; ++a) centre[i * P->d + a] = c4[4 * i + a];
+    }
+    return FKT_OK;
+}
+
+int fkt_plan_lists(fkt_plan_t plan, int64_t* block_range, int64_t* far_off, int32_t* far_node, int32_t* far_mask,
+                   int64_t* near_off, int32_t* near_leaf, int32_t* near_mask, uint32_t* masks) {
+    if (!plan) return FKT_ERR_INVALID_ARG;
+    fkt_plan_s* P = plan;
+    FKT_CUDA_TRY(cudaStreamSynchronize(P->stream));
+    const int64_t nb = P->nblocks;
+    if (block_range) {
+        std::vector<int2> v(nb);
+        FKT_CUDA_TRY(cudaMemcpy(v.data(), P->blk_range, sizeof(int2) * nb, cudaMemcpyDeviceToHost));
+        for (int64_t i = 0; i < nb; ++i) { block_range[2 * i] = v[i].x; block_range[2 * i + 1] = v[i].y; }
+    }
+    if (far_off) FKT_CUDA_TRY(cudaMemcpy(far_off, P->far_off, 8 * (nb + 1), cudaMemcpyDeviceToHost));
+    if (near_off) FKT_CUDA_TRY(cudaMemcpy(near_off, P->near_off, 8 * (nb + 1), cudaMemcpyDeviceToHost));
+    auto split = [&](const int2* src, int64_t n, int32_t* a, int32_t* b) -> int {
+        std::vector<int2> v(n);
+        if (n) FKT_CUDA_TRY(cudaMemcpy(v.data(), src, sizeof(int2) * n, cudaMemcpyDeviceToHost));
+        for (int64_t i = 0; i < n; ++i) {
+            if (a) a[i] = v[i].x;
+            if (b) b[i] = v[i].y;
+        }
+        return FKT_OK;
+    };
+    int rc;
+    if ((far_node || far_mask) && (rc = split(P->far_ent, P->nfar, far_node, far_mask))) return rc;
+    if ((near_leaf || near_mask) && (rc = split(P->near_ent, P->nnear, near_leaf, near_mask))) return rc;
+    if (masks && P->nmasks)
+        FKT_CUDA_TRY(cudaMemcpy(masks, P->masks, sizeof(uint32_t) * fkt::kMaskWords * P->nmasks, cudaMemcpyDeviceToHost));
+    return FKT_OK;
+}
+
+void fkt_destroy(fkt_plan_t plan) {
+    if (!plan) return;
+    cudaStreamSynchronize(plan->stream);
+    cudaStreamSynchronize(plan->stream2);
+    free_plan(plan);
+}
+
+}  // extern "C"

@@ -1,0 +1,132 @@
+// Internal declarations of the GB300 FKT library (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/fkt.h"
+
+namespace fkt {
+
+constexpr int kMaxP3 = 10;        // largest order for d = 3
+constexpr int kMaxP4 = 8;         // largest order for d = 4
+constexpr int kTB = 128;          // targets per target block (one CTA)
+constexpr int kMaskWords = kTB / 32;
+constexpr int kMaxRhs = 64;
+constexpr int kMaxTerms = 495;    // binom(8+4, 4); binom(10+3, 3) = 286
+
+// Far-field coefficient tables handed to the kernels by value (they land in the
+// constant bank).  Index conventions:
+//   radial pairs (k, j), j = k, k+2, ..., <= p, enumerated k-major: kj index q
+//   That[q][m] = m! * Tbar_{k,j,m} for m <= j   (Theorem 3.1 with the m! of the
+//   scaled derivatives folded in, see tables.cpp)
+//   Legendre-type recurrence coefficients of the normalised solid harmonics (d = 3)
+//   and of the extra Gegenbauer chain level (d = 4).
+struct FarTables {
+    float That[36][11];      // radial pairs up to p = 10: 36 pairs, m <= 10
+    float hA[11][11];        // d=3: Pi_l^m = hA[l][m] z Pi_{l-1}^m - hB[l][m] r2 Pi_{l-2}^m
+    float hB[11][11];
+    float hSeed[11];         // Pi_m^m
+    float gA[9][9];          // d=4 chain level: Q_n^{(l)} = gA[l][n] x4 Q_{n-1} - gB[l][n] r2 Q_{n-2}
+    float gB[9][9];
+    float gSeed[9];          // normalisation of the chain level per l (Q_0^{(l)})
+};
+
+struct KernelParams {
+    int kind;
+    float ell, alpha, scale;
+    float c1, c2;            // kind-specific precomputed constants
+};
+
+enum FarPrecision { FAR_FP32 = 0, FAR_TF32 = 1, FAR_BF16 = 2, FAR_BF16X3 = 3 };
+
+}  // namespace fkt
+
+struct fkt_plan_s {
+    // problem
+    int64_t N = 0;
+    int d = 3, p = 0, leaf_size = 0, nterms = 0;
+    double theta = 0.5;
+    fkt_kernel kernel{};
+    fkt::KernelParams kp{};
+    fkt::FarTables tabs{};
+    cudaStream_t stream = nullptr;
+    bool timing = false;
+    int far_precision = fkt::FAR_FP32;
+    // bounding cube
+    double lo[4] = {0, 0, 0, 0};
+    double L = 1.0;
+    int B = 21;
+    // sorted points: float4 (x, y, z, u) per point, u = 0 for d = 3
+    float4* xs = nullptr;
+    int32_t* perm = nullptr;       // sorted -> original
+    uint64_t* codes = nullptr;
+    // tree, breadth-first
+    int64_t nnodes = 0, nleaves = 0;
+    int depth = 0;
+    int32_t* nd_begin = nullptr;
+    int32_t* nd_end = nullptr;
+    int32_t* nd_level = nullptr;
+    int32_t* nd_leaf = nullptr;
+    int32_t* nd_child = nullptr;   // [nodes][2]
+    double* nd_centre = nullptr;   // [nodes][4]
+    double* nd_rho2 = nullptr;
+    float4* nd_cf = nullptr;       // float32 centre (x, y, z, u)
+    float* nd_scale = nullptr;     // s2m/m2t length scale of the node
+    int32_t* nd_used = nullptr;    // 1 if some target uses the node's coefficients
+    // target blocks and lists
+    int64_t nblocks = 0, nfar = 0, nnear = 0, nmasks = 0;
+    int2* blk_range = nullptr;     // [lo, hi) sorted targets
+    int64_t* far_off = nullptr;    // [nblocks+1]
+    int64_t* near_off = nullptr;
+    int2* far_ent = nullptr;       // (node, mask)
+    int2* near_ent = nullptr;      // (leaf, mask)
+    uint32_t* masks = nullptr;     // [nmasks][kMaskWords]
+    // s2m work items (node, first point, last point)
+    int64_t n_s2m_items = 0;
+    int4* s2m_items = nullptr;     // (node, begin, end, unused)
+    int32_t* s2m_node_items = nullptr; // per used node: [first item, last item) -> via offsets
+    int64_t* s2m_item_off = nullptr;   // [nodes+1] item offsets per node (nodes without items: empty)
+    // per-MVM scratch (grown on demand)
+    int cap_rhs = 0;
+    float* ws = nullptr;           // sorted weights [nrhs][N]
+    float* ynear = nullptr;        // near-field result, sorted [nrhs][N]
+    float* mult = nullptr;         // multipoles [nodes][nterms][nrhs]
+    float* s2m_part = nullptr;     // per-item partial multipoles [items][nterms][nrhs]
+    float* hbuf_w = nullptr;       // device staging for fkt_mvm_host
+    float* hbuf_y = nullptr;
+    int hbuf_cap = 0;              // right-hand sides the staging buffers hold
+    cudaStream_t stream2 = nullptr;
+    cudaEvent_t ev[8] = {};
+    // stats
+    fkt_stats stats{};
+};
+
+namespace fkt {
+
+// tables.cpp
+int build_far_tables(int d, int p, FarTables* out);
+KernelParams make_kernel_params(const fkt_kernel& k);
+
+// tree.cu / lists.cu
+int build_tree(fkt_plan_s* P, const float* points);
+int build_lists(fkt_plan_s* P);
+
+// mvm.cu
+int launch_mvm(fkt_plan_s* P, const float* w, float* y, int nrhs);
+int launch_dense(fkt_plan_s* P, const float* w, float* y, int nrhs);
+int ensure_rhs_capacity(fkt_plan_s* P, int nrhs);
+
+}  // namespace fkt
+
+#define FKT_CUDA_TRY(expr)                                        \
+    do {                                                          \
+        cudaError_t e__ = (expr);                                 \
+        if (e__ != cudaSuccess) {                                 \
+            return e__ == cudaErrorMemoryAllocation ? FKT_ERR_OOM \
+                                                    : FKT_ERR_CUDA; \
+        }                                                         \
+    } while (0)

@@ -1,0 +1,237 @@
+// Device code of the FKT matrix-vector product (Algorithm 1), templated on the
+// dimension D (3 or 4), the truncation order P and the number of right-hand sides
+// NR handled per pass.
+//
+// Expansion used (Theorem 3.1, eq. finaltrunc, with the node length scale s):
+//   K(|x - x'|) ~ sum_{k<=P} sum_h Yt_kh(x/|x|) (s/r)^j R_kj(r) * (r'/s)^(j-k) St_kh(x'/s)
+//   over j = k, k+2, ..., <= P, where
+//     x = target - c, r = |x|; x' = source - c, r' = |x'|
+//     St_kh(y) = |y|^k Yt_kh(y/|y|)  (normalised solid harmonic, sum_h Yt_kh(u) Yt_kh(v) = C_k(u.v))
+//     R_kj(r)  = sum_{m<=j} That_{kjm} J_m(r),  J_m = K^(m)(r) r^m / m!   (That = m! Tbar)
+// so the source side is a polynomial in x'/s (no square roots) and every factor is
+// bounded: r' <= rho <= s, and far pairs have s/r < theta when s = rho.
+#pragma once
+
+#include "fkt_internal.h"
+
+namespace fkt {
+
+// ----------------------------------------------------------------- layout
+template <int D, int P>
+struct Layout {
+    static constexpr int nj(int k) { return (P - k) / 2 + 1; }
+    static constexpr int dk(int k) { return D == 3 ? 2 * k + 1 : (k + 1) * (k + 1); }
+    static constexpr int off(int k) {
+        int o = 0;
+        for (int i = 0; i < k; ++i) o += dk(i) * nj(i);
+        return o;
+    }
+    static constexpr int pair(int k) {  // index of the first (k, j) radial pair of degree k
+        int o = 0;
+        for (int i = 0; i < k; ++i) o += nj(i);
+        return o;
+    }
+    static constexpr int nterms = off(P + 1);
+    static constexpr int npairs = pair(P + 1);
+};
+
+// -------------------------------------------------------- kernel values
+template <int KIND>
+__device__ __forceinline__ float kernel_r2(float r2, const KernelParams& kp) {
+    if (KIND == FKT_GAUSSIAN) {
+        return kp.scale * __expf(-r2 * kp.c1);
+    } else if (KIND == FKT_EXPONENTIAL) {
+        float r = r2 * rsqrtf(fmaxf(r2, 1e-30f));
+        return kp.scale * __expf(-r * kp.c1);
+    } else if (KIND == FKT_MATERN32) {
+        float t = r2 * rsqrtf(fmaxf(r2, 1e-30f)) * kp.c1;
+        return kp.scale * (1.0f + t) * __expf(-t);
+    } else if (KIND == FKT_MATERN52) {
+        float t = r2 * rsqrtf(fmaxf(r2, 1e-30f)) * kp.c1;
+        return kp.scale * (1.0f + t + t * t * (1.0f / 3.0f)) * __expf(-t);
+    } else if (KIND == FKT_CAUCHY) {
+        return __fdividef(kp.scale, 1.0f + r2 * kp.c1);
+    } else if (KIND == FKT_RATQUAD) {
+        float b = 1.0f + r2 * kp.c1;
+        return kp.alpha == 1.0f ? __fdividef(kp.scale, b) : kp.scale * exp2f(-kp.alpha * __log2f(b));
+    } else {  // FKT_LAPLACE: r = 0 pairs contribute nothing
+        return r2 > 0.0f ? kp.scale * rsqrtf(r2) : 0.0f;
+    }
+}
+
+// Scaled Taylor coefficients J_m = K^(m)(r) r^m / m! of t -> K(r (1 + t)), m = 0..P,
+// from closed-form recurrences per kernel (float32).
+template <int P>
+__device__ __forceinline__ void kernel_jets(const KernelParams& kp, float r, float rinv, float J[P + 1]) {
+    switch (kp.kind) {
+    case FKT_GAUSSIAN: {  // exp(-a (1+t)^2): e_m = -(2a/m)(e_{m-1} + e_{m-2})
+        float a = r * r * kp.c1;
+        float E = kp.scale * __expf(-a);
+        float em2 = 0.f, em1 = 1.f;
+        J[0] = E;
+#pragma unroll
+        for (int m = 1; m <= P; ++m) {
+            float em = -(2.0f * a / m) * (em1 + em2);
+            J[m] = E * em;
+            em2 = em1;
+            em1 = em;
+        }
+        break;
+    }
+    case FKT_EXPONENTIAL: {  // exp(-b (1+t)): (-b)^m / m!
+        float b = r * kp.c1;
+        float v = kp.scale * __expf(-b);
+        J[0] = v;
+#pragma unroll
+        for (int m = 1; m <= P; ++m) { v *= -b / m; J[m] = v; }
+        break;
+    }
+    case FKT_MATERN32: {  // (1 + b + b t) exp(-b) exp(-b t)
+        float b = r * kp.c1;
+        float E[P + 1];
+        E[0] = kp.scale * __expf(-b);
+#pragma unroll
+        for (int m = 1; m <= P; ++m) E[m] = E[m - 1] * (-b / m);
+        J[0] = (1.0f + b) * E[0];
+#pragma unroll
+        for (int m = 1; m <= P; ++m) J[m] = (1.0f + b) * E[m] + b * E[m - 1];
+        break;
+    }
+    case FKT_MATERN52: {  // (1 + b(1+t) + b^2 (1+t)^2 / 3) exp(-b (1+t))
+        float b = r * kp.c1;
+        float p0 = 1.0f + b + b * b * (1.0f / 3.0f), p1 = b + b * b * (2.0f / 3.0f), p2 = b * b * (1.0f / 3.0f);
+        float E[P + 1];
+        E[0] = kp.scale * __expf(-b);
+#pragma unroll
+        for (int m = 1; m <= P; ++m) E[m] = E[m - 1] * (-b / m);
+#pragma unroll
+        for (int m = 0; m <= P; ++m) J[m] = p0 * E[m] + (m >= 1 ? p1 * E[m - 1] : 0.f) + (m >= 2 ? p2 * E[m - 2] : 0.f);
+        break;
+    }
+    case FKT_CAUCHY: {  // 1 / ((1+c) + 2c t + c t^2)
+        float c = r * r * kp.c1;
+        float inv = __fdividef(1.0f, 1.0f + c);
+        float qm2 = 0.f, qm1 = kp.scale * inv;
+        J[0] = qm1;
+#pragma unroll
+        for (int m = 1; m <= P; ++m) {
+            float q = -(2.0f * c * qm1 + c * qm2) * inv;
+            J[m] = q;
+            qm2 = qm1;
+            qm1 = q;
+        }
+        break;
+    }
+    case FKT_RATQUAD: {  // ((1+c) + 2c t + c t^2)^(-alpha):  m d0 f_m = sum_i (beta i - (m - i)) d_i f_{m-i}
+        float c = r * r * kp.c1;
+        float d0 = 1.0f + c, d1 = 2.0f * c, d2 = c, beta = -kp.alpha;
+        float inv = __fdividef(1.0f, d0);
+        float fm2 = 0.f, fm1 = kp.scale * exp2f(beta * __log2f(d0));
+        J[0] = fm1;
+#pragma unroll
+        for (int m = 1; m <= P; ++m) {
+            float f = ((beta - (m - 1)) * d1 * fm1 + (2.0f * beta - (m - 2)) * d2 * fm2) * inv / m;
+            J[m] = f;
+            fm2 = fm1;
+            fm1 = f;
+        }
+        break;
+    }
+    default: {  // FKT_LAPLACE: s / (r (1+t))
+        float v = kp.scale * rinv;
+#pragma unroll
+        for (int m = 0; m <= P; ++m) { J[m] = v; v = -v; }
+        break;
+    }
+    }
+}
+
+// ---------------------------------------------------- solid harmonics
+// Calls f(k, h, value) for every normalised solid harmonic St_kh(x) of degree k <= P,
+// in an l-major order.  r2_3 = x0^2 + x1^2 + x2^2, r2 = |x|^2 (r2 = r2_3 when D = 3).
+// The recurrences are those of Legendre-type polynomials in homogeneous form (no
+// square roots), so the same routine serves s2m (arbitrary x') and m2t (unit x).
+template <int D, int P, class F>
+__device__ __forceinline__ void solid_harmonics(float x0, float x1, float x2, float x3, float r2_3, float r2,
+                                                const FarTables& T, F&& f) {
+    float C[P + 1], S[P + 1];
+    C[0] = 1.f;
+    S[0] = 0.f;
+#pragma unroll
+    for (int m = 1; m <= P; ++m) {
+        C[m] = x0 * C[m - 1] - x1 * S[m - 1];
+        S[m] = x0 * S[m - 1] + x1 * C[m - 1];
+    }
+    float pm2[P + 1], pm1[P + 1], cur[P + 1];
+#pragma unroll
+    for (int m = 0; m <= P; ++m) { pm2[m] = 0.f; pm1[m] = 0.f; cur[m] = 0.f; }
+#pragma unroll
+    for (int l = 0; l <= P; ++l) {
+#pragma unroll
+        for (int m = 0; m <= l; ++m) {
+            if (m == l) cur[m] = T.hSeed[m];
+            else if (m == l - 1) cur[m] = T.hA[l][m] * x2 * pm1[m];
+            else cur[m] = T.hA[l][m] * x2 * pm1[m] - T.hB[l][m] * r2_3 * pm2[m];
+        }
+        if (D == 3) {
+            f(l, 0, cur[0]);
+#pragma unroll
+            for (int m = 1; m <= l; ++m) {
+                f(l, 2 * m - 1, cur[m] * C[m]);
+                f(l, 2 * m, cur[m] * S[m]);
+            }
+        } else {
+            // Gegenbauer chain factor Q_n^(l+1)(x3, r2), normalised, for k = l + n
+            float Q[P + 1];
+            Q[0] = T.gSeed[l];
+#pragma unroll
+            for (int n = 1; n + l <= P; ++n)
+                Q[n] = T.gA[l][n] * x3 * Q[n - 1] - (n >= 2 ? T.gB[l][n] * r2 * Q[n - 2] : 0.f);
+#pragma unroll
+            for (int n = 0; n + l <= P; ++n) {
+                const int k = l + n, hb = l * l;
+                f(k, hb, Q[n] * cur[0]);
+#pragma unroll
+                for (int m = 1; m <= l; ++m) {
+                    f(k, hb + 2 * m - 1, Q[n] * cur[m] * C[m]);
+                    f(k, hb + 2 * m, Q[n] * cur[m] * S[m]);
+                }
+            }
+        }
+#pragma unroll
+        for (int m = 0; m <= P; ++m) { pm2[m] = pm1[m]; pm1[m] = cur[m]; }
+    }
+}
+
+// --------------------------------------------------------------- arguments
+struct MvmArgs {
+    int64_t N;
+    const float4* xs;          // sorted points
+    const int32_t* perm;       // sorted -> original
+    const int2* blk;           // target blocks
+    const int64_t* far_off;
+    const int2* far_ent;
+    const int64_t* near_off;
+    const int2* near_ent;
+    const uint32_t* masks;
+    const int32_t* nd_begin;
+    const int32_t* nd_end;
+    const float4* nd_cf;
+    const float* nd_scale;
+    const int4* s2m_items;
+    const int64_t* s2m_item_off;
+    int64_t nnodes;
+    // per pass (one group of NR right-hand sides)
+    const float* ws;           // sorted weights of this group, [NR][N]
+    float* ynear;              // sorted near-field result of this group, [NR][N]
+    float* mult;               // multipoles of this group, [nodes][nterms][NR]
+    float* part;               // s2m partials, [items][nterms][NR]
+    float* y;                  // output (original order), [nrhs][N]; this group starts at y
+    int nr;                    // right-hand sides actually present in this group (<= NR)
+};
+
+__device__ __forceinline__ bool entry_active(int mask, const uint32_t* __restrict__ masks, int t) {
+    return mask < 0 || ((__ldg(&masks[(int64_t)mask * kMaskWords + (t >> 5)]) >> (t & 31)) & 1u);
+}
+
+}  // namespace fkt

@@ -1,0 +1,246 @@
+"""Thin ctypes binding of libfkt.so (include/fkt.h).
+
+Argument marshalling only: every step of the MVM runs in the library's CUDA
+kernels.  The module-level functions carry the C names (``fkt_plan``,
+``fkt_mvm``, ...) and take torch CUDA tensors; ``Plan`` wraps them.  If the
+library is missing this module raises -- there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libfkt.so")
+
+FKT_OK, FKT_ERR_INVALID_ARG, FKT_ERR_CUDA, FKT_ERR_OOM = 0, 1, 2, 3
+FKT_ERR_NOT_CONVERGED, FKT_ERR_TIMEOUT, FKT_ERR_UNSUPPORTED, FKT_ERR_INTERNAL = 4, 5, 6, 7
+
+KERNELS = {"gaussian": 0, "exponential": 1, "matern32": 2, "matern52": 3, "cauchy": 4, "ratquad": 5, "laplace": 6}
+
+# Every entry point declared in include/fkt.h.
+EXPORTS = ["fkt_plan", "fkt_mvm", "fkt_mvm_host", "fkt_dense_mvm", "fkt_set_option", "fkt_plan_stats",
+           "fkt_plan_tree", "fkt_plan_lists", "fkt_destroy", "fkt_error_string"]
+
+
+class FktError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        super().__init__(f"{where}: {lib().fkt_error_string(status).decode()} (status {status})")
+
+
+class fkt_kernel(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("lengthscale", ctypes.c_double), ("alpha", ctypes.c_double),
+                ("scale", ctypes.c_double)]
+
+
+class fkt_stats(ctypes.Structure):
+    _fields_ = [("N", ctypes.c_int64), ("d", ctypes.c_int32), ("p", ctypes.c_int32), ("nterms", ctypes.c_int32),
+                ("leaf_size", ctypes.c_int32), ("depth", ctypes.c_int32), ("nodes", ctypes.c_int64),
+                ("leaves", ctypes.c_int64), ("target_blocks", ctypes.c_int64), ("far_entries", ctypes.c_int64),
+                ("near_entries", ctypes.c_int64), ("masks", ctypes.c_int64), ("far_pairs", ctypes.c_int64),
+                ("near_pairs", ctypes.c_int64), ("s2m_pairs", ctypes.c_int64), ("s2m_nodes", ctypes.c_int64),
+                ("plan_ms", ctypes.c_double), ("last_near_ms", ctypes.c_double), ("last_far_ms", ctypes.c_double),
+                ("last_s2m_ms", ctypes.c_double), ("last_total_ms", ctypes.c_double)]
+
+
+_LIB = None
+
+
+def lib() -> ctypes.CDLL:
+    """Load libfkt.so (built by ``__graft_entry__.build()``); raises if it is missing."""
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"libfkt.so not built ({LIB_PATH}); run __graft_entry__.build()")
+    L = ctypes.CDLL(LIB_PATH)
+    vp, i64, i32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32
+    L.fkt_plan.argtypes = [vp, i64, ctypes.c_int, fkt_kernel, ctypes.c_int, ctypes.c_int, ctypes.c_double, vp,
+                           ctypes.POINTER(vp)]
+    L.fkt_mvm.argtypes = [vp, vp, vp, ctypes.c_int]
+    L.fkt_mvm_host.argtypes = [vp, vp, vp, ctypes.c_int]
+    L.fkt_dense_mvm.argtypes = [vp, vp, vp, ctypes.c_int]
+    L.fkt_set_option.argtypes = [vp, ctypes.c_char_p, ctypes.c_char_p]
+    L.fkt_plan_stats.argtypes = [vp, ctypes.POINTER(fkt_stats)]
+    L.fkt_plan_tree.argtypes = [vp] + [vp] * 8
+    L.fkt_plan_lists.argtypes = [vp] + [vp] * 8
+    L.fkt_destroy.argtypes = [vp]
+    L.fkt_destroy.restype = None
+    L.fkt_error_string.argtypes = [ctypes.c_int]
+    L.fkt_error_string.restype = ctypes.c_char_p
+    for name in EXPORTS:
+        if not hasattr(L, name):
+            raise RuntimeError(f"libfkt.so lacks {name}")
+    _LIB = L
+    return L
+
+
+def _check(status: int, where: str):
+    if status != FKT_OK:
+        raise FktError(status, where)
+
+
+def _ptr(a) -> ctypes.c_void_p:
+    if a is None:
+        return ctypes.c_void_p(0)
+    if isinstance(a, np.ndarray):
+        return ctypes.c_void_p(a.ctypes.data)
+    return ctypes.c_void_p(a.data_ptr())
+
+
+def _stream_ptr(stream) -> ctypes.c_void_p:
+    import torch
+
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def make_kernel(kernel: str, lengthscale: float = 1.0, alpha: float = 1.0, scale: float = 1.0) -> fkt_kernel:
+    return fkt_kernel(KERNELS[kernel], float(lengthscale), float(alpha), float(scale))
+
+
+# ---------------------------------------------------------------- C names
+def fkt_plan(points, kernel: fkt_kernel, p: int, leaf_size: int, theta: float, stream=None) -> ctypes.c_void_p:
+    """points: CUDA float32 tensor [N][d] (contiguous)."""
+    N, d = points.shape
+    h = ctypes.c_void_p()
+    _check(lib().fkt_plan(_ptr(points), N, d, kernel, p, leaf_size, float(theta), _stream_ptr(stream),
+                          ctypes.byref(h)), "fkt_plan")
+    return h
+
+
+def fkt_mvm(plan, w, y, nrhs: int):
+    _check(lib().fkt_mvm(plan, _ptr(w), _ptr(y), nrhs), "fkt_mvm")
+
+
+def fkt_mvm_host(plan, w_host, y_host, nrhs: int):
+    _check(lib().fkt_mvm_host(plan, _ptr(w_host), _ptr(y_host), nrhs), "fkt_mvm_host")
+
+
+def fkt_dense_mvm(plan, w, y, nrhs: int):
+    _check(lib().fkt_dense_mvm(plan, _ptr(w), _ptr(y), nrhs), "fkt_dense_mvm")
+
+
+def fkt_set_option(plan, key: str, value: str):
+    _check(lib().fkt_set_option(plan, key.encode(), value.encode()), "fkt_set_option")
+
+
+def fkt_plan_stats(plan) -> dict:
+    s = fkt_stats()
+    _check(lib().fkt_plan_stats(plan, ctypes.byref(s)), "fkt_plan_stats")
+    return {k: getattr(s, k) for k, _ in fkt_stats._fields_}
+
+
+def fkt_destroy(plan):
+    lib().fkt_destroy(plan)
+
+
+def fkt_error_string(status: int) -> str:
+    return lib().fkt_error_string(status).decode()
+
+
+# ------------------------------------------------------------- convenience
+class Plan:
+    """An FKT plan over fixed points: ``Plan(points, "matern32", lengthscale=0.2, p=6).mvm(w)``."""
+
+    def __init__(self, points, kernel: str = "gaussian", lengthscale: float = 1.0, alpha: float = 1.0,
+                 scale: float = 1.0, p: int = 4, leaf_size: int = 512, theta: float = 0.5, stream=None):
+        import torch
+
+        pts = points if isinstance(points, torch.Tensor) else torch.as_tensor(points)
+        self.points = pts.to(device="cuda", dtype=torch.float32).contiguous()
+        self.N, self.d = self.points.shape
+        self.kernel = make_kernel(kernel, lengthscale, alpha, scale)
+        self.p, self.leaf_size, self.theta = p, leaf_size, theta
+        self.stream = stream
+        self.h = fkt_plan(self.points, self.kernel, p, leaf_size, theta, stream)
+
+    def close(self):
+        if getattr(self, "h", None):
+            fkt_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _io(self, w, out):
+        import torch
+
+        w2 = w if w.dim() == 2 else w[None]
+        w2 = w2.to(device="cuda", dtype=torch.float32).contiguous()
+        if w2.shape[1] != self.N:
+            raise ValueError(f"w has {w2.shape[1]} points, plan has {self.N}")
+        y = out if out is not None else torch.empty_like(w2)
+        return w2, y
+
+    def mvm(self, w, out=None):
+        """y = Ktilde w for w of shape [N] or [nrhs][N] (CUDA float32)."""
+        w2, y = self._io(w, out)
+        fkt_mvm(self.h, w2, y, w2.shape[0])
+        return y if w.dim() == 2 else y[0]
+
+    def dense(self, w, out=None):
+        """Exact O(N^2) product on the GPU (float32)."""
+        w2, y = self._io(w, out)
+        fkt_dense_mvm(self.h, w2, y, w2.shape[0])
+        return y if w.dim() == 2 else y[0]
+
+    def mvm_host(self, w_host: np.ndarray, y_host: np.ndarray | None = None) -> np.ndarray:
+        """Host buffers in and out: the call copies to and from the device itself."""
+        w2 = np.ascontiguousarray(np.atleast_2d(w_host), dtype=np.float32)
+        y = y_host if y_host is not None else np.empty_like(w2)
+        fkt_mvm_host(self.h, w2, y, w2.shape[0])
+        return y
+
+    def set_option(self, key: str, value: str):
+        fkt_set_option(self.h, key, value)
+
+    def stats(self) -> dict:
+        return fkt_plan_stats(self.h)
+
+    def tree(self) -> dict:
+        s = self.stats()
+        n, N, d = s["nodes"], self.N, self.d
+        out = dict(perm=np.zeros(N, np.int64), begin=np.zeros(n, np.int64), end=np.zeros(n, np.int64),
+                   level=np.zeros(n, np.int32), leaf=np.zeros(n, np.int32), child=np.zeros((n, 2), np.int64),
+                   centre=np.zeros((n, d)), rho2=np.zeros(n))
+        _check(lib().fkt_plan_tree(self.h, *[_ptr(out[k]) for k in
+                                             ("perm", "begin", "end", "level", "leaf", "child", "centre", "rho2")]),
+               "fkt_plan_tree")
+        out["leaf"] = out["leaf"].astype(bool)
+        return out
+
+    def lists(self) -> dict:
+        s = self.stats()
+        nb, nf, nn, nm = s["target_blocks"], s["far_entries"], s["near_entries"], s["masks"]
+        out = dict(block_range=np.zeros((nb, 2), np.int64), far_off=np.zeros(nb + 1, np.int64),
+                   far_node=np.zeros(nf, np.int32), far_mask=np.zeros(nf, np.int32),
+                   near_off=np.zeros(nb + 1, np.int64), near_leaf=np.zeros(nn, np.int32),
+                   near_mask=np.zeros(nn, np.int32), masks=np.zeros((max(nm, 1), 4), np.uint32))
+        _check(lib().fkt_plan_lists(self.h, *[_ptr(out[k]) for k in
+                                              ("block_range", "far_off", "far_node", "far_mask", "near_off",
+                                               "near_leaf", "near_mask", "masks")]), "fkt_plan_lists")
+        return out
+
+    def target_sets(self, lists: dict | None = None):
+        """Per sorted target position: (far node set, near leaf set), decoded from the block lists."""
+        L = lists or self.lists()
+        far, near = {}, {}
+        for b, (lo, hi) in enumerate(L["block_range"]):
+            for t in range(lo, hi):
+                far[t], near[t] = [], []
+            for kind, off, ids, msk, dst in (("far", L["far_off"], L["far_node"], L["far_mask"], far),
+                                             ("near", L["near_off"], L["near_leaf"], L["near_mask"], near)):
+                for e in range(off[b], off[b + 1]):
+                    m = msk[e]
+                    for t in range(lo, hi):
+                        i = t - lo
+                        if m < 0 or (L["masks"][m][i >> 5] >> np.uint32(i & 31)) & np.uint32(1):
+                            dst[t].append(int(ids[e]))
+        return far, near
