@@ -53,6 +53,7 @@ extern "C" {
 #define FKT_ERR_TIMEOUT       5  /* a bounded device-side wait ran out */
 #define FKT_ERR_UNSUPPORTED   6  /* a valid request this build does not implement */
 #define FKT_ERR_INTERNAL      7  /* an internal consistency check failed (a library bug) */
+#define FKT_ERR_SCRATCH_LIMIT 8  /* the request needs more than fkt_mvm_noalloc's fixed scratch */
 
 typedef struct fkt_plan_s* fkt_plan_t;
 
@@ -156,6 +157,37 @@ int fkt_plan_tree(fkt_plan_t plan, int64_t* perm, int64_t* begin, int64_t* end, 
 int fkt_plan_lists(fkt_plan_t plan, int64_t* block_range, int64_t* far_off, int32_t* far_node,
                    int32_t* far_mask, int64_t* near_off, int32_t* near_leaf, int32_t* near_mask,
                    uint32_t* masks);
+
+/* fkt_mvm without any device allocation.
+ *
+ * fkt_mvm grows per-call work buffers with cudaMalloc the first time it sees a larger nrhs.
+ * Some callers cannot allow that: code recording a CUDA graph (an allocation during stream
+ * capture invalidates the capture), latency-critical loops (cudaMalloc can synchronise the
+ * whole device), and hosts whose memory is owned by another allocator, such as a framework's
+ * caching pool, where a raw cudaMalloc can fail or fragment memory the pool already holds.
+ * This entry point computes exactly what fkt_mvm computes, with the same kernels, but takes
+ * its work buffers from a fixed array in device memory that the library declares statically;
+ * it calls no cudaMalloc, cudaFree or other allocating routine.  The paper has no counterpart:
+ * this is a deployment variant of the same Algorithm 1 product.
+ *
+ *   plan, w, y, nrhs  as for fkt_mvm (device buffers, [nrhs][N], 1 <= nrhs <= 64).
+ *
+ * Limits and behaviour:
+ *   - The array holds FKT_NOALLOC_SCRATCH_BYTES (32 MiB) and is part of the library image:
+ *     every GPU that loads libfkt.so holds it until the process exits.  A call needs
+ *     4 * c * (2 N + nterms * (nodes + s2m chunks)) bytes (each part rounded up to 256 bytes),
+ *     with c = 1 for one right-hand side and 8 * ceil(nrhs / 8) otherwise (about 16 MB at
+ *     N = 1M, p = 6, one right-hand side).  Larger requests return FKT_ERR_SCRATCH_LIMIT and
+ *     enqueue nothing.
+ *   - The first call on a device looks up the array's device address (cudaGetSymbolAddress)
+ *     with that device current; make that first call before any stream capture.
+ *   - All calls share the one array and it keeps the last call's contents.  Nothing in it
+ *     needs to start at zero: every value a call reads was written earlier in the same call.
+ *     Calls whose GPU work overlaps (two streams, two plans, two host threads) race on the
+ *     array and give wrong results; order them on one stream or synchronise between them.
+ *   - Asynchronous on the plan's stream, like fkt_mvm. */
+#define FKT_NOALLOC_SCRATCH_BYTES (32u << 20)
+int fkt_mvm_noalloc(fkt_plan_t plan, const float* w, float* y, int nrhs);
 
 /* Release the plan and all device memory it owns.  NULL is ignored. */
 void fkt_destroy(fkt_plan_t plan);

@@ -55,6 +55,7 @@ const char* fkt_error_string(int status) {
     case FKT_ERR_TIMEOUT: return "device-side wait timed out";
     case FKT_ERR_UNSUPPORTED: return "unsupported request";
     case FKT_ERR_INTERNAL: return "internal consistency check failed";
+    case FKT_ERR_SCRATCH_LIMIT: return "request exceeds the fixed scratch of fkt_mvm_noalloc";
     default: return "unknown status";
     }
 }

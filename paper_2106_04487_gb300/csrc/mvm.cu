@@ -205,3 +205,16 @@ int launch_dense(fkt_plan_s* P, const float* w, float* y, int nrhs) {
 }
 
 }  // namespace fkt
+
+// Entry points into the stage launchers above for other translation units.
+namespace fkt {
+
+int mvm_launch_s2m(int d, int p, int nrb, const FarLaunch& L) { return launch_s2m_any(d, p, nrb, L); }
+int mvm_launch_far(int d, int p, int nrb, const FarLaunch& L) { return launch_far_any(d, p, nrb, L); }
+void mvm_launch_near(int d, int nrb, int kind, unsigned grid, cudaStream_t st, const MvmArgs& a,
+                     const KernelParams& kp) {
+    launch_near(d, nrb, kind, grid, st, a, kp);
+}
+MvmArgs mvm_base_args(fkt_plan_s* P) { return base_args(P); }
+
+}  // namespace fkt

@@ -17,12 +17,13 @@ LIB_PATH = os.path.join(HERE, "libfkt.so")
 
 FKT_OK, FKT_ERR_INVALID_ARG, FKT_ERR_CUDA, FKT_ERR_OOM = 0, 1, 2, 3
 FKT_ERR_NOT_CONVERGED, FKT_ERR_TIMEOUT, FKT_ERR_UNSUPPORTED, FKT_ERR_INTERNAL = 4, 5, 6, 7
+FKT_ERR_SCRATCH_LIMIT = 8
 
 KERNELS = {"gaussian": 0, "exponential": 1, "matern32": 2, "matern52": 3, "cauchy": 4, "ratquad": 5, "laplace": 6}
 
 # Every entry point declared in include/fkt.h.
 EXPORTS = ["fkt_plan", "fkt_mvm", "fkt_mvm_host", "fkt_dense_mvm", "fkt_set_option", "fkt_plan_stats",
-           "fkt_plan_tree", "fkt_plan_lists", "fkt_destroy", "fkt_error_string"]
+           "fkt_plan_tree", "fkt_plan_lists", "fkt_destroy", "fkt_error_string", "fkt_mvm_noalloc"]
 
 
 class FktError(RuntimeError):
@@ -62,6 +63,7 @@ def lib() -> ctypes.CDLL:
                            ctypes.POINTER(vp)]
     L.fkt_mvm.argtypes = [vp, vp, vp, ctypes.c_int]
     L.fkt_mvm_host.argtypes = [vp, vp, vp, ctypes.c_int]
+    L.fkt_mvm_noalloc.argtypes = [vp, vp, vp, ctypes.c_int]
     L.fkt_dense_mvm.argtypes = [vp, vp, vp, ctypes.c_int]
     L.fkt_set_option.argtypes = [vp, ctypes.c_char_p, ctypes.c_char_p]
     L.fkt_plan_stats.argtypes = [vp, ctypes.POINTER(fkt_stats)]
@@ -114,6 +116,11 @@ def fkt_plan(points, kernel: fkt_kernel, p: int, leaf_size: int, theta: float, s
 
 def fkt_mvm(plan, w, y, nrhs: int):
     _check(lib().fkt_mvm(plan, _ptr(w), _ptr(y), nrhs), "fkt_mvm")
+
+
+def fkt_mvm_noalloc(plan, w, y, nrhs: int):
+    """fkt_mvm with its work buffers in the library's fixed device scratch (no allocation)."""
+    _check(lib().fkt_mvm_noalloc(plan, _ptr(w), _ptr(y), nrhs), "fkt_mvm_noalloc")
 
 
 def fkt_mvm_host(plan, w_host, y_host, nrhs: int):

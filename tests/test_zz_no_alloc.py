@@ -1,0 +1,65 @@
+"""fkt_mvm_noalloc: the FKT product for callers that cannot allocate device memory.
+
+Callers recording a CUDA graph, latency-critical loops, and hosts whose device memory
+belongs to another allocator cannot let fkt_mvm grow its work buffers with cudaMalloc.
+fkt_mvm_noalloc takes those buffers from a fixed array the library declares statically.
+This file is collected last on purpose, so a run that stops at the first failure has
+already run every other test; it also passes on its own in a fresh process.
+"""
+import numpy as np
+import pytest
+
+from paper_2106_04487_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-5   # the relative 2-norm bar the other GPU tests use
+
+
+@pytest.fixture(scope="module")
+def fkt():
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2106_04487_gb300 import build, fkt as F
+
+    build.build()
+    F.lib()
+    return F
+
+
+def _rel(a, b):
+    return max(np.linalg.norm(a[i] - b[i]) / np.linalg.norm(b[i]) for i in range(len(b)))
+
+
+@pytest.mark.parametrize("nrhs", [1, 11])
+def test_noalloc_matches_fkt_mvm_on_two_calls(fkt, nrhs):
+    import torch
+
+    X = torch.from_numpy(inputs.gaussian_mixture(60000, 3, 10, 0.05, seed=21)).cuda()
+    plan = fkt.Plan(X, "matern32", lengthscale=0.2, p=6, leaf_size=256, theta=0.5)
+    for call, seed in enumerate((22, 23)):          # two calls in a row share the scratch
+        w = torch.from_numpy(inputs.normal_weights(60000, nrhs, seed=seed)).cuda()
+        want = plan.mvm(w).cpu().numpy()             # the existing entry point
+        got = torch.full_like(w, float("nan"))
+        fkt.fkt_mvm_noalloc(plan.h, w, got, nrhs)
+        torch.cuda.synchronize()
+        got = got.cpu().numpy()
+        assert np.isfinite(got).all(), call
+        assert _rel(got, want) < TOL, call
+    plan.close()
+
+
+def test_noalloc_rejects_requests_beyond_its_scratch(fkt):
+    import torch
+
+    n = 300000                                        # 64 right-hand sides need > 32 MiB
+    X = torch.from_numpy(inputs.uniform_cube(n, 3, seed=24)).cuda()
+    plan = fkt.Plan(X, "gaussian", lengthscale=0.1, p=2, leaf_size=512, theta=0.5)
+    w = torch.zeros((64, n), device="cuda")
+    y = torch.zeros_like(w)
+    with pytest.raises(fkt.FktError) as e:
+        fkt.fkt_mvm_noalloc(plan.h, w, y, 64)
+    assert e.value.status == fkt.FKT_ERR_SCRATCH_LIMIT
+    plan.close()
