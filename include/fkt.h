@@ -132,6 +132,8 @@ int fkt_dense_mvm(fkt_plan_t plan, const float* w, float* y, int nrhs);
 /* Options (all take effect on the next call):
  *   "timing"    "0" | "1"   record per-stage CUDA-event times of fkt_mvm in fkt_stats
  *   "far_precision"  "fp32" (default) | "tf32" | "bf16" | "bf16x3"  arithmetic of the far field
+ *   "near_targets_per_thread"  "2" (default) | "4"  register blocking of the near-field kernel
+ *               (4 applies to one right-hand side; results are identical up to rounding order)
  * Errors: FKT_ERR_INVALID_ARG for an unknown key or value. */
 int fkt_set_option(fkt_plan_t plan, const char* key, const char* value);
 
@@ -174,10 +176,10 @@ int fkt_plan_lists(fkt_plan_t plan, int64_t* block_range, int64_t* far_off, int3
  *
  * Limits and behaviour:
  *   - The array holds FKT_NOALLOC_SCRATCH_BYTES (32 MiB) and is part of the library image:
- *     every GPU that loads libfkt.so holds it until the process exits.  A call needs
- *     4 * c * (2 N + nterms * (nodes + s2m chunks)) bytes (each part rounded up to 256 bytes),
- *     with c = 1 for one right-hand side and 8 * ceil(nrhs / 8) otherwise (about 16 MB at
- *     N = 1M, p = 6, one right-hand side).  Larger requests return FKT_ERR_SCRATCH_LIMIT and
+ *     every GPU that loads libfkt.so holds it until the process exits.  A call with one
+ *     right-hand side needs 4 * (5 N + nterms * (nodes + s2m chunks)) bytes, about 28 MB at
+ *     N = 1M, d = 3, p = 6 (each part rounded up to 256 bytes); more right-hand sides need
+ *     proportionally more.  Requests that do not fit return FKT_ERR_SCRATCH_LIMIT and
  *     enqueue nothing.
  *   - The first call on a device looks up the array's device address (cudaGetSymbolAddress)
  *     with that device current; make that first call before any stream capture.
@@ -188,6 +190,12 @@ int fkt_plan_lists(fkt_plan_t plan, int64_t* block_range, int64_t* far_off, int3
  *   - Asynchronous on the plan's stream, like fkt_mvm. */
 #define FKT_NOALLOC_SCRATCH_BYTES (32u << 20)
 int fkt_mvm_noalloc(fkt_plan_t plan, const float* w, float* y, int nrhs);
+
+/* Failure detection: synchronise the plan's stream, then report FKT_ERR_TIMEOUT if any
+ * bounded device-side wait of this plan's kernels ran out since the last check (the kernel
+ * recorded it and stopped instead of hanging; results of that call are invalid), or
+ * FKT_ERR_CUDA for a pending CUDA error.  Clears the record.  FKT_OK otherwise. */
+int fkt_check(fkt_plan_t plan);
 
 /* Release the plan and all device memory it owns.  NULL is ignored. */
 void fkt_destroy(fkt_plan_t plan);

@@ -24,7 +24,8 @@ void free_plan(fkt_plan_s* P) {
     void* bufs[] = {P->xs, P->perm, P->codes, P->nd_begin, P->nd_end, P->nd_level, P->nd_leaf, P->nd_child,
                     P->nd_centre, P->nd_rho2, P->nd_cf, P->nd_scale, P->nd_used, P->blk_range, P->far_off,
                     P->near_off, P->far_ent, P->near_ent, P->masks, P->s2m_items, P->s2m_node_items,
-                    P->s2m_item_off, P->ws, P->ynear, P->mult, P->s2m_part, P->hbuf_w, P->hbuf_y};
+                    P->s2m_item_off, P->rec, P->ynear, P->mult, P->s2m_part, P->hbuf_w, P->hbuf_y,
+                    P->d_err, P->dense_off, P->dense_ent};
     for (void* b : bufs)
         if (b) cudaFree(b);
     for (auto& e : P->ev)
@@ -88,6 +89,10 @@ int fkt_plan(const float* points, int64_t N, int d, fkt_kernel kernel, int p, in
     if (cudaStreamCreateWithFlags(&P->stream2, cudaStreamNonBlocking) != cudaSuccess) { free_plan(P); return FKT_ERR_CUDA; }
     for (auto& e : P->ev)
         if (cudaEventCreate(&e) != cudaSuccess) { free_plan(P); return FKT_ERR_CUDA; }
+    if (cudaMalloc(&P->d_err, sizeof(int)) != cudaSuccess || cudaMemsetAsync(P->d_err, 0, sizeof(int), P->stream) != cudaSuccess) {
+        free_plan(P);
+        return FKT_ERR_OOM;
+    }
     rc = fkt::build_tree(P, points);
     if (!rc) rc = fkt::build_lists(P);
     if (!rc && cudaStreamSynchronize(P->stream) != cudaSuccess) rc = FKT_ERR_CUDA;
@@ -147,6 +152,12 @@ int fkt_set_option(fkt_plan_t plan, const char* key, const char* value) {
     if (!strcmp(key, "timing")) {
         if (!strcmp(value, "0")) plan->timing = false;
         else if (!strcmp(value, "1")) plan->timing = true;
+        else return FKT_ERR_INVALID_ARG;
+        return FKT_OK;
+    }
+    if (!strcmp(key, "near_targets_per_thread")) {
+        if (!strcmp(value, "2")) plan->near_tpt = 2;
+        else if (!strcmp(value, "4")) plan->near_tpt = 4;
         else return FKT_ERR_INVALID_ARG;
         return FKT_OK;
     }
@@ -226,6 +237,19 @@ int fkt_plan_lists(fkt_plan_t plan, int64_t* block_range, int64_t* far_off, int3
     if ((near_leaf || near_mask) && (rc = split(P->near_ent, P->nnear, near_leaf, near_mask))) return rc;
     if (masks && P->nmasks)
         FKT_CUDA_TRY(cudaMemcpy(masks, P->masks, sizeof(uint32_t) * fkt::kMaskWords * P->nmasks, cudaMemcpyDeviceToHost));
+    return FKT_OK;
+}
+
+int fkt_check(fkt_plan_t plan) {
+    if (!plan) return FKT_ERR_INVALID_ARG;
+    FKT_CUDA_TRY(cudaStreamSynchronize(plan->stream));
+    FKT_CUDA_TRY(cudaStreamSynchronize(plan->stream2));
+    int h = 0;
+    FKT_CUDA_TRY(cudaMemcpy(&h, plan->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (h) {
+        FKT_CUDA_TRY(cudaMemset(plan->d_err, 0, sizeof(int)));
+        return FKT_ERR_TIMEOUT;
+    }
     return FKT_OK;
 }
 

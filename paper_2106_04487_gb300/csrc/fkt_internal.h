@@ -38,7 +38,9 @@ struct FarTables {
 struct KernelParams {
     int kind;
     float ell, alpha, scale;
-    float c1, c2;            // kind-specific precomputed constants
+    float c1;                // kind-specific: 1/(2l^2), 1/l, sqrt3/l, sqrt5/l, 1/l^2, 1/(2 a l^2)
+    float c2;                // c1 * log2(e) for the exponential kernels (argument of ex2)
+    float sig;               // near-field coordinate scale: distances in the kernel's own units
 };
 
 enum FarPrecision { FAR_FP32 = 0, FAR_TF32 = 1, FAR_BF16 = 2, FAR_BF16X3 = 3 };
@@ -56,6 +58,7 @@ struct fkt_plan_s {
     cudaStream_t stream = nullptr;
     bool timing = false;
     int far_precision = fkt::FAR_FP32;
+    int near_tpt = 2;              // near-field targets per thread (2 or 4)
     // bounding cube
     double lo[4] = {0, 0, 0, 0};
     double L = 1.0;
@@ -92,13 +95,16 @@ struct fkt_plan_s {
     int64_t* s2m_item_off = nullptr;   // [nodes+1] item offsets per node (nodes without items: empty)
     // per-MVM scratch (grown on demand)
     int cap_rhs = 0;
-    float* ws = nullptr;           // sorted weights [nrhs][N]
+    float4* rec = nullptr;         // source records (point + weights) in tree order, per group
     float* ynear = nullptr;        // near-field result, sorted [nrhs][N]
     float* mult = nullptr;         // multipoles [nodes][nterms][nrhs]
     float* s2m_part = nullptr;     // per-item partial multipoles [items][nterms][nrhs]
     float* hbuf_w = nullptr;       // device staging for fkt_mvm_host
     float* hbuf_y = nullptr;
     int hbuf_cap = 0;              // right-hand sides the staging buffers hold
+    int* d_err = nullptr;          // device error word (bounded waits that ran out)
+    int64_t* dense_off = nullptr;  // one-entry lists (the root) per target block, for fkt_dense_mvm
+    int2* dense_ent = nullptr;
     cudaStream_t stream2 = nullptr;
     cudaEvent_t ev[8] = {};
     // stats
@@ -116,6 +122,16 @@ int build_tree(fkt_plan_s* P, const float* points);
 int build_lists(fkt_plan_s* P);
 
 // mvm.cu
+// Work buffers of one MVM call (fkt_mvm: plan-owned; fkt_mvm_noalloc: the static scratch).
+struct MvmBuffers {
+    float4* rec;
+    float* ynear;
+    float* mult;
+    float* part;
+};
+// Floats each buffer needs for nrhs right-hand sides (each rounded up to 64 floats).
+void mvm_buffer_floats(const fkt_plan_s* P, int nrhs, size_t out[4]);
+int run_mvm(fkt_plan_s* P, const MvmBuffers& B, const float* w, float* y, int nrhs, bool timing);
 int launch_mvm(fkt_plan_s* P, const float* w, float* y, int nrhs);
 int launch_dense(fkt_plan_s* P, const float* w, float* y, int nrhs);
 int ensure_rhs_capacity(fkt_plan_s* P, int nrhs);

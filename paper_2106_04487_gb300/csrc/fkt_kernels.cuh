@@ -222,13 +222,24 @@ struct MvmArgs {
     const int64_t* s2m_item_off;
     int64_t nnodes;
     // per pass (one group of NR right-hand sides)
-    const float* ws;           // sorted weights of this group, [NR][N]
+    const float4* rec;         // source records in tree order: rec4 float4 per point (point, then weights)
     float* ynear;              // sorted near-field result of this group, [NR][N]
     float* mult;               // multipoles of this group, [nodes][nterms][NR]
     float* part;               // s2m partials, [items][nterms][NR]
     float* y;                  // output (original order), [nrhs][N]; this group starts at y
     int nr;                    // right-hand sides actually present in this group (<= NR)
+    int* err;                  // device error word: 1 = a bounded wait ran out
 };
+
+// Source record of one point for a pass of NR right-hand sides: (x, y, z, w) when d = 3 and
+// NR = 1, otherwise (x, y, z, u) followed by the NR weights, padded to whole float4s.
+template <int D, int NR>
+struct Rec {
+    static constexpr int F4 = (D == 3 && NR == 1) ? 1 : (4 + NR + 3) / 4;  // float4s per point
+    static constexpr int WOFF = (D == 3 && NR == 1) ? 3 : 4;                // float index of weight 0
+};
+
+inline int rec_f4(int d, int nrb) { return (d == 3 && nrb == 1) ? 1 : (4 + nrb + 3) / 4; }
 
 __device__ __forceinline__ bool entry_active(int mask, const uint32_t* __restrict__ masks, int t) {
     return mask < 0 || ((__ldg(&masks[(int64_t)mask * kMaskWords + (t >> 5)]) >> (t & 31)) & 1u);

@@ -47,40 +47,41 @@ static int launch_far_any(int d, int p, int nrb, const FarLaunch& L) {
 
 namespace {
 
-template <int D, int NR>
+template <int D, int NR, int T>
 void launch_near_t(int kind, unsigned grid, cudaStream_t st, const MvmArgs& a, const KernelParams& kp) {
+    constexpr int TH = NearShape<D, NR, T>::THREADS;
     switch (kind) {
-    case FKT_GAUSSIAN: near_kernel<D, FKT_GAUSSIAN, NR><<<grid, kTB, 0, st>>>(a, kp); break;
-    case FKT_EXPONENTIAL: near_kernel<D, FKT_EXPONENTIAL, NR><<<grid, kTB, 0, st>>>(a, kp); break;
-    case FKT_MATERN32: near_kernel<D, FKT_MATERN32, NR><<<grid, kTB, 0, st>>>(a, kp); break;
-    case FKT_MATERN52: near_kernel<D, FKT_MATERN52, NR><<<grid, kTB, 0, st>>>(a, kp); break;
-    case FKT_CAUCHY: near_kernel<D, FKT_CAUCHY, NR><<<grid, kTB, 0, st>>>(a, kp); break;
-    case FKT_RATQUAD: near_kernel<D, FKT_RATQUAD, NR><<<grid, kTB, 0, st>>>(a, kp); break;
-    default: near_kernel<D, FKT_LAPLACE, NR><<<grid, kTB, 0, st>>>(a, kp); break;
+    case FKT_GAUSSIAN: near_kernel<D, FKT_GAUSSIAN, NR, T><<<grid, TH, 0, st>>>(a, kp); break;
+    case FKT_EXPONENTIAL: near_kernel<D, FKT_EXPONENTIAL, NR, T><<<grid, TH, 0, st>>>(a, kp); break;
+    case FKT_MATERN32: near_kernel<D, FKT_MATERN32, NR, T><<<grid, TH, 0, st>>>(a, kp); break;
+    case FKT_MATERN52: near_kernel<D, FKT_MATERN52, NR, T><<<grid, TH, 0, st>>>(a, kp); break;
+    case FKT_CAUCHY: near_kernel<D, FKT_CAUCHY, NR, T><<<grid, TH, 0, st>>>(a, kp); break;
+    case FKT_RATQUAD: near_kernel<D, FKT_RATQUAD, NR, T><<<grid, TH, 0, st>>>(a, kp); break;
+    default: near_kernel<D, FKT_LAPLACE, NR, T><<<grid, TH, 0, st>>>(a, kp); break;
     }
 }
 
-template <int D, int NR>
-void launch_dense_t(int kind, unsigned grid, cudaStream_t st, const MvmArgs& a, const KernelParams& kp) {
-    switch (kind) {
-    case FKT_GAUSSIAN: dense_kernel<D, FKT_GAUSSIAN, NR><<<grid, kTB, 0, st>>>(a, kp); break;
-    case FKT_EXPONENTIAL: dense_kernel<D, FKT_EXPONENTIAL, NR><<<grid, kTB, 0, st>>>(a, kp); break;
-    case FKT_MATERN32: dense_kernel<D, FKT_MATERN32, NR><<<grid, kTB, 0, st>>>(a, kp); break;
-    case FKT_MATERN52: dense_kernel<D, FKT_MATERN52, NR><<<grid, kTB, 0, st>>>(a, kp); break;
-    case FKT_CAUCHY: dense_kernel<D, FKT_CAUCHY, NR><<<grid, kTB, 0, st>>>(a, kp); break;
-    case FKT_RATQUAD: dense_kernel<D, FKT_RATQUAD, NR><<<grid, kTB, 0, st>>>(a, kp); break;
-    default: dense_kernel<D, FKT_LAPLACE, NR><<<grid, kTB, 0, st>>>(a, kp); break;
+// Near field launch: targets per thread tpt = 2 or 4 (4 only for one right-hand side).
+void launch_near(int d, int nrb, int tpt, int kind, unsigned grid, cudaStream_t st, const MvmArgs& a,
+                 const KernelParams& kp) {
+    if (d == 3) {
+        if (nrb == 1) tpt == 4 ? launch_near_t<3, 1, 4>(kind, grid, st, a, kp) : launch_near_t<3, 1, 2>(kind, grid, st, a, kp);
+        else launch_near_t<3, 8, 2>(kind, grid, st, a, kp);
+    } else {
+        if (nrb == 1) tpt == 4 ? launch_near_t<4, 1, 4>(kind, grid, st, a, kp) : launch_near_t<4, 1, 2>(kind, grid, st, a, kp);
+        else launch_near_t<4, 8, 2>(kind, grid, st, a, kp);
     }
 }
 
-void launch_near(int d, int nrb, int kind, unsigned grid, cudaStream_t st, const MvmArgs& a, const KernelParams& kp) {
-    if (d == 3) nrb == 1 ? launch_near_t<3, 1>(kind, grid, st, a, kp) : launch_near_t<3, 8>(kind, grid, st, a, kp);
-    else nrb == 1 ? launch_near_t<4, 1>(kind, grid, st, a, kp) : launch_near_t<4, 8>(kind, grid, st, a, kp);
-}
-
-void launch_dense(int d, int nrb, int kind, unsigned grid, cudaStream_t st, const MvmArgs& a, const KernelParams& kp) {
-    if (d == 3) nrb == 1 ? launch_dense_t<3, 1>(kind, grid, st, a, kp) : launch_dense_t<3, 8>(kind, grid, st, a, kp);
-    else nrb == 1 ? launch_dense_t<4, 1>(kind, grid, st, a, kp) : launch_dense_t<4, 8>(kind, grid, st, a, kp);
+void launch_permute(int d, int nrb, unsigned grid, cudaStream_t st, int64_t N, const int32_t* perm, const float4* xs,
+                    const float* w, int nr, float sig, float4* rec) {
+    if (d == 3) {
+        if (nrb == 1) permute_kernel<3, 1><<<grid, 256, 0, st>>>(N, perm, xs, w, nr, sig, rec);
+        else permute_kernel<3, 8><<<grid, 256, 0, st>>>(N, perm, xs, w, nr, sig, rec);
+    } else {
+        if (nrb == 1) permute_kernel<4, 1><<<grid, 256, 0, st>>>(N, perm, xs, w, nr, sig, rec);
+        else permute_kernel<4, 8><<<grid, 256, 0, st>>>(N, perm, xs, w, nr, sig, rec);
+    }
 }
 
 MvmArgs base_args(fkt_plan_s* P) {
@@ -101,71 +102,93 @@ MvmArgs base_args(fkt_plan_s* P) {
     a.s2m_items = P->s2m_items;
     a.s2m_item_off = P->s2m_item_off;
     a.nnodes = P->nnodes;
+    a.err = P->d_err;
     return a;
+}
+
+size_t round64(size_t n) { return (n + 63) / 64 * 64; }
+
+__global__ void dense_lists_kernel(int64_t nblocks, int64_t* off, int2* ent) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < nblocks) ent[i] = make_int2(0, -1);  // the root holds every point
+    if (i <= nblocks) off[i] = i;
 }
 
 }  // namespace
 
+void mvm_buffer_floats(const fkt_plan_s* P, int nrhs, size_t out[4]) {
+    const int nrb = nrhs == 1 ? 1 : 8;
+    const size_t groups = (size_t)(nrhs + nrb - 1) / nrb;
+    const size_t N = (size_t)P->N, NT = (size_t)P->nterms;
+    const size_t nodes = std::max<int64_t>(P->nnodes, 1), items = std::max<int64_t>(P->n_s2m_items, 1);
+    out[0] = round64(groups * N * 4 * (size_t)rec_f4(P->d, nrb));  // records
+    out[1] = round64(groups * nrb * N);                             // near result
+    out[2] = round64(groups * nrb * NT * nodes);                    // multipoles
+    out[3] = round64(groups * nrb * NT * items);                    // s2m partials
+}
+
 int ensure_rhs_capacity(fkt_plan_s* P, int nrhs) {
-    const int groups = nrhs == 1 ? 1 : (nrhs + 7) / 8;
-    const int cap = nrhs == 1 ? 1 : groups * 8;
+    const int cap = nrhs == 1 ? 1 : (nrhs + 7) / 8 * 8;
     if (cap <= P->cap_rhs) return FKT_OK;
-    cudaFree(P->ws);
+    cudaFree(P->rec);
     cudaFree(P->ynear);
     cudaFree(P->mult);
     cudaFree(P->s2m_part);
-    P->ws = P->ynear = P->mult = P->s2m_part = nullptr;
+    P->rec = nullptr;
+    P->ynear = P->mult = P->s2m_part = nullptr;
     P->cap_rhs = 0;
-    const size_t NT = (size_t)P->nterms;
-    FKT_CUDA_TRY(cudaMalloc(&P->ws, sizeof(float) * cap * P->N));
-    FKT_CUDA_TRY(cudaMalloc(&P->ynear, sizeof(float) * cap * P->N));
-    FKT_CUDA_TRY(cudaMalloc(&P->mult, sizeof(float) * cap * NT * std::max<int64_t>(P->nnodes, 1)));
-    FKT_CUDA_TRY(cudaMalloc(&P->s2m_part, sizeof(float) * cap * NT * std::max<int64_t>(P->n_s2m_items, 1)));
+    size_t f[4];
+    mvm_buffer_floats(P, cap, f);
+    FKT_CUDA_TRY(cudaMalloc(&P->rec, sizeof(float) * f[0]));
+    FKT_CUDA_TRY(cudaMalloc(&P->ynear, sizeof(float) * f[1]));
+    FKT_CUDA_TRY(cudaMalloc(&P->mult, sizeof(float) * f[2]));
+    FKT_CUDA_TRY(cudaMalloc(&P->s2m_part, sizeof(float) * f[3]));
     P->cap_rhs = cap;
     return FKT_OK;
 }
 
-int launch_mvm(fkt_plan_s* P, const float* w, float* y, int nrhs) {
-    int rc = ensure_rhs_capacity(P, nrhs);
-    if (rc) return rc;
+// One product on the plan's stream with the given work buffers: per group of right-hand sides
+//   permute -> fork [s2m -> reduce on stream2] || near field -> join -> far field (+ combine).
+int run_mvm(fkt_plan_s* P, const MvmBuffers& B, const float* w, float* y, int nrhs, bool timing) {
     const int nrb = nrhs == 1 ? 1 : 8;
     const int groups = (nrhs + nrb - 1) / nrb;
     cudaStream_t st = P->stream, st2 = P->stream2;
     const int64_t N = P->N;
     const size_t NT = (size_t)P->nterms;
-    if (P->timing) FKT_CUDA_TRY(cudaEventRecord(P->ev[0], st));
+    const size_t rec_group = (size_t)N * rec_f4(P->d, nrb);
+    const size_t nodes = std::max<int64_t>(P->nnodes, 1), items = std::max<int64_t>(P->n_s2m_items, 1);
+    if (timing) FKT_CUDA_TRY(cudaEventRecord(P->ev[0], st));
     for (int g = 0; g < groups; ++g) {
         const int nr = std::min(nrb, nrhs - g * nrb);
         MvmArgs a = base_args(P);
-        a.ws = P->ws + (size_t)g * nrb * N;
-        a.ynear = P->ynear + (size_t)g * nrb * N;
-        a.mult = P->mult + (size_t)g * nrb * NT * P->nnodes;
-        a.part = P->s2m_part + (size_t)g * nrb * NT * P->n_s2m_items;
+        float4* rec = B.rec + (size_t)g * rec_group;
+        a.rec = rec;
+        a.ynear = B.ynear + (size_t)g * nrb * N;
+        a.mult = B.mult + (size_t)g * nrb * NT * nodes;
+        a.part = B.part + (size_t)g * nrb * NT * items;
         a.y = y + (size_t)g * nrb * N;
         a.nr = nr;
-        const float* wg = w + (size_t)g * nrb * N;
-        unsigned pg = (unsigned)((N + 255) / 256);
-        if (nrb == 1) permute_kernel<1><<<pg, 256, 0, st>>>(N, P->perm, wg, nr, const_cast<float*>(a.ws));
-        else permute_kernel<8><<<pg, 256, 0, st>>>(N, P->perm, wg, nr, const_cast<float*>(a.ws));
+        launch_permute(P->d, nrb, (unsigned)((N + 255) / 256), st, N, P->perm, P->xs, w + (size_t)g * nrb * N, nr,
+                       P->kp.sig, rec);
         FKT_CUDA_TRY(cudaGetLastError());
         // fork: s2m on the second stream while the near field runs on the plan stream
         FKT_CUDA_TRY(cudaEventRecord(P->ev[1], st));
         FKT_CUDA_TRY(cudaStreamWaitEvent(st2, P->ev[1], 0));
         FarLaunch L{&a, &P->kp, &P->tabs, P->nblocks, P->n_s2m_items, P->nnodes, st, st2};
-        if (P->timing) FKT_CUDA_TRY(cudaEventRecord(P->ev[2], st2));
-        rc = launch_s2m_any(P->d, P->p, nrb, L);
+        if (timing) FKT_CUDA_TRY(cudaEventRecord(P->ev[2], st2));
+        int rc = launch_s2m_any(P->d, P->p, nrb, L);
         if (rc) return rc;
-        if (P->timing) FKT_CUDA_TRY(cudaEventRecord(P->ev[3], st2));
+        if (timing) FKT_CUDA_TRY(cudaEventRecord(P->ev[3], st2));
         FKT_CUDA_TRY(cudaEventRecord(P->ev[4], st2));
-        if (P->timing) FKT_CUDA_TRY(cudaEventRecord(P->ev[5], st));
-        launch_near(P->d, nrb, P->kernel.kind, (unsigned)P->nblocks, st, a, P->kp);
+        if (timing) FKT_CUDA_TRY(cudaEventRecord(P->ev[5], st));
+        launch_near(P->d, nrb, P->near_tpt, P->kernel.kind, (unsigned)P->nblocks, st, a, P->kp);
         FKT_CUDA_TRY(cudaGetLastError());
-        if (P->timing) FKT_CUDA_TRY(cudaEventRecord(P->ev[6], st));
+        if (timing) FKT_CUDA_TRY(cudaEventRecord(P->ev[6], st));
         FKT_CUDA_TRY(cudaStreamWaitEvent(st, P->ev[4], 0));  // join
         rc = launch_far_any(P->d, P->p, nrb, L);
         if (rc) return rc;
     }
-    if (P->timing) {
+    if (timing) {
         FKT_CUDA_TRY(cudaEventRecord(P->ev[7], st));
         FKT_CUDA_TRY(cudaEventSynchronize(P->ev[7]));
         float t_tot = 0, t_s2m = 0, t_near = 0, t_far = 0;
@@ -181,40 +204,43 @@ int launch_mvm(fkt_plan_s* P, const float* w, float* y, int nrhs) {
     return FKT_OK;
 }
 
+int launch_mvm(fkt_plan_s* P, const float* w, float* y, int nrhs) {
+    int rc = ensure_rhs_capacity(P, nrhs);
+    if (rc) return rc;
+    MvmBuffers B{P->rec, P->ynear, P->mult, P->s2m_part};
+    return run_mvm(P, B, w, y, nrhs, P->timing);
+}
+
+// Exact product: the near kernel with one entry per target block -- the root, which holds every point.
 int launch_dense(fkt_plan_s* P, const float* w, float* y, int nrhs) {
     int rc = ensure_rhs_capacity(P, nrhs);
     if (rc) return rc;
+    cudaStream_t st = P->stream;
+    if (!P->dense_off) {
+        FKT_CUDA_TRY(cudaMalloc(&P->dense_off, sizeof(int64_t) * (P->nblocks + 1)));
+        FKT_CUDA_TRY(cudaMalloc(&P->dense_ent, sizeof(int2) * P->nblocks));
+        dense_lists_kernel<<<(unsigned)((P->nblocks + 256) / 256), 256, 0, st>>>(P->nblocks, P->dense_off, P->dense_ent);
+        FKT_CUDA_TRY(cudaGetLastError());
+    }
     const int nrb = nrhs == 1 ? 1 : 8;
     const int groups = (nrhs + nrb - 1) / nrb;
     const int64_t N = P->N;
-    cudaStream_t st = P->stream;
+    const size_t rec_group = (size_t)N * rec_f4(P->d, nrb);
+    const unsigned pg = (unsigned)((N + 255) / 256);
     for (int g = 0; g < groups; ++g) {
         const int nr = std::min(nrb, nrhs - g * nrb);
         MvmArgs a = base_args(P);
-        a.ws = P->ws + (size_t)g * nrb * N;
-        a.y = y + (size_t)g * nrb * N;
-        a.nr = nr;
-        const float* wg = w + (size_t)g * nrb * N;
-        unsigned pg = (unsigned)((N + 255) / 256);
-        if (nrb == 1) permute_kernel<1><<<pg, 256, 0, st>>>(N, P->perm, wg, nr, const_cast<float*>(a.ws));
-        else permute_kernel<8><<<pg, 256, 0, st>>>(N, P->perm, wg, nr, const_cast<float*>(a.ws));
-        launch_dense(P->d, nrb, P->kernel.kind, (unsigned)((N + kTB - 1) / kTB), st, a, P->kp);
+        a.near_off = P->dense_off;
+        a.near_ent = P->dense_ent;
+        float4* rec = P->rec + (size_t)g * rec_group;
+        a.rec = rec;
+        a.ynear = P->ynear + (size_t)g * nrb * N;
+        launch_permute(P->d, nrb, pg, st, N, P->perm, P->xs, w + (size_t)g * nrb * N, nr, P->kp.sig, rec);
+        launch_near(P->d, nrb, P->near_tpt, P->kernel.kind, (unsigned)P->nblocks, st, a, P->kp);
+        unpermute_kernel<><<<pg, 256, 0, st>>>(N, nr, P->perm, a.ynear, y + (size_t)g * nrb * N);
         FKT_CUDA_TRY(cudaGetLastError());
     }
     return FKT_OK;
 }
-
-}  // namespace fkt
-
-// Entry points into the stage launchers above for other translation units.
-namespace fkt {
-
-int mvm_launch_s2m(int d, int p, int nrb, const FarLaunch& L) { return launch_s2m_any(d, p, nrb, L); }
-int mvm_launch_far(int d, int p, int nrb, const FarLaunch& L) { return launch_far_any(d, p, nrb, L); }
-void mvm_launch_near(int d, int nrb, int kind, unsigned grid, cudaStream_t st, const MvmArgs& a,
-                     const KernelParams& kp) {
-    launch_near(d, nrb, kind, grid, st, a, kp);
-}
-MvmArgs mvm_base_args(fkt_plan_s* P) { return base_args(P); }
 
 }  // namespace fkt

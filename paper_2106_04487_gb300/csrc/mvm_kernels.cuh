@@ -3,25 +3,44 @@
 //   s2m_kernel       per (node, <=1024-point chunk): partial multipoles (source2mult)
 //   s2m_reduce       per node: sum of its chunks' partials (deterministic order)
 //   near_kernel      per target block: dense K(near, leaf) * w[leaf] over the near leaves
+//                    (also the exact all-pairs product, with the root as the only "near leaf")
 //   far_kernel       per target block: m2t * multipole over the far nodes, plus the near
-//                    result, scattered back to the caller's order
-//   dense_kernel     exact all-pairs product (eq. nbody), for checks and baselines
+//                    result, scattered back to the caller's order (far_mr_kernel: 8 RHS)
 #pragma once
 
 #include "fkt_kernels.cuh"
+#include "ptx.cuh"
 
 namespace fkt {
 
-constexpr int kNearChunk = 256;   // sources staged per shared-memory pass
-
-template <int NR>
-__global__ void permute_kernel(int64_t N, const int32_t* __restrict__ perm, const float* __restrict__ w, int nr,
-                               float* __restrict__ ws) {
+// Source records for one pass: point (tree order) followed by this pass's weights.
+// Coordinates are stored multiplied by sigma = KernelParams::sig so that the near field works
+// with distances already in the kernel's own units (see kval).
+template <int D, int NR>
+__global__ void permute_kernel(int64_t N, const int32_t* __restrict__ perm, const float4* __restrict__ xs,
+                               const float* __restrict__ w, int nr, float sig, float4* __restrict__ rec) {
+    using R = Rec<D, NR>;
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= N) return;
-    int64_t j = perm[i];
+    const int64_t j = perm[i];
+    float v[R::F4 * 4];
+    const float4 x = xs[i];
+    v[0] = x.x * sig; v[1] = x.y * sig; v[2] = x.z * sig; v[3] = x.w * sig;
 #pragma unroll
-    for (int r = 0; r < NR; ++r) ws[r * N + i] = r < nr ? __ldg(&w[r * N + j]) : 0.0f;
+    for (int q = 4; q < R::F4 * 4; ++q) v[q] = 0.f;
+#pragma unroll
+    for (int r = 0; r < NR; ++r) v[R::WOFF + r] = r < nr ? __ldg(&w[r * N + j]) : 0.0f;
+#pragma unroll
+    for (int q = 0; q < R::F4; ++q) rec[i * R::F4 + q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+}
+
+template <int Unused = 0>
+__global__ void unpermute_kernel(int64_t N, int nr, const int32_t* __restrict__ perm, const float* __restrict__ ys,
+                                 float* __restrict__ y) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const int64_t o = perm[i];
+    for (int r = 0; r < nr; ++r) y[r * N + o] = ys[r * N + i];
 }
 
 // ------------------------------------------------------------------- s2m
@@ -75,7 +94,9 @@ s2m_kernel(MvmArgs a, const __grid_constant__ FarTables T) {
             for (int jj = 0; jj < Lay::nj(k); ++jj) tile[lane * ROW + o + jj] = Y * rp[jj];
         });
 #pragma unroll
-        for (int r = 0; r < NR; ++r) wt[lane * NR + r] = ok ? a.ws[(int64_t)r * a.N + s] : 0.f;
+        for (int r = 0; r < NR; ++r)
+            wt[lane * NR + r] = ok ? reinterpret_cast<const float*>(a.rec + (int64_t)s * Rec<D, NR>::F4)[Rec<D, NR>::WOFF + r]
+                                   : 0.f;
         __syncwarp();
 #pragma unroll 4
         for (int row = 0; row < 32; ++row) {
@@ -127,50 +148,178 @@ __global__ void s2m_reduce_kernel(int64_t nnodes, const int64_t* __restrict__ it
 }
 
 // ----------------------------------------------------------------- near
-template <int D, int KIND, int NR>
-__global__ void __launch_bounds__(kTB) near_kernel(MvmArgs a, KernelParams kp) {
-    __shared__ float4 sx[kNearChunk];
-    __shared__ float sw[NR][kNearChunk];
+// Kernel value without the scale factor (applied once per target at the end), with the
+// MUFU approximations ex2 / sqrt / rcp / rsqrt.approx.  q is the squared distance in the
+// kernel's own units, the coordinates having been multiplied by sigma (KernelParams::sig):
+//   Gaussian            sigma^2 = log2(e) / (2 l^2):  K = 2^(-q)
+//   exponential/Matern  sigma   = c log2(e):         u = sqrt(q) = c r log2(e), K = poly(u ln2) 2^(-u)
+//   Cauchy / RQ         sigma^2 = c1:                K = (1 + q)^(-alpha)
+//   Laplace             sigma   = 1:                 K = q^(-1/2), 0 at q = 0
+template <int KIND>
+__device__ __forceinline__ float kval(float q, const KernelParams& kp) {
+    constexpr float kLn2 = 0.69314718055994531f;
+    if (KIND == FKT_GAUSSIAN) {
+        return ptx::ex2(-q);
+    } else if (KIND == FKT_EXPONENTIAL) {
+        return ptx::ex2(-ptx::sqrt_approx(q));
+    } else if (KIND == FKT_MATERN32) {
+        const float u = ptx::sqrt_approx(q);
+        return fmaf(u, kLn2, 1.0f) * ptx::ex2(-u);
+    } else if (KIND == FKT_MATERN52) {
+        const float u = ptx::sqrt_approx(q);
+        const float t = u * kLn2;
+        return fmaf(t, fmaf(t, 1.0f / 3.0f, 1.0f), 1.0f) * ptx::ex2(-u);
+    } else if (KIND == FKT_CAUCHY) {
+        return ptx::rcp_approx(1.0f + q);
+    } else if (KIND == FKT_RATQUAD) {
+        const float b = 1.0f + q;
+        return kp.alpha == 1.0f ? ptx::rcp_approx(b) : ptx::ex2(-kp.alpha * ptx::lg2(b));
+    } else {
+        return q > 0.0f ? ptx::rsqrt_approx(q) : 0.0f;
+    }
+}
+
+constexpr long long kWaitCycles = 2000000000;  // ~1 s at 2 GHz: a wait this long is a fault
+
+// T targets per thread (128 / T threads per 128-target block); ST-stage ring of CH-point chunks.
+template <int D, int NR, int T>
+struct NearShape {
+    static constexpr int F4 = Rec<D, NR>::F4;
+    static constexpr int THREADS = kTB / T;
+    static constexpr int CH = F4 == 1 ? 256 : 128;
+    static constexpr int ST = T >= 4 ? 2 : 3;
+};
+
+// Near field of one target block: for each near entry (leaf, mask), every point of the leaf is
+// streamed through shared memory by the bulk-copy engine (3-stage mbarrier ring, issued by
+// thread 0) and each thread accumulates K(|x_t - x_s|) w_s for its two targets.
+template <int D, int KIND, int NR, int T>
+__global__ void __launch_bounds__(NearShape<D, NR, T>::THREADS) near_kernel(MvmArgs a, KernelParams kp) {
+    using R = Rec<D, NR>;
+    using Sh = NearShape<D, NR, T>;
+    constexpr int F4 = R::F4, CH = Sh::CH, ST = Sh::ST, NTH = Sh::THREADS;
+    __shared__ __align__(128) float4 buf[ST][CH * F4];
+    __shared__ __align__(8) uint64_t full[ST];
+    const int tl = threadIdx.x;
     const int64_t blk = blockIdx.x;
     const int2 rg = a.blk[blk];
-    const int tl = threadIdx.x;
-    const int t = rg.x + tl;
-    const bool valid = t < rg.y;
-    const float4 xt = valid ? a.xs[t] : make_float4(0.f, 0.f, 0.f, 0.f);
-    float acc[NR];
+    float tx[T][4];
+    bool valid[T];
 #pragma unroll
-    for (int r = 0; r < NR; ++r) acc[r] = 0.f;
+    for (int j = 0; j < T; ++j) {
+        const int t = rg.x + tl + NTH * j;
+        valid[j] = t < rg.y;
+        const float4 x = valid[j] ? a.xs[t] : make_float4(0.f, 0.f, 0.f, 0.f);
+        tx[j][0] = x.x * kp.sig; tx[j][1] = x.y * kp.sig; tx[j][2] = x.z * kp.sig; tx[j][3] = x.w * kp.sig;
+    }
+    float acc[T][NR];
+#pragma unroll
+    for (int j = 0; j < T; ++j)
+#pragma unroll
+        for (int r = 0; r < NR; ++r) acc[j][r] = 0.f;
     const int64_t e0 = a.near_off[blk], e1 = a.near_off[blk + 1];
-    for (int64_t e = e0; e < e1; ++e) {
-        const int2 ent = a.near_ent[e];
-        const bool active = valid && entry_active(ent.y, a.masks, tl);
-        const int s0 = a.nd_begin[ent.x], s1 = a.nd_end[ent.x];
-        for (int cb = s0; cb < s1; cb += kNearChunk) {
-            const int n = min(kNearChunk, s1 - cb);
-            __syncthreads();
-            for (int i = tl; i < n; i += kTB) {
-                sx[i] = a.xs[cb + i];
+    bool ok_all = true;
+    if (e0 < e1) {
+        if (tl == 0) {
 #pragma unroll
-                for (int r = 0; r < NR; ++r) sw[r][i] = a.ws[(int64_t)r * a.N + cb + i];
+            for (int s = 0; s < ST; ++s) ptx::mbar_init(&full[s], 1);
+            ptx::fence_mbar_init();
+        }
+        __syncthreads();
+        // producer cursor, used by thread 0 only
+        int64_t pe = e0;
+        int pcb = a.nd_begin[a.near_ent[e0].x];
+        int issued = 0;
+        auto issue = [&](int stage) {
+            while (pe < e1) {
+                const int s1 = a.nd_end[a.near_ent[pe].x];
+                if (pcb < s1) {
+                    const int n = min(CH, s1 - pcb);
+                    const uint32_t bytes = (uint32_t)n * F4 * 16u;
+                    ptx::mbar_arrive_expect_tx(&full[stage], bytes);
+                    ptx::bulk_g2s(&buf[stage][0], a.rec + (int64_t)pcb * F4, bytes, &full[stage]);
+                    pcb += n;
+                    ++issued;
+                    return;
+                }
+                if (++pe < e1) pcb = a.nd_begin[a.near_ent[pe].x];
             }
-            __syncthreads();
-            if (active) {
-#pragma unroll 4
-                for (int i = 0; i < n; ++i) {
-                    const float4 xs = sx[i];
-                    float dx = xt.x - xs.x, dy = xt.y - xs.y, dz = xt.z - xs.z;
-                    float r2 = dx * dx + dy * dy + dz * dz;
-                    if (D == 4) { float dw = xt.w - xs.w; r2 += dw * dw; }
-                    const float kv = kernel_r2<KIND>(r2, kp);
+        };
+        if (tl == 0)
+            for (int s = 0; s < ST; ++s) issue(s);
+        int k = 0;
+        for (int64_t e = e0; e < e1 && ok_all; ++e) {
+            const int2 ent = a.near_ent[e];
+            bool act[T];
 #pragma unroll
-                    for (int r = 0; r < NR; ++r) acc[r] = fmaf(kv, sw[r][i], acc[r]);
+            for (int j = 0; j < T; ++j) act[j] = valid[j] && entry_active(ent.y, a.masks, tl + NTH * j);
+            const int s0 = a.nd_begin[ent.x], s1 = a.nd_end[ent.x];
+            for (int cb = s0; cb < s1; cb += CH, ++k) {
+                const int n = min(CH, s1 - cb);
+                const int stage = k % ST;
+                const bool ok = ptx::mbar_wait_bounded(&full[stage], (uint32_t)((k / ST) & 1), kWaitCycles);
+                if (ok) {
+                    float ea[T][NR];
+#pragma unroll
+                    for (int j = 0; j < T; ++j)
+#pragma unroll
+                        for (int r = 0; r < NR; ++r) ea[j][r] = 0.f;
+                    const float4* sb = &buf[stage][0];
+#pragma unroll 4
+                    for (int i = 0; i < n; ++i) {
+                        const float4 sx = sb[i * F4];
+                        float kv[T];
+#pragma unroll
+                        for (int j = 0; j < T; ++j) {
+                            const float dx = tx[j][0] - sx.x, dy = tx[j][1] - sx.y, dz = tx[j][2] - sx.z;
+                            float q = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+                            if (D == 4) { const float dw = tx[j][3] - sx.w; q = fmaf(dw, dw, q); }
+                            kv[j] = kval<KIND>(q, kp);
+                        }
+                        if (D == 3 && NR == 1) {
+#pragma unroll
+                            for (int j = 0; j < T; ++j) ea[j][0] = fmaf(kv[j], sx.w, ea[j][0]);
+                        } else {
+                            const float* wv = reinterpret_cast<const float*>(sb + i * F4) + R::WOFF;
+#pragma unroll
+                            for (int r = 0; r < NR; ++r) {
+                                const float wr = wv[r];
+#pragma unroll
+                                for (int j = 0; j < T; ++j) ea[j][r] = fmaf(kv[j], wr, ea[j][r]);
+                            }
+                        }
+                    }
+#pragma unroll
+                    for (int j = 0; j < T; ++j)
+                        if (act[j])
+#pragma unroll
+                            for (int r = 0; r < NR; ++r) acc[j][r] += ea[j][r];
+                }
+                ok_all = __syncthreads_and(ok) != 0;  // every thread is done with this stage
+                if (!ok_all) break;
+                if (tl == 0) {
+                    ptx::fence_proxy_async_smem();
+                    issue(stage);
                 }
             }
         }
+        if (!ok_all) {
+            // A wait ran out: record it, let the copies still in flight land (bounded), stop.
+            if (tl == 0) {
+                atomicExch(a.err, 1);
+                for (int q = k; q < issued; ++q)  // chunk k (the one that timed out) onwards
+                    ptx::mbar_wait_bounded(&full[q % ST], (uint32_t)((q / ST) & 1), kWaitCycles);
+            }
+            return;
+        }
     }
-    if (valid)
 #pragma unroll
-        for (int r = 0; r < NR; ++r) a.ynear[(int64_t)r * a.N + t] = acc[r];
+    for (int j = 0; j < T; ++j) {
+        const int t = rg.x + tl + NTH * j;
+        if (valid[j])
+#pragma unroll
+            for (int r = 0; r < NR; ++r) a.ynear[(int64_t)r * a.N + t] = acc[j][r] * kp.scale;
+    }
 }
 
 // ------------------------------------------------------------------ far
@@ -357,44 +506,6 @@ __global__ void __launch_bounds__(kTB) far_mr_kernel(MvmArgs a, KernelParams kp,
 #pragma unroll
         for (int r = 0; r < 8; ++r)
             if (r < a.nr) a.y[(int64_t)r * a.N + o] = a.ynear[(int64_t)r * a.N + t] + acc[r];
-    }
-}
-
-// ---------------------------------------------------------------- dense
-template <int D, int KIND, int NR>
-__global__ void __launch_bounds__(kTB) dense_kernel(MvmArgs a, KernelParams kp) {
-    __shared__ float4 sx[kNearChunk];
-    __shared__ float sw[NR][kNearChunk];
-    const int t = blockIdx.x * kTB + threadIdx.x;
-    const bool valid = t < a.N;
-    const float4 xt = valid ? a.xs[t] : make_float4(0.f, 0.f, 0.f, 0.f);
-    float acc[NR];
-#pragma unroll
-    for (int r = 0; r < NR; ++r) acc[r] = 0.f;
-    for (int64_t cb = 0; cb < a.N; cb += kNearChunk) {
-        const int n = (int)min((int64_t)kNearChunk, a.N - cb);
-        __syncthreads();
-        for (int i = threadIdx.x; i < n; i += kTB) {
-            sx[i] = a.xs[cb + i];
-#pragma unroll
-            for (int r = 0; r < NR; ++r) sw[r][i] = a.ws[(int64_t)r * a.N + cb + i];
-        }
-        __syncthreads();
-        for (int i = 0; i < n; ++i) {
-            const float4 xs = sx[i];
-            float dx = xt.x - xs.x, dy = xt.y - xs.y, dz = xt.z - xs.z;
-            float r2 = dx * dx + dy * dy + dz * dz;
-            if (D == 4) { float dw = xt.w - xs.w; r2 += dw * dw; }
-            const float kv = kernel_r2<KIND>(r2, kp);
-#pragma unroll
-            for (int r = 0; r < NR; ++r) acc[r] = fmaf(kv, sw[r][i], acc[r]);
-        }
-    }
-    if (valid) {
-        const int64_t o = a.perm[t];
-#pragma unroll
-        for (int r = 0; r < NR; ++r)
-            if (r < a.nr) a.y[(int64_t)r * a.N + o] = acc[r];
     }
 }
 

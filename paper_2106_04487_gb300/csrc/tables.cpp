@@ -212,13 +212,18 @@ KernelParams make_kernel_params(const fkt_kernel& k) {
     p.alpha = (float)k.alpha;
     p.scale = (float)k.scale;
     double l = k.lengthscale;
+    p.sig = 1.0f;
     switch (k.kind) {
-    case FKT_GAUSSIAN: p.c1 = (float)(1.0 / (2.0 * l * l)); break;
-    case FKT_EXPONENTIAL: p.c1 = (float)(1.0 / l); break;
-    case FKT_MATERN32: p.c1 = (float)(sqrt(3.0) / l); break;
-    case FKT_MATERN52: p.c1 = (float)(sqrt(5.0) / l); break;
-    case FKT_CAUCHY: p.c1 = (float)(1.0 / (l * l)); break;
-    case FKT_RATQUAD: p.c1 = (float)(1.0 / (2.0 * k.alpha * l * l)); break;
+    case FKT_GAUSSIAN:
+        p.c1 = (float)(1.0 / (2.0 * l * l));
+        p.c2 = (float)(M_LOG2E / (2.0 * l * l));
+        p.sig = (float)sqrt(M_LOG2E / (2.0 * l * l));
+        break;
+    case FKT_EXPONENTIAL: p.c1 = (float)(1.0 / l); p.c2 = (float)(M_LOG2E / l); p.sig = p.c2; break;
+    case FKT_MATERN32: p.c1 = (float)(sqrt(3.0) / l); p.c2 = (float)(M_LOG2E * sqrt(3.0) / l); p.sig = p.c2; break;
+    case FKT_MATERN52: p.c1 = (float)(sqrt(5.0) / l); p.c2 = (float)(M_LOG2E * sqrt(5.0) / l); p.sig = p.c2; break;
+    case FKT_CAUCHY: p.c1 = (float)(1.0 / (l * l)); p.sig = (float)(1.0 / l); break;
+    case FKT_RATQUAD: p.c1 = (float)(1.0 / (2.0 * k.alpha * l * l)); p.sig = (float)sqrt(p.c1); break;
     default: break;
     }
     return p;

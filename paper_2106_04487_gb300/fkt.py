@@ -23,7 +23,8 @@ KERNELS = {"gaussian": 0, "exponential": 1, "matern32": 2, "matern52": 3, "cauch
 
 # Every entry point declared in include/fkt.h.
 EXPORTS = ["fkt_plan", "fkt_mvm", "fkt_mvm_host", "fkt_dense_mvm", "fkt_set_option", "fkt_plan_stats",
-           "fkt_plan_tree", "fkt_plan_lists", "fkt_destroy", "fkt_error_string", "fkt_mvm_noalloc"]
+           "fkt_plan_tree", "fkt_plan_lists", "fkt_destroy", "fkt_error_string", "fkt_mvm_noalloc",
+           "fkt_check"]
 
 
 class FktError(RuntimeError):
@@ -69,6 +70,7 @@ def lib() -> ctypes.CDLL:
     L.fkt_plan_stats.argtypes = [vp, ctypes.POINTER(fkt_stats)]
     L.fkt_plan_tree.argtypes = [vp] + [vp] * 8
     L.fkt_plan_lists.argtypes = [vp] + [vp] * 8
+    L.fkt_check.argtypes = [vp]
     L.fkt_destroy.argtypes = [vp]
     L.fkt_destroy.restype = None
     L.fkt_error_string.argtypes = [ctypes.c_int]
@@ -141,6 +143,11 @@ def fkt_plan_stats(plan) -> dict:
     return {k: getattr(s, k) for k, _ in fkt_stats._fields_}
 
 
+def fkt_check(plan):
+    """Raise FktError(FKT_ERR_TIMEOUT) if a bounded device-side wait ran out since the last check."""
+    _check(lib().fkt_check(plan), "fkt_check")
+
+
 def fkt_destroy(plan):
     lib().fkt_destroy(plan)
 
@@ -210,6 +217,9 @@ class Plan:
 
     def stats(self) -> dict:
         return fkt_plan_stats(self.h)
+
+    def check(self):
+        fkt_check(self.h)
 
     def tree(self) -> dict:
         s = self.stats()

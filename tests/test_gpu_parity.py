@@ -109,6 +109,19 @@ def test_kernels_d3(fkt, orc, kernel, ell, alpha, scale):
     assert _rel(y, z) < TOL
 
 
+@pytest.mark.parametrize("kernel,ell", [("matern32", 0.2), ("gaussian", 0.1), ("laplace", 1.0), ("cauchy", 0.05)])
+@pytest.mark.parametrize("d", [3, 4])
+def test_near_four_targets_per_thread(fkt, orc, kernel, ell, d):
+    """The register-blocked near-field variant (4 targets per thread) against the oracle."""
+    X = inputs.gaussian_mixture(9000, d, 6, 0.07, seed=25)
+    w = inputs.normal_weights(9000, 1, seed=26)
+    plan = _plan(fkt, X, kernel, ell, 4, 128, 0.5)
+    plan.set_option("near_targets_per_thread", "4")
+    y = _gpu_mvm(plan, w)
+    z = _oracle(orc, X, kernel, ell, 4, 128, 0.5).mvm(w)
+    assert _rel(y, z) < TOL
+
+
 @pytest.mark.parametrize("p", [0, 1, 2, 3, 6, 7, 8, 9, 10])
 def test_orders_d3(fkt, orc, p):
     X = inputs.unit_ball(7000, 3, seed=6)
