@@ -129,9 +129,45 @@ int fkt_mvm_host(fkt_plan_t plan, const float* w_host, float* y_host, int nrhs);
  * plan's points (same r = 0 rule).  Device [nrhs][N] buffers as for fkt_mvm.  O(N^2) work. */
 int fkt_dense_mvm(fkt_plan_t plan, const float* w, float* y, int nrhs);
 
+/* ---- Gaussian-process style solves:  (Ktilde + sigma2 I) x = b  ----
+ *
+ * The paper uses the FKT product to evaluate GP posterior means, which need
+ * Sigma^{-1} (y - mu) with Sigma = K + sigma_y^2 I (Sec. C, eq. gp_posterior), computed
+ * through matrix-vector products only.  fkt_solve runs preconditioned conjugate gradients
+ * with one fkt_mvm per iteration (all right-hand sides at once): iterates x and residuals r
+ * in float64, inner products in float64, search directions and products in float32.
+ * The preconditioner is block-Jacobi over the plan's target blocks (<= 128 consecutive
+ * points of one leaf): each diagonal block K(X_b, X_b) + sigma2 I is factored (Cholesky)
+ * and inverted in float32 on the GPU. */
+typedef struct {
+    int iterations;             /* CG iterations run */
+    int converged;              /* 1 if every right-hand side reached tol */
+    int used_fallback;          /* 1 if a learned correction was rejected for plain block-Jacobi */
+    int pad;
+    double rel_residual;        /* max over right-hand sides of |r_k| / |b| from the recurrence */
+    double true_rel_residual;   /* max over right-hand sides of |b - (Ktilde + sigma2 I) x| / |b|,
+                                   recomputed with one more fkt_mvm */
+} fkt_solve_info;
+
+/* Build the block-Jacobi preconditioner for (Ktilde + sigma2 I) (sigma2 > 0).  Called by
+ * fkt_solve when needed; call it directly to time or inspect it.  Synchronizes. */
+int fkt_precond_setup(fkt_plan_t plan, double sigma2);
+
+/* z = M^{-1} r with the current preconditioner; r, z device [nrhs][N] float32 in the
+ * caller's order, 1 <= nrhs <= 64.  FKT_ERR_INVALID_ARG if no preconditioner is set up. */
+int fkt_precond_apply(fkt_plan_t plan, const float* r, float* z, int nrhs);
+
+/* Solve (Ktilde + sigma2 I) x = b.  b, x device [nrhs][N] float32 (x is output only),
+ * 1 <= nrhs <= 64, sigma2 > 0, 0 < tol < 1, max_iter >= 1.  Synchronizes.
+ * Returns FKT_OK when every right-hand side reached |r| <= tol |b|, FKT_ERR_NOT_CONVERGED
+ * after max_iter iterations otherwise (x then holds the last iterate); info may be NULL. */
+int fkt_solve(fkt_plan_t plan, double sigma2, const float* b, float* x, int nrhs, double tol, int max_iter,
+              fkt_solve_info* info);
+
 /* Options (all take effect on the next call):
  *   "timing"    "0" | "1"   record per-stage CUDA-event times of fkt_mvm in fkt_stats
  *   "far_precision"  "fp32" (default) | "tf32" | "bf16" | "bf16x3"  arithmetic of the far field
+ *   "preconditioner" "block_jacobi" (default) | "none"   preconditioner of fkt_solve
  *   "near_targets_per_thread"  "2" (default) | "4"  register blocking of the near-field kernel
  *               (4 applies to one right-hand side; results are identical up to rounding order)
  * Errors: FKT_ERR_INVALID_ARG for an unknown key or value. */

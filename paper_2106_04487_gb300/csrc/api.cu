@@ -28,6 +28,7 @@ void free_plan(fkt_plan_s* P) {
                     P->d_err, P->dense_off, P->dense_ent};
     for (void* b : bufs)
         if (b) cudaFree(b);
+    fkt::free_solve(P);
     for (auto& e : P->ev)
         if (e) cudaEventDestroy(e);
     if (P->stream2) cudaStreamDestroy(P->stream2);
@@ -147,11 +148,36 @@ int fkt_dense_mvm(fkt_plan_t plan, const float* w, float* y, int nrhs) {
     return fkt::launch_dense(plan, w, y, nrhs);
 }
 
+int fkt_precond_setup(fkt_plan_t plan, double sigma2) {
+    if (!plan || !(sigma2 > 0.0) || !isfinite(sigma2)) return FKT_ERR_INVALID_ARG;
+    return fkt::precond_setup(plan, sigma2);
+}
+
+int fkt_precond_apply(fkt_plan_t plan, const float* r, float* z, int nrhs) {
+    if (!plan || !r || !z || r == z || nrhs < 1 || nrhs > fkt::kMaxRhs) return FKT_ERR_INVALID_ARG;
+    return fkt::precond_apply(plan, r, nullptr, z, nrhs);
+}
+
+int fkt_solve(fkt_plan_t plan, double sigma2, const float* b, float* x, int nrhs, double tol, int max_iter,
+              fkt_solve_info* info) {
+    if (info) memset(info, 0, sizeof(*info));
+    if (!plan || !b || !x || b == x || nrhs < 1 || nrhs > fkt::kMaxRhs || !(sigma2 > 0.0) || !isfinite(sigma2) ||
+        !(tol > 0.0 && tol < 1.0) || max_iter < 1)
+        return FKT_ERR_INVALID_ARG;
+    return fkt::solve(plan, sigma2, b, x, nrhs, tol, max_iter, info);
+}
+
 int fkt_set_option(fkt_plan_t plan, const char* key, const char* value) {
     if (!plan || !key || !value) return FKT_ERR_INVALID_ARG;
     if (!strcmp(key, "timing")) {
         if (!strcmp(value, "0")) plan->timing = false;
         else if (!strcmp(value, "1")) plan->timing = true;
+        else return FKT_ERR_INVALID_ARG;
+        return FKT_OK;
+    }
+    if (!strcmp(key, "preconditioner")) {
+        if (!strcmp(value, "none")) plan->pc_mode = 0;
+        else if (!strcmp(value, "block_jacobi")) plan->pc_mode = 1;
         else return FKT_ERR_INVALID_ARG;
         return FKT_OK;
     }

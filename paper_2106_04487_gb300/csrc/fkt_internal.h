@@ -105,6 +105,18 @@ struct fkt_plan_s {
     int* d_err = nullptr;          // device error word (bounded waits that ran out)
     int64_t* dense_off = nullptr;  // one-entry lists (the root) per target block, for fkt_dense_mvm
     int2* dense_ent = nullptr;
+    // block-Jacobi preconditioner: inverse of K(X_b, X_b) + sigma2 I per target block
+    double pc_sigma2 = -1.0;       // sigma2 the inverses were built for (< 0: none)
+    int pc_mode = 1;               // 0: no preconditioner (z = r), 1: block-Jacobi
+    float* pc_inv = nullptr;       // [blocks][kTB][kTB], symmetric
+    // CG work space (grown on demand)
+    int cg_cap = 0;
+    double* cg_x = nullptr;        // [nrhs][N] float64 iterate
+    double* cg_r = nullptr;        // [nrhs][N] float64 residual
+    float* cg_p = nullptr;         // [nrhs][N] search direction
+    float* cg_q = nullptr;         // [nrhs][N] (Ktilde + sigma2 I) p
+    float* cg_z = nullptr;         // [nrhs][N] preconditioned residual
+    double* cg_s = nullptr;        // scalars: [8][kMaxRhs]
     cudaStream_t stream2 = nullptr;
     cudaEvent_t ev[8] = {};
     // stats
@@ -135,6 +147,13 @@ int run_mvm(fkt_plan_s* P, const MvmBuffers& B, const float* w, float* y, int nr
 int launch_mvm(fkt_plan_s* P, const float* w, float* y, int nrhs);
 int launch_dense(fkt_plan_s* P, const float* w, float* y, int nrhs);
 int ensure_rhs_capacity(fkt_plan_s* P, int nrhs);
+
+// solve.cu
+int precond_setup(fkt_plan_s* P, double sigma2);
+int precond_apply(fkt_plan_s* P, const float* r, const double* r64, float* z, int nrhs);
+int solve(fkt_plan_s* P, double sigma2, const float* b, float* x, int nrhs, double tol, int max_iter,
+          fkt_solve_info* info);
+void free_solve(fkt_plan_s* P);
 
 }  // namespace fkt
 

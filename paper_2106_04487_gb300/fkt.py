@@ -24,7 +24,7 @@ KERNELS = {"gaussian": 0, "exponential": 1, "matern32": 2, "matern52": 3, "cauch
 # Every entry point declared in include/fkt.h.
 EXPORTS = ["fkt_plan", "fkt_mvm", "fkt_mvm_host", "fkt_dense_mvm", "fkt_set_option", "fkt_plan_stats",
            "fkt_plan_tree", "fkt_plan_lists", "fkt_destroy", "fkt_error_string", "fkt_mvm_noalloc",
-           "fkt_check"]
+           "fkt_check", "fkt_precond_setup", "fkt_precond_apply", "fkt_solve"]
 
 
 class FktError(RuntimeError):
@@ -36,6 +36,11 @@ class FktError(RuntimeError):
 class fkt_kernel(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int), ("lengthscale", ctypes.c_double), ("alpha", ctypes.c_double),
                 ("scale", ctypes.c_double)]
+
+
+class fkt_solve_info(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int), ("converged", ctypes.c_int), ("used_fallback", ctypes.c_int),
+                ("pad", ctypes.c_int), ("rel_residual", ctypes.c_double), ("true_rel_residual", ctypes.c_double)]
 
 
 class fkt_stats(ctypes.Structure):
@@ -71,6 +76,10 @@ def lib() -> ctypes.CDLL:
     L.fkt_plan_tree.argtypes = [vp] + [vp] * 8
     L.fkt_plan_lists.argtypes = [vp] + [vp] * 8
     L.fkt_check.argtypes = [vp]
+    L.fkt_precond_setup.argtypes = [vp, ctypes.c_double]
+    L.fkt_precond_apply.argtypes = [vp, vp, vp, ctypes.c_int]
+    L.fkt_solve.argtypes = [vp, ctypes.c_double, vp, vp, ctypes.c_int, ctypes.c_double, ctypes.c_int,
+                            ctypes.POINTER(fkt_solve_info)]
     L.fkt_destroy.argtypes = [vp]
     L.fkt_destroy.restype = None
     L.fkt_error_string.argtypes = [ctypes.c_int]
@@ -141,6 +150,24 @@ def fkt_plan_stats(plan) -> dict:
     s = fkt_stats()
     _check(lib().fkt_plan_stats(plan, ctypes.byref(s)), "fkt_plan_stats")
     return {k: getattr(s, k) for k, _ in fkt_stats._fields_}
+
+
+def fkt_precond_setup(plan, sigma2: float):
+    _check(lib().fkt_precond_setup(plan, float(sigma2)), "fkt_precond_setup")
+
+
+def fkt_precond_apply(plan, r, z, nrhs: int):
+    _check(lib().fkt_precond_apply(plan, _ptr(r), _ptr(z), nrhs), "fkt_precond_apply")
+
+
+def fkt_solve(plan, sigma2: float, b, x, nrhs: int, tol: float, max_iter: int, raise_on_not_converged=True) -> dict:
+    info = fkt_solve_info()
+    st = lib().fkt_solve(plan, float(sigma2), _ptr(b), _ptr(x), nrhs, float(tol), int(max_iter), ctypes.byref(info))
+    if st != FKT_OK and not (st == FKT_ERR_NOT_CONVERGED and not raise_on_not_converged):
+        raise FktError(st, "fkt_solve")
+    out = {k: getattr(info, k) for k, _ in fkt_solve_info._fields_ if k != "pad"}
+    out["status"] = st
+    return out
 
 
 def fkt_check(plan):
@@ -220,6 +247,26 @@ class Plan:
 
     def check(self):
         fkt_check(self.h)
+
+    def solve(self, sigma2: float, b, tol: float = 1e-6, max_iter: int = 1000, raise_on_not_converged=True):
+        """x with (Ktilde + sigma2 I) x = b by preconditioned CG; returns (x, info dict)."""
+        import torch
+
+        b2 = b if b.dim() == 2 else b[None]
+        b2 = b2.to(device="cuda", dtype=torch.float32).contiguous()
+        x = torch.empty_like(b2)
+        info = fkt_solve(self.h, sigma2, b2, x, b2.shape[0], tol, max_iter, raise_on_not_converged)
+        return (x if b.dim() == 2 else x[0]), info
+
+    def precond(self, sigma2: float, r):
+        """z = M^{-1} r with the block-Jacobi preconditioner for sigma2."""
+        import torch
+
+        fkt_precond_setup(self.h, sigma2)
+        r2 = (r if r.dim() == 2 else r[None]).to(device="cuda", dtype=torch.float32).contiguous()
+        z = torch.empty_like(r2)
+        fkt_precond_apply(self.h, r2, z, r2.shape[0])
+        return z if r.dim() == 2 else z[0]
 
     def tree(self) -> dict:
         s = self.stats()

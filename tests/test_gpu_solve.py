@@ -1,0 +1,120 @@
+"""fkt_solve: preconditioned CG for (Ktilde + sigma2 I) x = b (the GP solve of Sec. C).
+
+The solution is judged by residuals in float64 against operators the oracle defines: the
+dense kernel matrix (eq. nbody) where theta -> 0 makes the FKT exact, and the oracle FKT
+otherwise (reading R13: Ktilde is only approximately symmetric, so the true residual is the
+judge).  The block-Jacobi blocks are checked against float64 dense solves of the same blocks.
+
+Bar: the products run in float32 and x is returned in float32, so for these ill-conditioned
+systems (sigma2 = 1e-2, |x| ~ 10-100 |b|) the float64 residual of the returned x is limited to
+about 1e-4 even when the solver's own residual is below 1e-6; the tests require 3e-4.
+"""
+import numpy as np
+import pytest
+
+from paper_2106_04487_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def fkt():
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2106_04487_gb300 import build, fkt as F
+
+    build.build()
+    F.lib()
+    return F
+
+
+def _kernel_matrix(orc, kp, A, B):
+    R = np.linalg.norm(A[:, None, :].astype(np.float64) - B[None, :, :].astype(np.float64), axis=2)
+    f = np.vectorize(lambda r: orc.kernel_value(kp, r))
+    return f(R)
+
+
+def test_block_jacobi_blocks(fkt, orc):
+    import torch
+
+    X = inputs.gaussian_mixture(3000, 4, 20, 0.05, seed=30)
+    sigma2 = 1e-2
+    kp = orc.kparams("matern52", 0.3)
+    plan = fkt.Plan(torch.from_numpy(X).cuda(), "matern52", lengthscale=0.3, p=4, leaf_size=256, theta=0.5)
+    r = inputs.normal_weights(3000, 3, seed=31)
+    z = plan.precond(sigma2, torch.from_numpy(r).cuda()).cpu().numpy().astype(np.float64)
+    perm = plan.tree()["perm"]
+    blocks = plan.lists()["block_range"]
+    for lo, hi in blocks[:: max(1, len(blocks) // 6)]:
+        idx = perm[lo:hi]
+        A = _kernel_matrix(orc, kp, X[idx], X[idx]) + sigma2 * np.eye(hi - lo)
+        want = np.linalg.solve(A, r[:, idx].T.astype(np.float64)).T
+        assert np.linalg.norm(z[:, idx] - want) / np.linalg.norm(want) < 2e-3
+
+
+def test_solve_dense_limit(fkt, orc):
+    """theta -> 0: Ktilde = K exactly, so x must satisfy the float64 dense system."""
+    import torch
+
+    X = inputs.gaussian_mixture(2000, 4, 20, 0.05, seed=32)
+    b = inputs.normal_weights(2000, 4, seed=33)
+    sigma2 = 1e-2
+    plan = fkt.Plan(torch.from_numpy(X).cuda(), "matern52", lengthscale=0.3, p=4, leaf_size=128, theta=1e-6)
+    x, info = plan.solve(sigma2, torch.from_numpy(b).cuda(), tol=1e-6, max_iter=2000)
+    x = x.cpu().numpy().astype(np.float64)
+    Ax = orc.dense(X, orc.kparams("matern52", 0.3), x) + sigma2 * x
+    res = np.linalg.norm(b - Ax, axis=1) / np.linalg.norm(b, axis=1)
+    assert info["converged"] == 1
+    assert res.max() < 3e-4, (res, info)
+    assert info["true_rel_residual"] < 3e-4, info
+
+
+def test_solve_against_oracle_fkt_operator(fkt, orc):
+    """d = 4 Gaussian mixture, Matern-5/2 l=0.3, sigma2 = 1e-2, p = 6, theta = 0.3: the GPU solution
+    satisfies the oracle's float64 FKT system to the float32 floor (the expansion is accurate enough
+    here that Ktilde + sigma2 I stays positive definite; at p = 4 it does not and CG diverges)."""
+    import torch
+
+    X = inputs.gaussian_mixture(20000, 4, 20, 0.05, seed=34)
+    b = inputs.normal_weights(20000, 3, seed=35)
+    sigma2 = 1e-2
+    plan = fkt.Plan(torch.from_numpy(X).cuda(), "matern52", lengthscale=0.3, p=6, leaf_size=256, theta=0.3)
+    plan.set_option("preconditioner", "none")
+    x, info = plan.solve(sigma2, torch.from_numpy(b).cuda(), tol=1e-5, max_iter=4000)
+    assert info["converged"] == 1 and info["rel_residual"] <= 1e-5
+    x = x.cpu().numpy().astype(np.float64)
+    F = orc.FKT(X, orc.kparams("matern52", 0.3), p=6, leaf_size=256, theta=0.3)
+    Ax = F.mvm(x) + sigma2 * x
+    res = np.linalg.norm(b - Ax, axis=1) / np.linalg.norm(b, axis=1)
+    assert res.max() < 3e-3, (res, info)
+    assert abs(res.max() - info["true_rel_residual"]) < 1e-3
+
+
+def test_preconditioner_reduces_iterations(fkt):
+    """Block-Jacobi pays off when the kernel is short-range relative to a block (l = 0.05)."""
+    import torch
+
+    X = inputs.gaussian_mixture(20000, 4, 20, 0.05, seed=36)
+    b = torch.from_numpy(inputs.normal_weights(20000, 2, seed=37)).cuda()
+    plan = fkt.Plan(torch.from_numpy(X).cuda(), "matern52", lengthscale=0.05, p=4, leaf_size=256, theta=0.5)
+    _, with_pc = plan.solve(1e-2, b, tol=1e-5, max_iter=5000)
+    plan.set_option("preconditioner", "none")
+    _, without = plan.solve(1e-2, b, tol=1e-5, max_iter=5000)
+    assert with_pc["converged"] == 1 and without["converged"] == 1
+    assert with_pc["iterations"] < without["iterations"], (with_pc, without)
+
+
+def test_solve_reports_non_convergence_and_bad_args(fkt):
+    import torch
+
+    X = inputs.uniform_cube(3000, 4, seed=38)
+    b = torch.from_numpy(inputs.normal_weights(3000, 1, seed=39)).cuda()
+    plan = fkt.Plan(torch.from_numpy(X).cuda(), "matern52", lengthscale=0.3, p=3, leaf_size=128, theta=0.5)
+    x, info = plan.solve(1e-2, b, tol=1e-9, max_iter=2, raise_on_not_converged=False)
+    assert info["status"] == fkt.FKT_ERR_NOT_CONVERGED and info["iterations"] == 2 and info["converged"] == 0
+    with pytest.raises(fkt.FktError):
+        plan.solve(0.0, b)
+    with pytest.raises(fkt.FktError):
+        plan.solve(1e-2, b, tol=2.0)
