@@ -30,9 +30,16 @@ sys.path.insert(0, ROOT)
 from paper_2106_04487_gb300 import inputs  # noqa: E402
 
 KERNELS = {"matern32": ("matern32", 0.2), "cauchy": ("cauchy", 0.05)}
-# Launches of the library's own kernels per MVM with one right-hand side:
-# permute, s2m, s2m_reduce, near field, far field (+ combine).
-LAUNCHES_PER_MVM_1RHS = 5
+def launches_per_step(nrhs: int, far_precision: str) -> int:
+    """Kernels the library launches per fkt_mvm: per group of right-hand sides (1 or 8) permute, s2m,
+    s2m_reduce and near field; the float32 far field once per group, the tensor-core far field
+    (pack + far) once per pass of 32."""
+    if far_precision == "fp32":
+        groups = 1 if nrhs == 1 else (nrhs + 7) // 8
+        return 5 * groups
+    groups = (nrhs + 7) // 8
+    passes = (nrhs + 31) // 32
+    return 4 * groups + 2 * passes
 
 
 def parse():
@@ -47,6 +54,7 @@ def parse():
     ap.add_argument("--leaf", type=int, default=256)
     ap.add_argument("--nrhs", type=int, default=1)
     ap.add_argument("--near-tpt", type=int, default=2, choices=[2, 4])
+    ap.add_argument("--far-precision", default="fp32", choices=["fp32", "bf16x3", "tf32", "bf16"])
     ap.add_argument("--n", type=int, default=1_000_000)
     ap.add_argument("--err-targets", type=int, default=1000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -56,7 +64,7 @@ def parse():
 def workload_name(a):
     k, ell = KERNELS[a.kernel]
     return (f"{k} l={ell} d=3 N={a.n} gaussian-mixture(10 comps, std 0.05) p={a.p} leaf={a.leaf} "
-            f"theta={a.theta} nrhs={a.nrhs} near_tpt={a.near_tpt}")
+            f"theta={a.theta} nrhs={a.nrhs} near_tpt={a.near_tpt} far={a.far_precision}")
 
 
 def load_peaks():
@@ -154,6 +162,7 @@ def run_ours(a):
     plan = fkt.Plan(Xd, kname, lengthscale=ell, p=a.p, leaf_size=a.leaf, theta=a.theta)
     plan.set_option("timing", "1")
     plan.set_option("near_targets_per_thread", str(a.near_tpt))
+    plan.set_option("far_precision", a.far_precision)
     stats = plan.stats()
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     stream = torch.cuda.current_stream()
@@ -256,7 +265,7 @@ def run_ours(a):
                                     f"SM-clocks per pair ({src} clock)"},
         "e2e": {"value": e2e_value, "unit": "MVM/s", "h2d_bytes_per_step": int(W.nbytes),
                 "d2h_bytes_per_step": int(W.nbytes)},
-        "gpu_launches": LAUNCHES_PER_MVM_1RHS * a.steps * ((a.nrhs + 7) // 8 if a.nrhs > 1 else 1),
+        "gpu_launches": launches_per_step(a.nrhs, a.far_precision) * a.steps,
         "clocks": clocks,
     }
     if rank == 0 and not a.no_cpu_baseline:

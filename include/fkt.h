@@ -166,7 +166,11 @@ int fkt_solve(fkt_plan_t plan, double sigma2, const float* b, float* x, int nrhs
 
 /* Options (all take effect on the next call):
  *   "timing"    "0" | "1"   record per-stage CUDA-event times of fkt_mvm in fkt_stats
- *   "far_precision"  "fp32" (default) | "tf32" | "bf16" | "bf16x3"  arithmetic of the far field
+ *   "far_precision"  "fp32" (default) | "tf32" | "bf16" | "bf16x3"  arithmetic of the far-field
+ *               contraction: fp32 on CUDA cores; otherwise on the tensor cores (tcgen05.mma,
+ *               float32 accumulation in tensor memory) with operands in TF32, BF16, or BF16
+ *               split into hi + lo parts (three products, about 16 significant bits); the
+ *               near field always stays float32.  Right-hand sides go 32 per pass.
  *   "preconditioner" "block_jacobi" (default) | "none"   preconditioner of fkt_solve
  *   "near_targets_per_thread"  "2" (default) | "4"  register blocking of the near-field kernel
  *               (4 applies to one right-hand side; results are identical up to rounding order)

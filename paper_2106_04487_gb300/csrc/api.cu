@@ -24,7 +24,7 @@ void free_plan(fkt_plan_s* P) {
     void* bufs[] = {P->xs, P->perm, P->codes, P->nd_begin, P->nd_end, P->nd_level, P->nd_leaf, P->nd_child,
                     P->nd_centre, P->nd_rho2, P->nd_cf, P->nd_scale, P->nd_used, P->blk_range, P->far_off,
                     P->near_off, P->far_ent, P->near_ent, P->masks, P->s2m_items, P->s2m_node_items,
-                    P->s2m_item_off, P->rec, P->ynear, P->mult, P->s2m_part, P->hbuf_w, P->hbuf_y,
+                    P->s2m_item_off, P->rec, P->ynear, P->mult, P->s2m_part, P->tc_image, P->hbuf_w, P->hbuf_y,
                     P->d_err, P->dense_off, P->dense_ent};
     for (void* b : bufs)
         if (b) cudaFree(b);
@@ -189,8 +189,10 @@ int fkt_set_option(fkt_plan_t plan, const char* key, const char* value) {
     }
     if (!strcmp(key, "far_precision")) {
         if (!strcmp(value, "fp32")) plan->far_precision = fkt::FAR_FP32;
-        else return !strcmp(value, "tf32") || !strcmp(value, "bf16") || !strcmp(value, "bf16x3") ? FKT_ERR_UNSUPPORTED
-                                                                                                   : FKT_ERR_INVALID_ARG;
+        else if (!strcmp(value, "tf32")) plan->far_precision = fkt::FAR_TF32;
+        else if (!strcmp(value, "bf16")) plan->far_precision = fkt::FAR_BF16;
+        else if (!strcmp(value, "bf16x3")) plan->far_precision = fkt::FAR_BF16X3;
+        else return FKT_ERR_INVALID_ARG;
         return FKT_OK;
     }
     return FKT_ERR_INVALID_ARG;

@@ -1,0 +1,304 @@
+// Far field on the 5th-generation tensor cores (the precision form of the far field).
+//
+// For one block of 128 targets the far field is a product accumulated over its far nodes b:
+//     z[t][r] += sum_q U_b[t][q] M_b[q][r],   U_b[t][q] = Yt_kh(x_t - c_b) (s/r)^j R_kj(r)
+// (the same basis as far_kernel).  CUDA cores generate the 128 x NTP basis tile U_b into shared
+// memory, converted to BF16 (or split into BF16 hi + lo, or TF32); the node's multipoles, packed
+// beforehand into the tensor-core operand image, arrive by a bulk copy; one thread issues
+// tcgen05.mma (M = 128 targets, N = 32 right-hand sides, K = 16 terms per instruction) into a
+// float32 accumulator in tensor memory, which the epilogue reads back with tcgen05.ld.
+//
+// Operand layout (both K-major, no swizzle): core matrices of 8 rows x 16 bytes stored
+// contiguously; the core matrices of one 8-row group follow each other along K (128 bytes
+// apart, the leading-dimension offset), and 8-row groups are SBO = (NTP * elem / 16) * 128 bytes
+// apart (the stride-dimension offset).
+#pragma once
+
+#include <cuda_bf16.h>
+
+#include "mvm_kernels.cuh"
+
+namespace fkt {
+
+enum TcPrec { TC_BF16 = 0, TC_BF16X3 = 1, TC_TF32 = 2 };
+
+constexpr int kTcN = 32;  // right-hand-side columns per pass
+
+template <int D, int P, int PREC>
+struct TcShape {
+    static constexpr int NT = Layout<D, P>::nterms;
+    static constexpr int NTP = (NT + 15) / 16 * 16;                 // K padded to whole MMA steps
+    static constexpr int EL = PREC == TC_TF32 ? 4 : 2;              // bytes per operand element
+    static constexpr int PER16 = 16 / EL;                           // elements per 16-byte core row
+    static constexpr int SBO_A = NTP / PER16 * 128;                 // bytes between 8-row groups
+    static constexpr int PLANES = PREC == TC_BF16X3 ? 2 : 1;        // hi (+ lo)
+    static constexpr int A_BYTES = 128 * NTP * EL * PLANES;
+    static constexpr int B_BYTES = kTcN * NTP * EL * PLANES;
+    static constexpr int STAGES = (2 * (A_BYTES + B_BYTES) <= 112 * 1024) ? 2 : 1;
+    static constexpr size_t smem_bytes() { return (size_t)STAGES * (A_BYTES + B_BYTES) + 128; }
+    static constexpr bool supported = smem_bytes() <= 200 * 1024;
+    // byte offset of element (row, k) of one plane
+    __host__ __device__ static constexpr int off(int row, int k) {
+        return (row / 8) * SBO_A + (k / PER16) * 128 + (row % 8) * 16 + (k % PER16) * EL;
+    }
+};
+
+template <int PREC>
+__device__ __forceinline__ void tc_store(unsigned char* plane0, int plane_bytes, int off, float v) {
+    if (PREC == TC_TF32) {
+        *reinterpret_cast<float*>(plane0 + off) = v;  // the tensor core reads the top 19 bits
+    } else {
+        const __nv_bfloat16 hi = __float2bfloat16_rn(v);
+        *reinterpret_cast<__nv_bfloat16*>(plane0 + off) = hi;
+        if (PREC == TC_BF16X3)
+            *reinterpret_cast<__nv_bfloat16*>(plane0 + plane_bytes + off) =
+                __float2bfloat16_rn(v - __bfloat162float(hi));
+    }
+}
+
+// Pack node multipoles (float32, [group][node][NT][8]) into the B-operand image of one pass of
+// kTcN right-hand sides: rows = right-hand sides, columns = terms (K-major).
+template <int D, int P, int PREC>
+__global__ void tc_pack_kernel(int64_t nnodes, const int64_t* __restrict__ item_off, const float* __restrict__ mult,
+                               int64_t group_stride, int nr_total, unsigned char* __restrict__ image) {
+    using S = TcShape<D, P, PREC>;
+    const int64_t node = blockIdx.x;
+    if (item_off[node] == item_off[node + 1]) return;  // no target uses this node
+    unsigned char* img = image + node * (int64_t)S::B_BYTES;
+    const int plane = kTcN * S::NTP * S::EL;
+    for (int e = threadIdx.x; e < kTcN * S::NTP; e += blockDim.x) {
+        const int n = e / S::NTP, k = e - n * S::NTP;
+        float v = 0.f;
+        if (k < S::NT && n < nr_total) v = mult[(n / 8) * group_stride + (node * S::NT + k) * 8 + (n % 8)];
+        // B rows are right-hand sides: same core-matrix rule with kTcN rows
+        tc_store<PREC>(img, plane, S::off(n, k), v);
+    }
+}
+
+template <int D, int P, int PREC>
+__global__ void __launch_bounds__(kTB) far_tc_kernel(MvmArgs a, KernelParams kp, const __grid_constant__ FarTables T,
+                                                      const unsigned char* __restrict__ image, int nr_total,
+                                                      int64_t ynear_group_stride) {
+    using Lay = Layout<D, P>;
+    using S = TcShape<D, P, PREC>;
+    constexpr int NT = S::NT, NTP = S::NTP, ST = S::STAGES;
+    constexpr int APLANE = 128 * NTP * S::EL, BPLANE = kTcN * NTP * S::EL;
+    constexpr uint32_t IDESC = tc::instr_desc(PREC == TC_TF32 ? 2u : 1u, 128u, (uint32_t)kTcN);
+    extern __shared__ __align__(128) unsigned char tc_smem[];
+    unsigned char* Abuf = tc_smem;                                  // [ST][A_BYTES]
+    unsigned char* Bbuf = tc_smem + ST * S::A_BYTES;                // [ST][B_BYTES]
+    __shared__ __align__(8) uint64_t bar_b[2], bar_mma[2];
+    __shared__ uint32_t tmem_base;
+    __shared__ int s_fail;
+    const int tl = threadIdx.x, warp = tl >> 5;
+    const int64_t blk = blockIdx.x;
+    const int2 rg = a.blk[blk];
+    const int t = rg.x + tl;
+    const bool valid = t < rg.y;
+    const float4 xt = valid ? a.xs[t] : make_float4(0.f, 0.f, 0.f, 0.f);
+    const int64_t e0 = a.far_off[blk], e1 = a.far_off[blk + 1];
+    const int ne = (int)(e1 - e0);
+    if (tl == 0) {
+        for (int s = 0; s < 2; ++s) {
+            ptx::mbar_init(&bar_b[s], 1);
+            ptx::mbar_init(&bar_mma[s], 1);
+        }
+        ptx::fence_mbar_init();
+        s_fail = 0;
+    }
+    if (warp == 0) {
+        tc::alloc(&tmem_base, 32);
+        tc::relinquish();
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tmem = tmem_base;
+    bool ok = true;
+    for (int i = 0; i < ne && ok; ++i) {
+        const int s = i % ST;
+        unsigned char* A = Abuf + s * S::A_BYTES;
+        unsigned char* B = Bbuf + s * S::B_BYTES;
+        if (i >= ST) ok = ptx::mbar_wait_bounded(&bar_mma[s], (uint32_t)(((i / ST) - 1) & 1), kWaitCycles);
+        if (!__syncthreads_and(ok)) { ok = false; break; }
+        const int2 ent = a.far_ent[e0 + i];
+        if (tl == 0) {
+            ptx::fence_proxy_async_smem();
+            ptx::mbar_arrive_expect_tx(&bar_b[s], (uint32_t)S::B_BYTES);
+            ptx::bulk_g2s(B, image + (int64_t)ent.x * S::B_BYTES, (uint32_t)S::B_BYTES, &bar_b[s]);
+        }
+        // basis row of this target for node ent.x (zeros when the entry does not apply to it)
+        const bool active = valid && entry_active(ent.y, a.masks, tl);
+        if (active) {
+            const float4 c = a.nd_cf[ent.x];
+            const float dx = xt.x - c.x, dy = xt.y - c.y, dz = xt.z - c.z, dw = D == 4 ? xt.w - c.w : 0.f;
+            const float r2 = dx * dx + dy * dy + dz * dz + dw * dw;
+            const float rinv = rsqrtf(r2);
+            const float r = r2 * rinv;
+            const float u = a.nd_scale[ent.x] * rinv;
+            float J[P + 1];
+            kernel_jets<P>(kp, r, rinv, J);
+            float up[P + 1];
+            up[0] = 1.f;
+#pragma unroll
+            for (int j = 1; j <= P; ++j) up[j] = up[j - 1] * u;
+            float G[Lay::npairs];
+#pragma unroll
+            for (int k = 0; k <= P; ++k)
+#pragma unroll
+                for (int jj = 0; jj < Lay::nj(k); ++jj) {
+                    const int j = k + 2 * jj, q = Lay::pair(k) + jj;
+                    float R = 0.f;
+#pragma unroll
+                    for (int m = 0; m <= j; ++m) R = fmaf(T.That[q][m], J[m], R);
+                    G[q] = up[j] * R;
+                }
+            const float ux = dx * rinv, uy = dy * rinv, uz = dz * rinv, uw = dw * rinv;
+            const float u2_3 = ux * ux + uy * uy + uz * uz;
+            solid_harmonics<D, P>(ux, uy, uz, uw, u2_3, u2_3 + uw * uw, T, [&](int k, int h, float Y) {
+                const int o = Lay::off(k) + h * Lay::nj(k);
+#pragma unroll
+                for (int jj = 0; jj < Lay::nj(k); ++jj) tc_store<PREC>(A, APLANE, S::off(tl, o + jj), Y * G[Lay::pair(k) + jj]);
+            });
+#pragma unroll
+            for (int q = NT; q < NTP; ++q) tc_store<PREC>(A, APLANE, S::off(tl, q), 0.f);
+        } else {
+#pragma unroll 4
+            for (int q = 0; q < NTP; ++q) tc_store<PREC>(A, APLANE, S::off(tl, q), 0.f);
+        }
+        ptx::fence_proxy_async_smem();  // generic-proxy stores -> visible to the tensor core
+        __syncthreads();
+        if (tl == 0) {
+            bool got = ptx::mbar_wait_bounded(&bar_b[s], (uint32_t)((i / ST) & 1), kWaitCycles);
+            if (got) {
+                tc::fence_after_sync();
+                constexpr int KSTEP_BYTES = 256;  // one MMA consumes 2 core matrices (32 bytes) of K
+                constexpr int NSTEP = PREC == TC_TF32 ? NTP / 8 : NTP / 16;
+#pragma unroll 1
+                for (int ks = 0; ks < NSTEP; ++ks) {
+                    const uint64_t da = tc::smem_desc(A + ks * KSTEP_BYTES, 128, S::SBO_A);
+                    const uint64_t db = tc::smem_desc(B + ks * KSTEP_BYTES, 128, S::SBO_A);
+                    const bool acc = (i > 0) || (ks > 0);
+                    if (PREC == TC_TF32) {
+                        tc::mma_tf32(tmem, da, db, IDESC, acc);
+                    } else {
+                        tc::mma_bf16(tmem, da, db, IDESC, acc);
+                        if (PREC == TC_BF16X3) {
+                            const uint64_t da_lo = tc::smem_desc(A + APLANE + ks * KSTEP_BYTES, 128, S::SBO_A);
+                            const uint64_t db_lo = tc::smem_desc(B + BPLANE + ks * KSTEP_BYTES, 128, S::SBO_A);
+                            tc::mma_bf16(tmem, da, db_lo, IDESC, true);
+                            tc::mma_bf16(tmem, da_lo, db, IDESC, true);
+                        }
+                    }
+                }
+            } else {
+                s_fail = 1;
+            }
+            tc::commit(&bar_mma[s]);  // arrives when the MMAs above (if any) are done
+        }
+        __syncthreads();
+        if (s_fail) ok = false;
+    }
+    // wait for the last MMA group, then read the accumulator rows
+    if (ne > 0 && ok) {
+        const int last = ne - 1;
+        ok = ptx::mbar_wait_bounded(&bar_mma[last % ST], (uint32_t)((last / ST) & 1), kWaitCycles);
+    }
+    const bool all_ok = __syncthreads_and(ok) != 0;
+    tc::fence_after_sync();
+    float acc[kTcN];
+#pragma unroll
+    for (int r = 0; r < kTcN; ++r) acc[r] = 0.f;
+    if (ne > 0 && all_ok) {
+        const uint32_t lane_addr = tmem + ((uint32_t)(warp * 32) << 16);
+        tc::ld16(lane_addr, acc);
+        tc::ld16(lane_addr + 16, acc + 16);
+    }
+    if (!all_ok && tl == 0) {
+        atomicExch(a.err, 1);
+        // let any bulk copies and MMAs still in flight finish before the CTA leaves (bounded)
+        for (int s = 0; s < ST; ++s) {
+            ptx::mbar_wait_bounded(&bar_b[s], 0, kWaitCycles);
+            ptx::mbar_wait_bounded(&bar_mma[s], 0, kWaitCycles);
+        }
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    if (warp == 0) tc::dealloc(tmem, 32);
+    if (valid && all_ok) {
+        const int64_t o = a.perm[t];
+        for (int r = 0; r < nr_total; ++r)
+            a.y[(int64_t)r * a.N + o] = a.ynear[(int64_t)(r / 8) * ynear_group_stride + (int64_t)(r % 8) * a.N + t] + acc[r];
+    }
+}
+
+}  // namespace fkt
+
+namespace fkt {
+
+struct TcLaunch {
+    const MvmArgs* a;
+    const KernelParams* kp;
+    const FarTables* T;
+    int64_t nblocks, nnodes;
+    int64_t group_stride;        // floats between right-hand-side groups of the multipoles
+    int64_t ynear_group_stride;  // floats between right-hand-side groups of the near result
+    int nr_total;                // right-hand sides in this pass (<= kTcN)
+    unsigned char* image;        // packed B operands, [nodes][B_BYTES]
+    cudaStream_t s_pack, s_far;
+};
+
+template <int D, int P, int PREC>
+int launch_tc_t(const TcLaunch& L) {
+    using S = TcShape<D, P, PREC>;
+    if constexpr (!S::supported) {
+        return FKT_ERR_UNSUPPORTED;
+    } else {
+        tc_pack_kernel<D, P, PREC><<<(unsigned)L.nnodes, 256, 0, L.s_pack>>>(
+            L.nnodes, L.a->s2m_item_off, L.a->mult, L.group_stride, L.nr_total, L.image);
+        FKT_CUDA_TRY(cudaGetLastError());
+        return FKT_OK;
+    }
+}
+
+template <int D, int P, int PREC>
+int launch_tc_far_t(const TcLaunch& L) {
+    using S = TcShape<D, P, PREC>;
+    if constexpr (!S::supported) {
+        return FKT_ERR_UNSUPPORTED;
+    } else {
+        const size_t smem = S::smem_bytes();
+        static bool attr = false;
+        if (!attr) {
+            FKT_CUDA_TRY(cudaFuncSetAttribute(far_tc_kernel<D, P, PREC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              (int)smem));
+            attr = true;
+        }
+        far_tc_kernel<D, P, PREC><<<(unsigned)L.nblocks, kTB, smem, L.s_far>>>(*L.a, *L.kp, *L.T, L.image, L.nr_total,
+                                                                                L.ynear_group_stride);
+        FKT_CUDA_TRY(cudaGetLastError());
+        return FKT_OK;
+    }
+}
+
+template <int D, int PLO, int PHI>
+int launch_tc_range(int p, int prec, bool far, const TcLaunch& L) {
+    if (p == PHI) {
+        if (prec == TC_BF16) return far ? launch_tc_far_t<D, PHI, TC_BF16>(L) : launch_tc_t<D, PHI, TC_BF16>(L);
+        if (prec == TC_BF16X3) return far ? launch_tc_far_t<D, PHI, TC_BF16X3>(L) : launch_tc_t<D, PHI, TC_BF16X3>(L);
+        return far ? launch_tc_far_t<D, PHI, TC_TF32>(L) : launch_tc_t<D, PHI, TC_TF32>(L);
+    }
+    if constexpr (PHI > PLO) return launch_tc_range<D, PLO, PHI - 1>(p, prec, far, L);
+    return FKT_ERR_INVALID_ARG;
+}
+
+// Bytes of the packed B-operand image per node.
+inline int tc_b_bytes(int d, int p, int prec) {
+    int nt = 1;
+    for (int i = 1; i <= d; ++i) nt = nt * (p + i) / i;
+    const int ntp = (nt + 15) / 16 * 16;
+    const int el = prec == TC_TF32 ? 4 : 2;
+    return kTcN * ntp * el * (prec == TC_BF16X3 ? 2 : 1);
+}
+
+}  // namespace fkt

@@ -99,6 +99,8 @@ struct fkt_plan_s {
     float* ynear = nullptr;        // near-field result, sorted [nrhs][N]
     float* mult = nullptr;         // multipoles [nodes][nterms][nrhs]
     float* s2m_part = nullptr;     // per-item partial multipoles [items][nterms][nrhs]
+    unsigned char* tc_image = nullptr;  // packed tensor-core operands of the multipoles
+    int cap_tc = 0;                // far_precision the image was sized for (0: none)
     float* hbuf_w = nullptr;       // device staging for fkt_mvm_host
     float* hbuf_y = nullptr;
     int hbuf_cap = 0;              // right-hand sides the staging buffers hold
@@ -140,9 +142,10 @@ struct MvmBuffers {
     float* ynear;
     float* mult;
     float* part;
+    unsigned char* image;  // tensor-core operand image of the multipoles (far_precision != fp32)
 };
 // Floats each buffer needs for nrhs right-hand sides (each rounded up to 64 floats).
-void mvm_buffer_floats(const fkt_plan_s* P, int nrhs, size_t out[4]);
+void mvm_buffer_floats(const fkt_plan_s* P, int nrhs, size_t out[5]);
 int run_mvm(fkt_plan_s* P, const MvmBuffers& B, const float* w, float* y, int nrhs, bool timing);
 int launch_mvm(fkt_plan_s* P, const float* w, float* y, int nrhs);
 int launch_dense(fkt_plan_s* P, const float* w, float* y, int nrhs);

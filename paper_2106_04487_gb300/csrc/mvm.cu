@@ -6,6 +6,7 @@
 
 #include "mvm_kernels.cuh"
 #include "far_dispatch.cuh"
+#include "far_tc.cuh"
 
 namespace fkt {
 
@@ -20,6 +21,20 @@ FKT_DECL_RANGE(4, 0, 4)
 FKT_DECL_RANGE(4, 5, 6)
 FKT_DECL_RANGE(4, 7, 8)
 #undef FKT_DECL_RANGE
+
+int launch_tc_d3_p0_6(int p, int prec, bool far, const TcLaunch& L);
+int launch_tc_d3_p7_10(int p, int prec, bool far, const TcLaunch& L);
+int launch_tc_d4_p0_5(int p, int prec, bool far, const TcLaunch& L);
+int launch_tc_d4_p6_8(int p, int prec, bool far, const TcLaunch& L);
+
+static int launch_tc_any(int d, int p, int prec, bool far, const TcLaunch& L) {
+    if (d == 3) return p <= 6 ? launch_tc_d3_p0_6(p, prec, far, L) : launch_tc_d3_p7_10(p, prec, far, L);
+    return p <= 5 ? launch_tc_d4_p0_5(p, prec, far, L) : launch_tc_d4_p6_8(p, prec, far, L);
+}
+
+static int tc_prec_of(int far_precision) {
+    return far_precision == FAR_BF16 ? TC_BF16 : far_precision == FAR_BF16X3 ? TC_BF16X3 : TC_TF32;
+}
 
 static int launch_s2m_any(int d, int p, int nrb, const FarLaunch& L) {
     if (d == 3) {
@@ -116,8 +131,12 @@ __global__ void dense_lists_kernel(int64_t nblocks, int64_t* off, int2* ent) {
 
 }  // namespace
 
-void mvm_buffer_floats(const fkt_plan_s* P, int nrhs, size_t out[4]) {
-    const int nrb = nrhs == 1 ? 1 : 8;
+// Right-hand sides per pass of the s2m / near kernels: 1 for a single right-hand side on the
+// float32 far path, 8 otherwise (the tensor-core far field always consumes groups of 8).
+static int rhs_block(const fkt_plan_s* P, int nrhs) { return (nrhs == 1 && P->far_precision == FAR_FP32) ? 1 : 8; }
+
+void mvm_buffer_floats(const fkt_plan_s* P, int nrhs, size_t out[5]) {
+    const int nrb = rhs_block(P, nrhs);
     const size_t groups = (size_t)(nrhs + nrb - 1) / nrb;
     const size_t N = (size_t)P->N, NT = (size_t)P->nterms;
     const size_t nodes = std::max<int64_t>(P->nnodes, 1), items = std::max<int64_t>(P->n_s2m_items, 1);
@@ -125,32 +144,47 @@ void mvm_buffer_floats(const fkt_plan_s* P, int nrhs, size_t out[4]) {
     out[1] = round64(groups * nrb * N);                             // near result
     out[2] = round64(groups * nrb * NT * nodes);                    // multipoles
     out[3] = round64(groups * nrb * NT * items);                    // s2m partials
+    out[4] = P->far_precision == FAR_FP32 ? 0
+             : round64(nodes * (size_t)tc_b_bytes(P->d, P->p, tc_prec_of(P->far_precision)) / 4);
 }
 
 int ensure_rhs_capacity(fkt_plan_s* P, int nrhs) {
-    const int cap = nrhs == 1 ? 1 : (nrhs + 7) / 8 * 8;
-    if (cap <= P->cap_rhs) return FKT_OK;
-    cudaFree(P->rec);
-    cudaFree(P->ynear);
-    cudaFree(P->mult);
-    cudaFree(P->s2m_part);
-    P->rec = nullptr;
-    P->ynear = P->mult = P->s2m_part = nullptr;
-    P->cap_rhs = 0;
-    size_t f[4];
+    const int nrb = rhs_block(P, nrhs);
+    const int cap = nrb == 1 ? 1 : (nrhs + 7) / 8 * 8;
+    size_t f[5];
     mvm_buffer_floats(P, cap, f);
-    FKT_CUDA_TRY(cudaMalloc(&P->rec, sizeof(float) * f[0]));
-    FKT_CUDA_TRY(cudaMalloc(&P->ynear, sizeof(float) * f[1]));
-    FKT_CUDA_TRY(cudaMalloc(&P->mult, sizeof(float) * f[2]));
-    FKT_CUDA_TRY(cudaMalloc(&P->s2m_part, sizeof(float) * f[3]));
-    P->cap_rhs = cap;
+    if (cap > P->cap_rhs) {
+        cudaFree(P->rec);
+        cudaFree(P->ynear);
+        cudaFree(P->mult);
+        cudaFree(P->s2m_part);
+        P->rec = nullptr;
+        P->ynear = P->mult = P->s2m_part = nullptr;
+        P->cap_rhs = 0;
+        FKT_CUDA_TRY(cudaMalloc(&P->rec, sizeof(float) * f[0]));
+        FKT_CUDA_TRY(cudaMalloc(&P->ynear, sizeof(float) * f[1]));
+        FKT_CUDA_TRY(cudaMalloc(&P->mult, sizeof(float) * f[2]));
+        FKT_CUDA_TRY(cudaMalloc(&P->s2m_part, sizeof(float) * f[3]));
+        P->cap_rhs = cap;
+    }
+    if (f[4] && P->cap_tc != P->far_precision + 1) {
+        cudaFree(P->tc_image);
+        P->tc_image = nullptr;
+        P->cap_tc = 0;
+        FKT_CUDA_TRY(cudaMalloc(&P->tc_image, sizeof(float) * f[4]));
+        P->cap_tc = P->far_precision + 1;
+    }
     return FKT_OK;
 }
 
 // One product on the plan's stream with the given work buffers: per group of right-hand sides
 //   permute -> fork [s2m -> reduce on stream2] || near field -> join -> far field (+ combine).
+static int run_mvm_tc(fkt_plan_s* P, const MvmBuffers& B, const float* w, float* y, int nrhs, bool timing);
+static int finish_timing(fkt_plan_s* P);
+
 int run_mvm(fkt_plan_s* P, const MvmBuffers& B, const float* w, float* y, int nrhs, bool timing) {
-    const int nrb = nrhs == 1 ? 1 : 8;
+    if (P->far_precision != FAR_FP32) return run_mvm_tc(P, B, w, y, nrhs, timing);
+    const int nrb = rhs_block(P, nrhs);
     const int groups = (nrhs + nrb - 1) / nrb;
     cudaStream_t st = P->stream, st2 = P->stream2;
     const int64_t N = P->N;
@@ -188,26 +222,86 @@ int run_mvm(fkt_plan_s* P, const MvmBuffers& B, const float* w, float* y, int nr
         rc = launch_far_any(P->d, P->p, nrb, L);
         if (rc) return rc;
     }
-    if (timing) {
-        FKT_CUDA_TRY(cudaEventRecord(P->ev[7], st));
-        FKT_CUDA_TRY(cudaEventSynchronize(P->ev[7]));
-        float t_tot = 0, t_s2m = 0, t_near = 0, t_far = 0;
-        cudaEventElapsedTime(&t_tot, P->ev[0], P->ev[7]);
-        cudaEventElapsedTime(&t_s2m, P->ev[2], P->ev[3]);
-        cudaEventElapsedTime(&t_near, P->ev[5], P->ev[6]);
-        cudaEventElapsedTime(&t_far, P->ev[6], P->ev[7]);  // includes the wait for s2m, if any
-        P->stats.last_total_ms = t_tot;
-        P->stats.last_s2m_ms = t_s2m;
-        P->stats.last_near_ms = t_near;
-        P->stats.last_far_ms = t_far;
+    if (timing) return finish_timing(P);
+    return FKT_OK;
+}
+
+// Stage times of the last product from the plan's events: 0 start, 2-3 s2m (second stream),
+// 5-6 near field, 7 end; "far" is 6 -> 7 and includes any wait for s2m.
+static int finish_timing(fkt_plan_s* P) {
+    FKT_CUDA_TRY(cudaEventRecord(P->ev[7], P->stream));
+    FKT_CUDA_TRY(cudaEventSynchronize(P->ev[7]));
+    float t_tot = 0, t_s2m = 0, t_near = 0, t_far = 0;
+    cudaEventElapsedTime(&t_tot, P->ev[0], P->ev[7]);
+    cudaEventElapsedTime(&t_s2m, P->ev[2], P->ev[3]);
+    cudaEventElapsedTime(&t_near, P->ev[5], P->ev[6]);
+    cudaEventElapsedTime(&t_far, P->ev[6], P->ev[7]);
+    P->stats.last_total_ms = t_tot;
+    P->stats.last_s2m_ms = t_s2m;
+    P->stats.last_near_ms = t_near;
+    P->stats.last_far_ms = t_far;
+    return FKT_OK;
+}
+
+// Tensor-core far field: passes of up to kTcN right-hand sides; within a pass, groups of 8 run
+// permute / s2m / near as usual, then the multipoles of the pass are packed into the operand
+// image and one far_tc launch accumulates every far node into TMEM and writes y.
+static int run_mvm_tc(fkt_plan_s* P, const MvmBuffers& B, const float* w, float* y, int nrhs, bool timing) {
+    cudaStream_t st = P->stream, st2 = P->stream2;
+    if (timing) FKT_CUDA_TRY(cudaEventRecord(P->ev[0], st));
+    const int64_t N = P->N;
+    const size_t NT = (size_t)P->nterms;
+    const size_t rec_group = (size_t)N * rec_f4(P->d, 8);
+    const size_t nodes = std::max<int64_t>(P->nnodes, 1), items = std::max<int64_t>(P->n_s2m_items, 1);
+    const int prec = tc_prec_of(P->far_precision);
+    for (int r0 = 0; r0 < nrhs; r0 += kTcN) {
+        const int npass = std::min(kTcN, nrhs - r0);
+        const int g0 = r0 / 8, ng = (npass + 7) / 8;
+        MvmArgs a = base_args(P);
+        for (int gi = 0; gi < ng; ++gi) {
+            const int g = g0 + gi;
+            const int nr = std::min(8, nrhs - g * 8);
+            float4* rec = B.rec + (size_t)g * rec_group;
+            a.rec = rec;
+            a.ynear = B.ynear + (size_t)g * 8 * N;
+            a.mult = B.mult + (size_t)g * 8 * NT * nodes;
+            a.part = B.part + (size_t)g * 8 * NT * items;
+            a.nr = nr;
+            launch_permute(P->d, 8, (unsigned)((N + 255) / 256), st, N, P->perm, P->xs, w + (size_t)g * 8 * N, nr,
+                           P->kp.sig, rec);
+            FKT_CUDA_TRY(cudaGetLastError());
+            FKT_CUDA_TRY(cudaEventRecord(P->ev[1], st));
+            FKT_CUDA_TRY(cudaStreamWaitEvent(st2, P->ev[1], 0));
+            FarLaunch L{&a, &P->kp, &P->tabs, P->nblocks, P->n_s2m_items, P->nnodes, st, st2};
+            if (timing && r0 == 0 && gi == 0) FKT_CUDA_TRY(cudaEventRecord(P->ev[2], st2));
+            int rc = launch_s2m_any(P->d, P->p, 8, L);
+            if (rc) return rc;
+            if (timing) FKT_CUDA_TRY(cudaEventRecord(P->ev[3], st2));
+            if (timing && r0 == 0 && gi == 0) FKT_CUDA_TRY(cudaEventRecord(P->ev[5], st));
+            launch_near(P->d, 8, 2, P->kernel.kind, (unsigned)P->nblocks, st, a, P->kp);
+            FKT_CUDA_TRY(cudaGetLastError());
+            if (timing) FKT_CUDA_TRY(cudaEventRecord(P->ev[6], st));
+        }
+        a.mult = B.mult + (size_t)g0 * 8 * NT * nodes;
+        a.ynear = B.ynear + (size_t)g0 * 8 * N;
+        a.y = y + (size_t)r0 * N;
+        TcLaunch T{&a, &P->kp, &P->tabs, P->nblocks, P->nnodes, (int64_t)(8 * NT * nodes), (int64_t)(8 * N), npass,
+                   B.image, st2, st};
+        int rc = launch_tc_any(P->d, P->p, prec, false, T);  // pack on the s2m stream
+        if (rc) return rc;
+        FKT_CUDA_TRY(cudaEventRecord(P->ev[4], st2));
+        FKT_CUDA_TRY(cudaStreamWaitEvent(st, P->ev[4], 0));
+        rc = launch_tc_any(P->d, P->p, prec, true, T);
+        if (rc) return rc;
     }
+    if (timing) return finish_timing(P);
     return FKT_OK;
 }
 
 int launch_mvm(fkt_plan_s* P, const float* w, float* y, int nrhs) {
     int rc = ensure_rhs_capacity(P, nrhs);
     if (rc) return rc;
-    MvmBuffers B{P->rec, P->ynear, P->mult, P->s2m_part};
+    MvmBuffers B{P->rec, P->ynear, P->mult, P->s2m_part, P->tc_image};
     return run_mvm(P, B, w, y, nrhs, P->timing);
 }
 
@@ -222,7 +316,7 @@ int launch_dense(fkt_plan_s* P, const float* w, float* y, int nrhs) {
         dense_lists_kernel<<<(unsigned)((P->nblocks + 256) / 256), 256, 0, st>>>(P->nblocks, P->dense_off, P->dense_ent);
         FKT_CUDA_TRY(cudaGetLastError());
     }
-    const int nrb = nrhs == 1 ? 1 : 8;
+    const int nrb = rhs_block(P, nrhs);
     const int groups = (nrhs + nrb - 1) / nrb;
     const int64_t N = P->N;
     const size_t rec_group = (size_t)N * rec_f4(P->d, nrb);

@@ -44,12 +44,18 @@ int scratch_for_current_device(float** out) {
 extern "C" int fkt_mvm_noalloc(fkt_plan_t plan, const float* w, float* y, int nrhs) {
     using namespace fkt;
     if (!plan || !w || !y || nrhs < 1 || nrhs > kMaxRhs || w == y) return FKT_ERR_INVALID_ARG;
-    size_t f[4];
+    size_t f[5];
     mvm_buffer_floats(plan, nrhs, f);   // each part is already a multiple of 64 floats (256 bytes)
-    if (f[0] + f[1] + f[2] + f[3] > kScratchFloats) return FKT_ERR_SCRATCH_LIMIT;
+    if (f[0] + f[1] + f[2] + f[3] + f[4] > kScratchFloats) return FKT_ERR_SCRATCH_LIMIT;
     float* base = nullptr;
     int rc = scratch_for_current_device(&base);
     if (rc) return rc;
-    MvmBuffers B{reinterpret_cast<float4*>(base), base + f[0], base + f[0] + f[1], base + f[0] + f[1] + f[2]};
+    float* q = base;
+    MvmBuffers B{};
+    B.rec = reinterpret_cast<float4*>(q);
+    B.ynear = (q += f[0]);
+    B.mult = (q += f[1]);
+    B.part = (q += f[2]);
+    B.image = reinterpret_cast<unsigned char*>(q += f[3]);
     return run_mvm(plan, B, w, y, nrhs, false);
 }
