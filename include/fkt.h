@@ -164,6 +164,48 @@ int fkt_precond_apply(fkt_plan_t plan, const float* r, float* z, int nrhs);
 int fkt_solve(fkt_plan_t plan, double sigma2, const float* b, float* x, int nrhs, double tol, int max_iter,
               fkt_solve_info* info);
 
+/* ---- Batches of independent problems (one product over all of them) ----
+ * Each problem has its own points and kernel; all share d, p and theta.  The batch plan builds
+ * every problem's tree, lists and expansion, then merges them into one arena so each stage of the
+ * product runs as one launch over the whole batch (near-field blocks grouped by kernel kind and
+ * ordered by work, largest first), and captures the whole product as one CUDA graph that later
+ * calls with the same buffers replay. */
+typedef struct fkt_batch_s* fkt_batch_t;
+typedef struct {
+    const float* points;   /* device [N][d] float32 */
+    int64_t N;             /* >= 1 */
+    fkt_kernel kernel;
+} fkt_problem;
+
+/* leaf_size > 0 uses it for every problem; leaf_size = 0 autotunes it per size class (problems
+ * whose N has the same power of two) by timing candidate plans (64, 128, 256, 512 points) on the
+ * device with 8 right-hand sides (fkt_autotune_leaf).  Other arguments as for fkt_plan. */
+int fkt_batch_plan(int nprob, const fkt_problem* probs, int d, int p, int leaf_size, double theta,
+                   void* cuda_stream, fkt_batch_t* out);
+
+/* y = Ktilde_i w for every problem i at once.  w, y device [nrhs][N_total] float32 where
+ * N_total = sum N_i and problem i occupies columns [offset_i, offset_i + N_i) (fkt_batch_info),
+ * each in its caller's point order.  The first call with given (w, y, nrhs) runs the product and
+ * captures it as a CUDA graph; calls with the same buffers replay the graph.  Asynchronous. */
+int fkt_batch_mvm(fkt_batch_t batch, const float* w, float* y, int nrhs);
+
+/* fkt_set_option for every problem of the batch (drops the captured graph). */
+int fkt_batch_set_option(fkt_batch_t batch, const char* key, const char* value);
+
+/* offsets [nprob+1] (column offsets), leaf_sizes [nprob], totals; any pointer may be NULL. */
+int fkt_batch_info(fkt_batch_t batch, int64_t* offsets, int32_t* leaf_sizes, fkt_stats* total);
+
+/* fkt_check for the batch. */
+int fkt_batch_check(fkt_batch_t batch);
+
+void fkt_batch_destroy(fkt_batch_t batch);
+
+/* Autotuner: build a plan for each candidate leaf size, time fkt_mvm with nrhs right-hand sides
+ * (best of 3 after a warm-up, CUDA events), and return the fastest leaf size (and its time in
+ * milliseconds if best_ms is not NULL).  Synchronizes. */
+int fkt_autotune_leaf(const float* points, int64_t N, int d, fkt_kernel kernel, int p, double theta, int nrhs,
+                      const int* candidates, int ncand, void* cuda_stream, int* best_leaf, double* best_ms);
+
 /* Options (all take effect on the next call):
  *   "timing"    "0" | "1"   record per-stage CUDA-event times of fkt_mvm in fkt_stats
  *   "far_precision"  "fp32" (default) | "tf32" | "bf16" | "bf16x3"  arithmetic of the far-field

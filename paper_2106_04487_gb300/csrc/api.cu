@@ -29,6 +29,7 @@ void free_plan(fkt_plan_s* P) {
     for (void* b : bufs)
         if (b) cudaFree(b);
     fkt::free_solve(P);
+    fkt::free_batch_arrays(P);
     for (auto& e : P->ev)
         if (e) cudaEventDestroy(e);
     if (P->stream2) cudaStreamDestroy(P->stream2);
@@ -145,6 +146,7 @@ int fkt_mvm_host(fkt_plan_t plan, const float* w_host, float* y_host, int nrhs) 
 
 int fkt_dense_mvm(fkt_plan_t plan, const float* w, float* y, int nrhs) {
     if (!plan || !w || !y || nrhs < 1 || nrhs > fkt::kMaxRhs || w == y) return FKT_ERR_INVALID_ARG;
+    if (plan->nprob) return FKT_ERR_UNSUPPORTED;
     return fkt::launch_dense(plan, w, y, nrhs);
 }
 

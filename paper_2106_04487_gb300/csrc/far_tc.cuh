@@ -76,7 +76,7 @@ __global__ void tc_pack_kernel(int64_t nnodes, const int64_t* __restrict__ item_
 }
 
 template <int D, int P, int PREC>
-__global__ void __launch_bounds__(kTB) far_tc_kernel(MvmArgs a, KernelParams kp, const __grid_constant__ FarTables T,
+__global__ void __launch_bounds__(kTB) far_tc_kernel(MvmArgs a, KernelParams kp_all, const __grid_constant__ FarTables T,
                                                       const unsigned char* __restrict__ image, int nr_total,
                                                       int64_t ynear_group_stride) {
     using Lay = Layout<D, P>;
@@ -91,7 +91,8 @@ __global__ void __launch_bounds__(kTB) far_tc_kernel(MvmArgs a, KernelParams kp,
     __shared__ uint32_t tmem_base;
     __shared__ int s_fail;
     const int tl = threadIdx.x, warp = tl >> 5;
-    const int64_t blk = blockIdx.x;
+    const int64_t blk = cta_block(a);
+    const KernelParams kp = block_params(a, blk, kp_all);
     const int2 rg = a.blk[blk];
     const int t = rg.x + tl;
     const bool valid = t < rg.y;

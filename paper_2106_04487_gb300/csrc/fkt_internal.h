@@ -121,6 +121,21 @@ struct fkt_plan_s {
     double* cg_s = nullptr;        // scalars: [8][kMaxRhs]
     cudaStream_t stream2 = nullptr;
     cudaEvent_t ev[8] = {};
+    // batch of independent problems merged into one plan (empty for a single problem)
+    int nprob = 0;
+    std::vector<int64_t> prob_off;          // first point of each problem, nprob + 1 entries
+    fkt::KernelParams* kps = nullptr;       // device, per problem
+    int32_t* blk_prob = nullptr;            // device, per target block
+    float* pt_sig = nullptr;                // device, per point: near-field coordinate scale
+    std::vector<int> kind_of_list;          // kernel kind of each near work list
+    std::vector<int32_t*> kind_list;        // device: target blocks of that kind, largest first
+    std::vector<int64_t> kind_list_n;
+    int32_t* far_list = nullptr;            // device: all target blocks, most far entries first
+    // CUDA graph of the last batched product (replayed while w, y, nrhs stay the same)
+    cudaGraphExec_t graph = nullptr;
+    const void* graph_w = nullptr;
+    const void* graph_y = nullptr;
+    int graph_nrhs = 0;
     // stats
     fkt_stats stats{};
 };
@@ -134,6 +149,8 @@ KernelParams make_kernel_params(const fkt_kernel& k);
 // tree.cu / lists.cu
 int build_tree(fkt_plan_s* P, const float* points);
 int build_lists(fkt_plan_s* P);
+
+struct MvmArgs;
 
 // mvm.cu
 // Work buffers of one MVM call (fkt_mvm: plan-owned; fkt_mvm_noalloc: the static scratch).
@@ -150,6 +167,10 @@ int run_mvm(fkt_plan_s* P, const MvmBuffers& B, const float* w, float* y, int nr
 int launch_mvm(fkt_plan_s* P, const float* w, float* y, int nrhs);
 int launch_dense(fkt_plan_s* P, const float* w, float* y, int nrhs);
 int ensure_rhs_capacity(fkt_plan_s* P, int nrhs);
+
+// stage launch helpers shared with batch.cu
+void launch_near_stage(fkt_plan_s* P, MvmArgs& a, int nrb, int tpt, cudaStream_t st);
+int free_batch_arrays(fkt_plan_s* P);
 
 // solve.cu
 int precond_setup(fkt_plan_s* P, double sigma2);

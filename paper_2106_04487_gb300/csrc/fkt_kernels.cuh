@@ -229,7 +229,20 @@ struct MvmArgs {
     float* y;                  // output (original order), [nrhs][N]; this group starts at y
     int nr;                    // right-hand sides actually present in this group (<= NR)
     int* err;                  // device error word: 1 = a bounded wait ran out
+    // batches of independent problems (all null for a single problem)
+    const KernelParams* kps;   // kernel parameters per problem
+    const int32_t* blk_prob;   // problem of each target block
+    const int32_t* blk_list;   // grid index -> target block (work ordered largest first)
+    const float* pt_sig;       // near-field coordinate scale of each point's problem
 };
+
+// Target block handled by this CTA and its kernel parameters (per problem in a batch).
+__device__ __forceinline__ int64_t cta_block(const MvmArgs& a) {
+    return a.blk_list ? (int64_t)a.blk_list[blockIdx.x] : (int64_t)blockIdx.x;
+}
+__device__ __forceinline__ KernelParams block_params(const MvmArgs& a, int64_t blk, const KernelParams& kp) {
+    return a.kps ? a.kps[a.blk_prob[blk]] : kp;
+}
 
 // Source record of one point for a pass of NR right-hand sides: (x, y, z, w) when d = 3 and
 // NR = 1, otherwise (x, y, z, u) followed by the NR weights, padded to whole float4s.

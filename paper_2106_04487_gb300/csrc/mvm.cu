@@ -89,13 +89,13 @@ void launch_near(int d, int nrb, int tpt, int kind, unsigned grid, cudaStream_t 
 }
 
 void launch_permute(int d, int nrb, unsigned grid, cudaStream_t st, int64_t N, const int32_t* perm, const float4* xs,
-                    const float* w, int nr, float sig, float4* rec) {
+                    const float* w, int nr, float sig, const float* pt_sig, float4* rec) {
     if (d == 3) {
-        if (nrb == 1) permute_kernel<3, 1><<<grid, 256, 0, st>>>(N, perm, xs, w, nr, sig, rec);
-        else permute_kernel<3, 8><<<grid, 256, 0, st>>>(N, perm, xs, w, nr, sig, rec);
+        if (nrb == 1) permute_kernel<3, 1><<<grid, 256, 0, st>>>(N, perm, xs, w, nr, sig, pt_sig, rec);
+        else permute_kernel<3, 8><<<grid, 256, 0, st>>>(N, perm, xs, w, nr, sig, pt_sig, rec);
     } else {
-        if (nrb == 1) permute_kernel<4, 1><<<grid, 256, 0, st>>>(N, perm, xs, w, nr, sig, rec);
-        else permute_kernel<4, 8><<<grid, 256, 0, st>>>(N, perm, xs, w, nr, sig, rec);
+        if (nrb == 1) permute_kernel<4, 1><<<grid, 256, 0, st>>>(N, perm, xs, w, nr, sig, pt_sig, rec);
+        else permute_kernel<4, 8><<<grid, 256, 0, st>>>(N, perm, xs, w, nr, sig, pt_sig, rec);
     }
 }
 
@@ -118,6 +118,10 @@ MvmArgs base_args(fkt_plan_s* P) {
     a.s2m_item_off = P->s2m_item_off;
     a.nnodes = P->nnodes;
     a.err = P->d_err;
+    a.kps = P->kps;
+    a.blk_prob = P->blk_prob;
+    a.blk_list = nullptr;
+    a.pt_sig = P->pt_sig;
     return a;
 }
 
@@ -130,6 +134,22 @@ __global__ void dense_lists_kernel(int64_t nblocks, int64_t* off, int2* ent) {
 }
 
 }  // namespace
+
+// Near field of every target block: one launch, or for a batch one launch per kernel kind over
+// that kind's blocks (largest first, so uneven problems balance across the SMs).
+void launch_near_stage(fkt_plan_s* P, MvmArgs& a, int nrb, int tpt, cudaStream_t st) {
+    if (P->nprob == 0) {
+        a.blk_list = nullptr;
+        launch_near(P->d, nrb, tpt, P->kernel.kind, (unsigned)P->nblocks, st, a, P->kp);
+        return;
+    }
+    for (size_t i = 0; i < P->kind_list.size(); ++i) {
+        if (P->kind_list_n[i] == 0) continue;
+        a.blk_list = P->kind_list[i];
+        launch_near(P->d, nrb, tpt, P->kind_of_list[i], (unsigned)P->kind_list_n[i], st, a, P->kp);
+    }
+    a.blk_list = P->far_list;  // the far stage that follows walks all blocks, most work first
+}
 
 // Right-hand sides per pass of the s2m / near kernels: 1 for a single right-hand side on the
 // float32 far path, 8 otherwise (the tensor-core far field always consumes groups of 8).
@@ -203,7 +223,7 @@ int run_mvm(fkt_plan_s* P, const MvmBuffers& B, const float* w, float* y, int nr
         a.y = y + (size_t)g * nrb * N;
         a.nr = nr;
         launch_permute(P->d, nrb, (unsigned)((N + 255) / 256), st, N, P->perm, P->xs, w + (size_t)g * nrb * N, nr,
-                       P->kp.sig, rec);
+                       P->kp.sig, P->pt_sig, rec);
         FKT_CUDA_TRY(cudaGetLastError());
         // fork: s2m on the second stream while the near field runs on the plan stream
         FKT_CUDA_TRY(cudaEventRecord(P->ev[1], st));
@@ -215,7 +235,7 @@ int run_mvm(fkt_plan_s* P, const MvmBuffers& B, const float* w, float* y, int nr
         if (timing) FKT_CUDA_TRY(cudaEventRecord(P->ev[3], st2));
         FKT_CUDA_TRY(cudaEventRecord(P->ev[4], st2));
         if (timing) FKT_CUDA_TRY(cudaEventRecord(P->ev[5], st));
-        launch_near(P->d, nrb, P->near_tpt, P->kernel.kind, (unsigned)P->nblocks, st, a, P->kp);
+        launch_near_stage(P, a, nrb, P->near_tpt, st);
         FKT_CUDA_TRY(cudaGetLastError());
         if (timing) FKT_CUDA_TRY(cudaEventRecord(P->ev[6], st));
         FKT_CUDA_TRY(cudaStreamWaitEvent(st, P->ev[4], 0));  // join
@@ -268,7 +288,7 @@ static int run_mvm_tc(fkt_plan_s* P, const MvmBuffers& B, const float* w, float*
             a.part = B.part + (size_t)g * 8 * NT * items;
             a.nr = nr;
             launch_permute(P->d, 8, (unsigned)((N + 255) / 256), st, N, P->perm, P->xs, w + (size_t)g * 8 * N, nr,
-                           P->kp.sig, rec);
+                           P->kp.sig, P->pt_sig, rec);
             FKT_CUDA_TRY(cudaGetLastError());
             FKT_CUDA_TRY(cudaEventRecord(P->ev[1], st));
             FKT_CUDA_TRY(cudaStreamWaitEvent(st2, P->ev[1], 0));
@@ -278,7 +298,7 @@ static int run_mvm_tc(fkt_plan_s* P, const MvmBuffers& B, const float* w, float*
             if (rc) return rc;
             if (timing) FKT_CUDA_TRY(cudaEventRecord(P->ev[3], st2));
             if (timing && r0 == 0 && gi == 0) FKT_CUDA_TRY(cudaEventRecord(P->ev[5], st));
-            launch_near(P->d, 8, 2, P->kernel.kind, (unsigned)P->nblocks, st, a, P->kp);
+            launch_near_stage(P, a, 8, 2, st);
             FKT_CUDA_TRY(cudaGetLastError());
             if (timing) FKT_CUDA_TRY(cudaEventRecord(P->ev[6], st));
         }
@@ -329,8 +349,8 @@ int launch_dense(fkt_plan_s* P, const float* w, float* y, int nrhs) {
         float4* rec = P->rec + (size_t)g * rec_group;
         a.rec = rec;
         a.ynear = P->ynear + (size_t)g * nrb * N;
-        launch_permute(P->d, nrb, pg, st, N, P->perm, P->xs, w + (size_t)g * nrb * N, nr, P->kp.sig, rec);
-        launch_near(P->d, nrb, P->near_tpt, P->kernel.kind, (unsigned)P->nblocks, st, a, P->kp);
+        launch_permute(P->d, nrb, pg, st, N, P->perm, P->xs, w + (size_t)g * nrb * N, nr, P->kp.sig, P->pt_sig, rec);
+        launch_near_stage(P, a, nrb, P->near_tpt, st);
         unpermute_kernel<><<<pg, 256, 0, st>>>(N, nr, P->perm, a.ynear, y + (size_t)g * nrb * N);
         FKT_CUDA_TRY(cudaGetLastError());
     }

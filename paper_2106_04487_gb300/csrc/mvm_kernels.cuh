@@ -18,11 +18,13 @@ namespace fkt {
 // with distances already in the kernel's own units (see kval).
 template <int D, int NR>
 __global__ void permute_kernel(int64_t N, const int32_t* __restrict__ perm, const float4* __restrict__ xs,
-                               const float* __restrict__ w, int nr, float sig, float4* __restrict__ rec) {
+                               const float* __restrict__ w, int nr, float sig_all, const float* __restrict__ pt_sig,
+                               float4* __restrict__ rec) {
     using R = Rec<D, NR>;
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= N) return;
     const int64_t j = perm[i];
+    const float sig = pt_sig ? pt_sig[i] : sig_all;
     float v[R::F4 * 4];
     const float4 x = xs[i];
     v[0] = x.x * sig; v[1] = x.y * sig; v[2] = x.z * sig; v[3] = x.w * sig;
@@ -194,14 +196,15 @@ struct NearShape {
 // streamed through shared memory by the bulk-copy engine (3-stage mbarrier ring, issued by
 // thread 0) and each thread accumulates K(|x_t - x_s|) w_s for its two targets.
 template <int D, int KIND, int NR, int T>
-__global__ void __launch_bounds__(NearShape<D, NR, T>::THREADS) near_kernel(MvmArgs a, KernelParams kp) {
+__global__ void __launch_bounds__(NearShape<D, NR, T>::THREADS) near_kernel(MvmArgs a, KernelParams kp_all) {
     using R = Rec<D, NR>;
     using Sh = NearShape<D, NR, T>;
     constexpr int F4 = R::F4, CH = Sh::CH, ST = Sh::ST, NTH = Sh::THREADS;
     __shared__ __align__(128) float4 buf[ST][CH * F4];
     __shared__ __align__(8) uint64_t full[ST];
     const int tl = threadIdx.x;
-    const int64_t blk = blockIdx.x;
+    const int64_t blk = cta_block(a);
+    const KernelParams kp = block_params(a, blk, kp_all);
     const int2 rg = a.blk[blk];
     float tx[T][4];
     bool valid[T];
@@ -332,7 +335,7 @@ struct FarShape {
 };
 
 template <int D, int P, int NR>
-__global__ void __launch_bounds__(kTB) far_kernel(MvmArgs a, KernelParams kp, const __grid_constant__ FarTables T) {
+__global__ void __launch_bounds__(kTB) far_kernel(MvmArgs a, KernelParams kp_all, const __grid_constant__ FarTables T) {
     using Lay = Layout<D, P>;
     using Sh = FarShape<D, P, NR>;
     constexpr int NT = Sh::NT, FB = Sh::FB;
@@ -340,7 +343,8 @@ __global__ void __launch_bounds__(kTB) far_kernel(MvmArgs a, KernelParams kp, co
     __shared__ float4 s_c[FB];
     __shared__ float s_s[FB];
     __shared__ int s_m[FB];
-    const int64_t blk = blockIdx.x;
+    const int64_t blk = cta_block(a);
+    const KernelParams kp = block_params(a, blk, kp_all);
     const int2 rg = a.blk[blk];
     const int tl = threadIdx.x;
     const int t = rg.x + tl;
@@ -425,7 +429,7 @@ struct FarMrShape {
 };
 
 template <int D, int P>
-__global__ void __launch_bounds__(kTB) far_mr_kernel(MvmArgs a, KernelParams kp, const __grid_constant__ FarTables T) {
+__global__ void __launch_bounds__(kTB) far_mr_kernel(MvmArgs a, KernelParams kp_all, const __grid_constant__ FarTables T) {
     using Lay = Layout<D, P>;
     constexpr int NT = Lay::nterms, ROW = FarMrShape<D, P>::ROW;
     extern __shared__ float sm[];
@@ -434,7 +438,8 @@ __global__ void __launch_bounds__(kTB) far_mr_kernel(MvmArgs a, KernelParams kp,
     __shared__ float4 s_c;
     __shared__ float s_s;
     __shared__ int s_m;
-    const int64_t blk = blockIdx.x;
+    const int64_t blk = cta_block(a);
+    const KernelParams kp = block_params(a, blk, kp_all);
     const int2 rg = a.blk[blk];
     const int tl = threadIdx.x;
     const int t = rg.x + tl;

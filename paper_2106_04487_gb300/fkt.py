@@ -24,7 +24,8 @@ KERNELS = {"gaussian": 0, "exponential": 1, "matern32": 2, "matern52": 3, "cauch
 # Every entry point declared in include/fkt.h.
 EXPORTS = ["fkt_plan", "fkt_mvm", "fkt_mvm_host", "fkt_dense_mvm", "fkt_set_option", "fkt_plan_stats",
            "fkt_plan_tree", "fkt_plan_lists", "fkt_destroy", "fkt_error_string", "fkt_mvm_noalloc",
-           "fkt_check", "fkt_precond_setup", "fkt_precond_apply", "fkt_solve"]
+           "fkt_check", "fkt_precond_setup", "fkt_precond_apply", "fkt_solve", "fkt_batch_plan", "fkt_batch_mvm",
+           "fkt_batch_set_option", "fkt_batch_info", "fkt_batch_check", "fkt_batch_destroy", "fkt_autotune_leaf"]
 
 
 class FktError(RuntimeError):
@@ -41,6 +42,10 @@ class fkt_kernel(ctypes.Structure):
 class fkt_solve_info(ctypes.Structure):
     _fields_ = [("iterations", ctypes.c_int), ("converged", ctypes.c_int), ("used_fallback", ctypes.c_int),
                 ("pad", ctypes.c_int), ("rel_residual", ctypes.c_double), ("true_rel_residual", ctypes.c_double)]
+
+
+class fkt_problem(ctypes.Structure):
+    _fields_ = [("points", ctypes.c_void_p), ("N", ctypes.c_int64), ("kernel", fkt_kernel)]
 
 
 class fkt_stats(ctypes.Structure):
@@ -76,6 +81,16 @@ def lib() -> ctypes.CDLL:
     L.fkt_plan_tree.argtypes = [vp] + [vp] * 8
     L.fkt_plan_lists.argtypes = [vp] + [vp] * 8
     L.fkt_check.argtypes = [vp]
+    L.fkt_batch_plan.argtypes = [ctypes.c_int, ctypes.POINTER(fkt_problem), ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                 ctypes.c_double, vp, ctypes.POINTER(vp)]
+    L.fkt_batch_mvm.argtypes = [vp, vp, vp, ctypes.c_int]
+    L.fkt_batch_set_option.argtypes = [vp, ctypes.c_char_p, ctypes.c_char_p]
+    L.fkt_batch_info.argtypes = [vp, vp, vp, ctypes.POINTER(fkt_stats)]
+    L.fkt_batch_check.argtypes = [vp]
+    L.fkt_batch_destroy.argtypes = [vp]
+    L.fkt_batch_destroy.restype = None
+    L.fkt_autotune_leaf.argtypes = [vp, i64, ctypes.c_int, fkt_kernel, ctypes.c_int, ctypes.c_double, ctypes.c_int, vp,
+                                    ctypes.c_int, vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)]
     L.fkt_precond_setup.argtypes = [vp, ctypes.c_double]
     L.fkt_precond_apply.argtypes = [vp, vp, vp, ctypes.c_int]
     L.fkt_solve.argtypes = [vp, ctypes.c_double, vp, vp, ctypes.c_int, ctypes.c_double, ctypes.c_int,
@@ -308,3 +323,62 @@ class Plan:
                         if m < 0 or (L["masks"][m][i >> 5] >> np.uint32(i & 31)) & np.uint32(1):
                             dst[t].append(int(ids[e]))
         return far, near
+
+
+def fkt_autotune_leaf(points, kernel: fkt_kernel, p: int, theta: float, nrhs: int = 8, candidates=(64, 128, 256, 512),
+                      stream=None):
+    """(best leaf size, its MVM time in ms) among the candidates, timed on the device."""
+    N, d = points.shape
+    cand = np.asarray(candidates, dtype=np.int32)
+    best = ctypes.c_int()
+    ms = ctypes.c_double()
+    _check(lib().fkt_autotune_leaf(_ptr(points), N, d, kernel, p, float(theta), nrhs, _ptr(cand), len(cand),
+                                   _stream_ptr(stream), ctypes.byref(best), ctypes.byref(ms)), "fkt_autotune_leaf")
+    return best.value, ms.value
+
+
+class Batch:
+    """Independent problems [(points [N_i][d], kernel, lengthscale, alpha, scale), ...] sharing d, p, theta."""
+
+    def __init__(self, problems, p: int = 4, leaf_size: int = 512, theta: float = 0.5, stream=None):
+        import torch
+
+        self.points = [torch.as_tensor(x).to(device="cuda", dtype=torch.float32).contiguous() for x, *_ in problems]
+        arr = (fkt_problem * len(problems))()
+        for i, (x, *k) in enumerate(problems):
+            arr[i] = fkt_problem(self.points[i].data_ptr(), self.points[i].shape[0], make_kernel(*k))
+        d = self.points[0].shape[1]
+        self.h = ctypes.c_void_p()
+        _check(lib().fkt_batch_plan(len(problems), arr, d, p, leaf_size, float(theta), _stream_ptr(stream),
+                                    ctypes.byref(self.h)), "fkt_batch_plan")
+        n = len(problems)
+        self.offsets = np.zeros(n + 1, np.int64)
+        self.leaf_sizes = np.zeros(n, np.int32)
+        st = fkt_stats()
+        _check(lib().fkt_batch_info(self.h, _ptr(self.offsets), _ptr(self.leaf_sizes), ctypes.byref(st)),
+               "fkt_batch_info")
+        self.totals = {k: getattr(st, k) for k, _ in fkt_stats._fields_}
+        self.N = int(self.offsets[-1])
+
+    def mvm(self, w, out=None):
+        """w: CUDA float32 [nrhs][N_total]; returns y of the same shape."""
+        y = out if out is not None else w.new_empty(w.shape)
+        _check(lib().fkt_batch_mvm(self.h, _ptr(w), _ptr(y), w.shape[0]), "fkt_batch_mvm")
+        return y
+
+    def set_option(self, key: str, value: str):
+        _check(lib().fkt_batch_set_option(self.h, key.encode(), value.encode()), "fkt_batch_set_option")
+
+    def check(self):
+        _check(lib().fkt_batch_check(self.h), "fkt_batch_check")
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().fkt_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
