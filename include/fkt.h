@@ -157,6 +157,59 @@ int fkt_precond_setup(fkt_plan_t plan, double sigma2);
  * caller's order, 1 <= nrhs <= 64.  FKT_ERR_INVALID_ARG if no preconditioner is set up. */
 int fkt_precond_apply(fkt_plan_t plan, const float* r, float* z, int nrhs);
 
+/* ---- Learned low-rank correction of the block-Jacobi preconditioner ----
+ * For each target block b (points X_b) with neighbourhood y = up to 32 trailing points of block
+ * b-1 and 32 leading points of block b+1 (neighbours in tree order), the teacher is the coupling of
+ * the block to its neighbours folded into the block,
+ *     T_b = A_by A_yy^{-1} A_yb  (positive semidefinite),  A = K + sigma2 I,
+ * so that the corrected block A_bb + T_b acts on locally smooth vectors like the rows of A do
+ * (the idea behind lumping dropped couplings into the diagonal in modified incomplete
+ * factorisations).  A small network maps the block's points and its neighbours' points (relative
+ * to the block's centroid, divided by the lengthscale) to V_b (n_b x rank):
+ *     phi(u) = tanh(W2^T tanh(W1^T u + b1) + b2)                      (per point, width H)
+ *     g = mean_{i in X_b} phi(u_i),  h = mean_{j in neighbours} phi(u_j)
+ *     V_i = Wo^T [phi(u_i); g; h] + bo,
+ * trained on the GPU (hand-written forward/backward kernels, Adam) to minimise
+ *     L = sum_b |beta^2 V_b V_b^T - T_b|_F^2 / sum_b |T_b|_F^2
+ * over a subset of blocks.  The preconditioner block is (A_bb + beta^2 V_b V_b^T)^{-1}, a rank-r
+ * update of the block-Jacobi block, symmetric positive definite by construction.  Parameters are
+ * one flat float32 vector: W1 [d][H], b1 [H], W2 [H][H], b2 [H], Wo [3H][rank], bo [rank], beta. */
+typedef struct {
+    int rank;          /* columns of V_b, 1..16 (default 8) */
+    int hidden;        /* H, 8..64 (default 32) */
+    int steps;         /* Adam steps (default 300) */
+    float lr;          /* Adam learning rate (default 3e-3) */
+    int train_blocks;  /* blocks used for training, every (nblocks / train_blocks)-th (default 512) */
+    int seed;          /* initialisation seed */
+    int install_teacher;  /* 1: install (A_bb + T_b)^{-1} itself (every block must be a training block,
+                             train_blocks >= blocks): the target the network approximates, for
+                             comparison; 0 (default): the network's correction */
+} fkt_learn_opts;
+
+typedef struct {
+    int nparams;
+    int ntrain;                 /* training blocks */
+    double loss_initial;        /* L at the initial parameters */
+    double loss_final;          /* L after training */
+    double train_ms;            /* teacher generation + training + installation */
+} fkt_learn_info;
+
+/* Build the teacher data for sigma2, train the network, compute V_b for every block and install
+ * the corrected preconditioner (used by fkt_solve with option "preconditioner" = "learned").
+ * opts may be NULL for the defaults.  Synchronizes. */
+int fkt_precond_learn(fkt_plan_t plan, double sigma2, const fkt_learn_opts* opts, fkt_learn_info* info);
+
+/* The trained parameters (host, *nparams floats).  params may be NULL to query *nparams. */
+int fkt_learn_params(fkt_plan_t plan, float* params, int* nparams);
+
+/* Loss L and its gradient at the given parameters (host buffers of nparams floats) on the
+ * training blocks of the last fkt_precond_learn, computed by the GPU forward/backward kernels. */
+int fkt_learn_eval(fkt_plan_t plan, const float* params, double* loss, float* grad);
+
+/* The training blocks' indices (host [ntrain]) and their teachers T_b (host [ntrain][128][128],
+ * rows and columns beyond the block's size are zero).  Either pointer may be NULL. */
+int fkt_learn_teacher(fkt_plan_t plan, int64_t* blocks, float* D);
+
 /* Solve (Ktilde + sigma2 I) x = b.  b, x device [nrhs][N] float32 (x is output only),
  * 1 <= nrhs <= 64, sigma2 > 0, 0 < tol < 1, max_iter >= 1.  Synchronizes.
  * Returns FKT_OK when every right-hand side reached |r| <= tol |b|, FKT_ERR_NOT_CONVERGED
@@ -213,7 +266,9 @@ int fkt_autotune_leaf(const float* points, int64_t N, int d, fkt_kernel kernel, 
  *               float32 accumulation in tensor memory) with operands in TF32, BF16, or BF16
  *               split into hi + lo parts (three products, about 16 significant bits); the
  *               near field always stays float32.  Right-hand sides go 32 per pass.
- *   "preconditioner" "block_jacobi" (default) | "none"   preconditioner of fkt_solve
+ *   "preconditioner" "block_jacobi" (default) | "learned" | "none"   preconditioner of fkt_solve;
+ *               "learned" needs fkt_precond_learn first and falls back to block_jacobi when
+ *               CG with the correction does not converge (fkt_solve_info.used_fallback)
  *   "near_targets_per_thread"  "2" (default) | "4"  register blocking of the near-field kernel
  *               (4 applies to one right-hand side; results are identical up to rounding order)
  * Errors: FKT_ERR_INVALID_ARG for an unknown key or value. */

@@ -28,6 +28,7 @@ void free_plan(fkt_plan_s* P) {
                     P->d_err, P->dense_off, P->dense_ent};
     for (void* b : bufs)
         if (b) cudaFree(b);
+    fkt::free_learn(P);
     fkt::free_solve(P);
     fkt::free_batch_arrays(P);
     for (auto& e : P->ev)
@@ -169,6 +170,27 @@ int fkt_solve(fkt_plan_t plan, double sigma2, const float* b, float* x, int nrhs
     return fkt::solve(plan, sigma2, b, x, nrhs, tol, max_iter, info);
 }
 
+int fkt_precond_learn(fkt_plan_t plan, double sigma2, const fkt_learn_opts* opts, fkt_learn_info* info) {
+    if (info) memset(info, 0, sizeof(*info));
+    if (!plan || !(sigma2 > 0.0) || !isfinite(sigma2)) return FKT_ERR_INVALID_ARG;
+    return fkt::precond_learn(plan, sigma2, opts, info);
+}
+
+int fkt_learn_params(fkt_plan_t plan, float* params, int* nparams) {
+    if (!plan || !nparams) return FKT_ERR_INVALID_ARG;
+    return fkt::learn_params(plan, params, nparams);
+}
+
+int fkt_learn_eval(fkt_plan_t plan, const float* params, double* loss, float* grad) {
+    if (!plan || !params) return FKT_ERR_INVALID_ARG;
+    return fkt::learn_eval(plan, params, loss, grad);
+}
+
+int fkt_learn_teacher(fkt_plan_t plan, int64_t* blocks, float* D) {
+    if (!plan) return FKT_ERR_INVALID_ARG;
+    return fkt::learn_teacher(plan, blocks, D);
+}
+
 int fkt_set_option(fkt_plan_t plan, const char* key, const char* value) {
     if (!plan || !key || !value) return FKT_ERR_INVALID_ARG;
     if (!strcmp(key, "timing")) {
@@ -180,6 +202,7 @@ int fkt_set_option(fkt_plan_t plan, const char* key, const char* value) {
     if (!strcmp(key, "preconditioner")) {
         if (!strcmp(value, "none")) plan->pc_mode = 0;
         else if (!strcmp(value, "block_jacobi")) plan->pc_mode = 1;
+        else if (!strcmp(value, "learned")) plan->pc_mode = 2;
         else return FKT_ERR_INVALID_ARG;
         return FKT_OK;
     }

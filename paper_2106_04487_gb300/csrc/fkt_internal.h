@@ -109,7 +109,10 @@ struct fkt_plan_s {
     int2* dense_ent = nullptr;
     // block-Jacobi preconditioner: inverse of K(X_b, X_b) + sigma2 I per target block
     double pc_sigma2 = -1.0;       // sigma2 the inverses were built for (< 0: none)
-    int pc_mode = 1;               // 0: no preconditioner (z = r), 1: block-Jacobi
+    int pc_mode = 1;               // 0: no preconditioner (z = r), 1: block-Jacobi, 2: learned correction
+    void* learn = nullptr;         // learned-correction state (learn.cu)
+    float* pc_learned = nullptr;   // [blocks][kTB][kTB]: A_bb^{-1} + beta^2 V_b V_b^T
+    double pc_learned_sigma2 = -1.0;
     float* pc_inv = nullptr;       // [blocks][kTB][kTB], symmetric
     // CG work space (grown on demand)
     int cg_cap = 0;
@@ -174,10 +177,18 @@ int free_batch_arrays(fkt_plan_s* P);
 
 // solve.cu
 int precond_setup(fkt_plan_s* P, double sigma2);
+int precond_build(fkt_plan_s* P, double sigma2, const float* addV, int R, const float* addT, float* out);
 int precond_apply(fkt_plan_s* P, const float* r, const double* r64, float* z, int nrhs);
 int solve(fkt_plan_s* P, double sigma2, const float* b, float* x, int nrhs, double tol, int max_iter,
           fkt_solve_info* info);
 void free_solve(fkt_plan_s* P);
+
+// learn.cu
+int precond_learn(fkt_plan_s* P, double sigma2, const fkt_learn_opts* opts, fkt_learn_info* info);
+int learn_params(fkt_plan_s* P, float* out, int* nparams);
+int learn_eval(fkt_plan_s* P, const float* params, double* loss, float* grad);
+int learn_teacher(fkt_plan_s* P, int64_t* blocks, float* D);
+void free_learn(fkt_plan_s* P);
 
 }  // namespace fkt
 

@@ -36,11 +36,13 @@ __device__ float kernel_any(int kind, float q, const KernelParams& kp) {
     }
 }
 
-// One CTA per target block: A = K(X_b, X_b) + sigma2 I, A = L L^T, A^{-1} = L^{-T} L^{-1}.
-// Singular kernels have no finite diagonal; there K(0) is taken as 0 (the r = 0 rule).
+// One CTA per target block: A = K(X_b, X_b) + sigma2 I (+ a correction: V V^T from addV, rank R,
+// or a full matrix addT), A = L L^T, A^{-1} = L^{-T} L^{-1}.  Singular kernels have no finite
+// diagonal; there K(0) is taken as 0 (the r = 0 rule).
 __global__ void __launch_bounds__(kPcThreads)
 precond_setup_kernel(const int2* __restrict__ blk, const float4* __restrict__ xs, KernelParams kp, float sigma2,
-                     float* __restrict__ inv, int* err) {
+                     const float* __restrict__ addV, int R, const float* __restrict__ addT, float* __restrict__ inv,
+                     int* err) {
     extern __shared__ float sm[];
     float* A = sm;                  // [kTB][kPcLd], lower triangle = L after the factorisation
     float* Li = sm + kTB * kPcLd;   // [kTB][kPcLd], L^{-1}
@@ -61,6 +63,11 @@ precond_setup_kernel(const int2* __restrict__ blk, const float4* __restrict__ xs
         const float q = dx * dx + dy * dy + dz * dz + dw * dw;
         float v = kernel_any(kp.kind, q, kp);
         if (i == j) v = (kp.kind == FKT_LAPLACE ? 0.f : v) + sigma2;
+        if (addV) {
+            const float* vb = addV + (int64_t)blockIdx.x * kTB * R;
+            for (int r = 0; r < R; ++r) v = fmaf(vb[i * R + r], vb[j * R + r], v);
+        }
+        if (addT) v += addT[(int64_t)blockIdx.x * kTB * kTB + i * kTB + j];
         A[i * kPcLd + j] = v;
     }
     __syncthreads();
@@ -252,23 +259,30 @@ void free_solve(fkt_plan_s* P) {
     P->pc_sigma2 = -1.0;
 }
 
-int precond_setup(fkt_plan_s* P, double sigma2) {
-    if (!(sigma2 > 0.0) || !isfinite(sigma2)) return FKT_ERR_INVALID_ARG;
-    if (P->pc_inv && P->pc_sigma2 == sigma2) return FKT_OK;
-    if (!P->pc_inv) FKT_CUDA_TRY(cudaMalloc(&P->pc_inv, sizeof(float) * kTB * kTB * P->nblocks));
+int precond_build(fkt_plan_s* P, double sigma2, const float* addV, int R, const float* addT, float* out) {
     const size_t smem = sizeof(float) * 2 * kTB * kPcLd;
     FKT_CUDA_TRY(cudaFuncSetAttribute(precond_setup_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     precond_setup_kernel<<<(unsigned)P->nblocks, kPcThreads, smem, P->stream>>>(P->blk_range, P->xs, P->kp,
-                                                                                (float)sigma2, P->pc_inv, P->d_err);
+                                                                                (float)sigma2, addV, R, addT, out,
+                                                                                P->d_err);
     FKT_CUDA_TRY(cudaGetLastError());
     FKT_CUDA_TRY(cudaStreamSynchronize(P->stream));
     int h = 0;
     FKT_CUDA_TRY(cudaMemcpy(&h, P->d_err, sizeof(int), cudaMemcpyDeviceToHost));
     if (h == 2) {  // a block was not positive definite in float32
         FKT_CUDA_TRY(cudaMemset(P->d_err, 0, sizeof(int)));
-        P->pc_sigma2 = -1.0;
         return FKT_ERR_INVALID_ARG;
     }
+    return FKT_OK;
+}
+
+int precond_setup(fkt_plan_s* P, double sigma2) {
+    if (!(sigma2 > 0.0) || !isfinite(sigma2)) return FKT_ERR_INVALID_ARG;
+    if (P->pc_inv && P->pc_sigma2 == sigma2) return FKT_OK;
+    if (!P->pc_inv) FKT_CUDA_TRY(cudaMalloc(&P->pc_inv, sizeof(float) * kTB * kTB * P->nblocks));
+    P->pc_sigma2 = -1.0;
+    const int rc = precond_build(P, sigma2, nullptr, 0, nullptr, P->pc_inv);
+    if (rc) return rc;
     P->pc_sigma2 = sigma2;
     return FKT_OK;
 }
@@ -282,18 +296,40 @@ int precond_apply(fkt_plan_s* P, const float* r, const double* r64, float* z, in
         return FKT_OK;
     }
     if (!P->pc_inv || P->pc_sigma2 < 0) return FKT_ERR_INVALID_ARG;
+    const float* inv = P->pc_inv;
+    if (P->pc_mode == 2) {
+        if (!P->pc_learned || P->pc_learned_sigma2 != P->pc_sigma2) return FKT_ERR_INVALID_ARG;
+        inv = P->pc_learned;
+    }
     for (int g = 0; g < nrhs; g += 8) {
         const int nr = std::min(8, nrhs - g);
         precond_apply_kernel<<<(unsigned)P->nblocks, kTB, 0, P->stream>>>(
-            P->blk_range, P->perm, P->pc_inv, P->N, nr, r ? r + (size_t)g * P->N : nullptr,
+            P->blk_range, P->perm, inv, P->N, nr, r ? r + (size_t)g * P->N : nullptr,
             r64 ? r64 + (size_t)g * P->N : nullptr, z + (size_t)g * P->N);
         FKT_CUDA_TRY(cudaGetLastError());
     }
     return FKT_OK;
 }
 
+static int solve_once(fkt_plan_s* P, double sigma2, const float* b, float* x, int nrhs, double tol, int max_iter,
+                      fkt_solve_info* info);
+
+// With the learned correction, a run that does not converge is repeated with plain block-Jacobi.
 int solve(fkt_plan_s* P, double sigma2, const float* b, float* x, int nrhs, double tol, int max_iter,
           fkt_solve_info* info) {
+    if (P->pc_mode != 2) return solve_once(P, sigma2, b, x, nrhs, tol, max_iter, info);
+    if (!P->pc_learned || P->pc_learned_sigma2 != sigma2) return FKT_ERR_INVALID_ARG;
+    int rc = solve_once(P, sigma2, b, x, nrhs, tol, max_iter, info);
+    if (rc != FKT_ERR_NOT_CONVERGED) return rc;
+    P->pc_mode = 1;
+    rc = solve_once(P, sigma2, b, x, nrhs, tol, max_iter, info);
+    P->pc_mode = 2;
+    if (info) info->used_fallback = 1;
+    return rc;
+}
+
+static int solve_once(fkt_plan_s* P, double sigma2, const float* b, float* x, int nrhs, double tol, int max_iter,
+                      fkt_solve_info* info) {
     int rc = P->pc_mode ? precond_setup(P, sigma2) : FKT_OK;
     if (rc) return rc;
     const int64_t N = P->N;
@@ -377,7 +413,6 @@ int solve(fkt_plan_s* P, double sigma2, const float* b, float* x, int nrhs, doub
     if (info) {
         info->iterations = it;
         info->converged = all_conv ? 1 : 0;
-        info->used_fallback = 0;
         info->rel_residual = worst;
         info->true_rel_residual = true_worst;
     }

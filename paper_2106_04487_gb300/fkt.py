@@ -25,7 +25,8 @@ KERNELS = {"gaussian": 0, "exponential": 1, "matern32": 2, "matern52": 3, "cauch
 EXPORTS = ["fkt_plan", "fkt_mvm", "fkt_mvm_host", "fkt_dense_mvm", "fkt_set_option", "fkt_plan_stats",
            "fkt_plan_tree", "fkt_plan_lists", "fkt_destroy", "fkt_error_string", "fkt_mvm_noalloc",
            "fkt_check", "fkt_precond_setup", "fkt_precond_apply", "fkt_solve", "fkt_batch_plan", "fkt_batch_mvm",
-           "fkt_batch_set_option", "fkt_batch_info", "fkt_batch_check", "fkt_batch_destroy", "fkt_autotune_leaf"]
+           "fkt_batch_set_option", "fkt_batch_info", "fkt_batch_check", "fkt_batch_destroy", "fkt_autotune_leaf",
+           "fkt_precond_learn", "fkt_learn_params", "fkt_learn_eval", "fkt_learn_teacher"]
 
 
 class FktError(RuntimeError):
@@ -42,6 +43,16 @@ class fkt_kernel(ctypes.Structure):
 class fkt_solve_info(ctypes.Structure):
     _fields_ = [("iterations", ctypes.c_int), ("converged", ctypes.c_int), ("used_fallback", ctypes.c_int),
                 ("pad", ctypes.c_int), ("rel_residual", ctypes.c_double), ("true_rel_residual", ctypes.c_double)]
+
+
+class fkt_learn_opts(ctypes.Structure):
+    _fields_ = [("rank", ctypes.c_int), ("hidden", ctypes.c_int), ("steps", ctypes.c_int), ("lr", ctypes.c_float),
+                ("train_blocks", ctypes.c_int), ("seed", ctypes.c_int), ("install_teacher", ctypes.c_int)]
+
+
+class fkt_learn_info(ctypes.Structure):
+    _fields_ = [("nparams", ctypes.c_int), ("ntrain", ctypes.c_int), ("loss_initial", ctypes.c_double),
+                ("loss_final", ctypes.c_double), ("train_ms", ctypes.c_double)]
 
 
 class fkt_problem(ctypes.Structure):
@@ -81,6 +92,10 @@ def lib() -> ctypes.CDLL:
     L.fkt_plan_tree.argtypes = [vp] + [vp] * 8
     L.fkt_plan_lists.argtypes = [vp] + [vp] * 8
     L.fkt_check.argtypes = [vp]
+    L.fkt_precond_learn.argtypes = [vp, ctypes.c_double, ctypes.POINTER(fkt_learn_opts), ctypes.POINTER(fkt_learn_info)]
+    L.fkt_learn_params.argtypes = [vp, vp, ctypes.POINTER(ctypes.c_int)]
+    L.fkt_learn_eval.argtypes = [vp, vp, ctypes.POINTER(ctypes.c_double), vp]
+    L.fkt_learn_teacher.argtypes = [vp, vp, vp]
     L.fkt_batch_plan.argtypes = [ctypes.c_int, ctypes.POINTER(fkt_problem), ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                  ctypes.c_double, vp, ctypes.POINTER(vp)]
     L.fkt_batch_mvm.argtypes = [vp, vp, vp, ctypes.c_int]
@@ -272,6 +287,35 @@ class Plan:
         x = torch.empty_like(b2)
         info = fkt_solve(self.h, sigma2, b2, x, b2.shape[0], tol, max_iter, raise_on_not_converged)
         return (x if b.dim() == 2 else x[0]), info
+
+    def learn_precond(self, sigma2: float, rank=8, hidden=32, steps=300, lr=3e-3, train_blocks=512, seed=1,
+                      install_teacher=False) -> dict:
+        """Train the low-rank correction of the block-Jacobi preconditioner on the GPU and install it."""
+        o = fkt_learn_opts(rank, hidden, steps, lr, train_blocks, seed, int(install_teacher))
+        info = fkt_learn_info()
+        _check(lib().fkt_precond_learn(self.h, float(sigma2), ctypes.byref(o), ctypes.byref(info)), "fkt_precond_learn")
+        return {k: getattr(info, k) for k, _ in fkt_learn_info._fields_}
+
+    def learn_params(self) -> np.ndarray:
+        n = ctypes.c_int()
+        _check(lib().fkt_learn_params(self.h, None, ctypes.byref(n)), "fkt_learn_params")
+        out = np.zeros(n.value, np.float32)
+        _check(lib().fkt_learn_params(self.h, _ptr(out), ctypes.byref(n)), "fkt_learn_params")
+        return out
+
+    def learn_eval(self, params: np.ndarray):
+        """(loss, gradient) of the learning objective at params, computed by the GPU kernels."""
+        params = np.ascontiguousarray(params, dtype=np.float32)
+        loss = ctypes.c_double()
+        grad = np.zeros_like(params)
+        _check(lib().fkt_learn_eval(self.h, _ptr(params), ctypes.byref(loss), _ptr(grad)), "fkt_learn_eval")
+        return loss.value, grad
+
+    def learn_teacher(self, ntrain: int):
+        blocks = np.zeros(ntrain, np.int64)
+        D = np.zeros((ntrain, 128, 128), np.float32)
+        _check(lib().fkt_learn_teacher(self.h, _ptr(blocks), _ptr(D)), "fkt_learn_teacher")
+        return blocks, D
 
     def precond(self, sigma2: float, r):
         """z = M^{-1} r with the block-Jacobi preconditioner for sigma2."""
