@@ -312,11 +312,11 @@ int fkt_plan_lists(fkt_plan_t plan, int64_t* block_range, int64_t* far_off, int3
  *   plan, w, y, nrhs  as for fkt_mvm (device buffers, [nrhs][N], 1 <= nrhs <= 64).
  *
  * Limits and behaviour:
- *   - The array holds FKT_NOALLOC_SCRATCH_BYTES (32 MiB) and is part of the library image:
+ *   - The array holds FKT_NOALLOC_SCRATCH_BYTES (48 MiB) and is part of the library image:
  *     every GPU that loads libfkt.so holds it until the process exits.  A call with one
- *     right-hand side needs 4 * (5 N + nterms * (nodes + s2m chunks)) bytes, about 28 MB at
- *     N = 1M, d = 3, p = 6 (each part rounded up to 256 bytes); more right-hand sides need
- *     proportionally more.  Requests that do not fit return FKT_ERR_SCRATCH_LIMIT and
+ *     right-hand side needs 4 * (6 N + nterms * (nodes + s2m chunks)) bytes, about 35 MB at
+ *     N = 1M, d = 3, p = 6, leaf 256 (each part rounded up to 256 bytes); more right-hand
+ *     sides need proportionally more.  Requests that do not fit return FKT_ERR_SCRATCH_LIMIT and
  *     enqueue nothing.
  *   - The first call on a device looks up the array's device address (cudaGetSymbolAddress)
  *     with that device current; make that first call before any stream capture.
@@ -325,7 +325,7 @@ int fkt_plan_lists(fkt_plan_t plan, int64_t* block_range, int64_t* far_off, int3
  *     Calls whose GPU work overlaps (two streams, two plans, two host threads) race on the
  *     array and give wrong results; order them on one stream or synchronise between them.
  *   - Asynchronous on the plan's stream, like fkt_mvm. */
-#define FKT_NOALLOC_SCRATCH_BYTES (32u << 20)
+#define FKT_NOALLOC_SCRATCH_BYTES (48u << 20)
 int fkt_mvm_noalloc(fkt_plan_t plan, const float* w, float* y, int nrhs);
 
 /* Failure detection: synchronise the plan's stream, then report FKT_ERR_TIMEOUT if any

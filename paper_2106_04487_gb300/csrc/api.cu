@@ -24,7 +24,7 @@ void free_plan(fkt_plan_s* P) {
     void* bufs[] = {P->xs, P->perm, P->codes, P->nd_begin, P->nd_end, P->nd_level, P->nd_leaf, P->nd_child,
                     P->nd_centre, P->nd_rho2, P->nd_cf, P->nd_scale, P->nd_used, P->blk_range, P->far_off,
                     P->near_off, P->far_ent, P->near_ent, P->masks, P->s2m_items, P->s2m_node_items,
-                    P->s2m_item_off, P->rec, P->ynear, P->mult, P->s2m_part, P->tc_image, P->hbuf_w, P->hbuf_y,
+                    P->s2m_item_off, P->rec, P->ynear, P->yfar, P->mult, P->s2m_part, P->tc_image, P->hbuf_w, P->hbuf_y,
                     P->d_err, P->dense_off, P->dense_ent};
     for (void* b : bufs)
         if (b) cudaFree(b);
@@ -89,7 +89,7 @@ int fkt_plan(const float* points, int64_t N, int d, fkt_kernel kernel, int p, in
         for (int i = 1; i <= d; ++i) nt = nt * (p + i) / i;
         P->nterms = (int)nt;
     }
-    if (cudaStreamCreateWithFlags(&P->stream2, cudaStreamNonBlocking) != cudaSuccess) { free_plan(P); return FKT_ERR_CUDA; }
+    if (fkt::create_far_stream(&P->stream2) != FKT_OK) { free_plan(P); return FKT_ERR_CUDA; }
     for (auto& e : P->ev)
         if (cudaEventCreate(&e) != cudaSuccess) { free_plan(P); return FKT_ERR_CUDA; }
     if (cudaMalloc(&P->d_err, sizeof(int)) != cudaSuccess || cudaMemsetAsync(P->d_err, 0, sizeof(int), P->stream) != cudaSuccess) {

@@ -309,7 +309,7 @@ int fkt_batch_plan(int nprob, const fkt_problem* probs, int d, int p, int leaf_s
         M->kernel = probs[0].kernel;
         M->kp = plans[0]->kp;
         M->stream = (cudaStream_t)cuda_stream;
-        if (cudaStreamCreateWithFlags(&M->stream2, cudaStreamNonBlocking) != cudaSuccess) rc = FKT_ERR_CUDA;
+        if (fkt::create_far_stream(&M->stream2) != FKT_OK) rc = FKT_ERR_CUDA;
         for (auto& e : M->ev)
             if (!rc && cudaEventCreate(&e) != cudaSuccess) rc = FKT_ERR_CUDA;
         if (!rc && (cudaMalloc(&M->d_err, sizeof(int)) != cudaSuccess || cudaMemset(M->d_err, 0, sizeof(int)) != cudaSuccess))

@@ -34,8 +34,10 @@ struct TcShape {
     static constexpr int PLANES = PREC == TC_BF16X3 ? 2 : 1;        // hi (+ lo)
     static constexpr int A_BYTES = 128 * NTP * EL * PLANES;
     static constexpr int B_BYTES = kTcN * NTP * EL * PLANES;
-    static constexpr int STAGES = (2 * (A_BYTES + B_BYTES) <= 112 * 1024) ? 2 : 1;
-    static constexpr size_t smem_bytes() { return (size_t)STAGES * (A_BYTES + B_BYTES) + 128; }
+    // ROW: the target's whole basis row is kept in registers and written as 16-byte core rows
+    // (NTP <= 128); otherwise each term is stored as it is generated.
+    static constexpr bool ROW = NTP <= 128;
+    static constexpr size_t smem_bytes() { return (size_t)A_BYTES + 2 * (size_t)B_BYTES + 128; }
     static constexpr bool supported = smem_bytes() <= 200 * 1024;
     // byte offset of element (row, k) of one plane
     __host__ __device__ static constexpr int off(int row, int k) {
@@ -53,6 +55,36 @@ __device__ __forceinline__ void tc_store(unsigned char* plane0, int plane_bytes,
         if (PREC == TC_BF16X3)
             *reinterpret_cast<__nv_bfloat16*>(plane0 + plane_bytes + off) =
                 __float2bfloat16_rn(v - __bfloat162float(hi));
+    }
+}
+
+__device__ __forceinline__ uint32_t bf2_bits(__nv_bfloat162 v) {
+    uint32_t u;
+    memcpy(&u, &v, sizeof(u));
+    return u;
+}
+
+// One 16-byte core-matrix row (16 / elem consecutive terms) of one target: a single
+// conflict-free 16-byte shared store per plane.
+template <int PREC>
+__device__ __forceinline__ void tc_store_row16(unsigned char* plane0, int plane_bytes, int off, const float* u) {
+    if constexpr (PREC == TC_TF32) {
+        *reinterpret_cast<float4*>(plane0 + off) = make_float4(u[0], u[1], u[2], u[3]);
+    } else {
+        __nv_bfloat162 h[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) h[i] = __floats2bfloat162_rn(u[2 * i], u[2 * i + 1]);
+        *reinterpret_cast<uint4*>(plane0 + off) = make_uint4(bf2_bits(h[0]), bf2_bits(h[1]), bf2_bits(h[2]), bf2_bits(h[3]));
+        if constexpr (PREC == TC_BF16X3) {
+            __nv_bfloat162 l[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const float2 f = __bfloat1622float2(h[i]);
+                l[i] = __floats2bfloat162_rn(u[2 * i] - f.x, u[2 * i + 1] - f.y);
+            }
+            *reinterpret_cast<uint4*>(plane0 + plane_bytes + off) =
+                make_uint4(bf2_bits(l[0]), bf2_bits(l[1]), bf2_bits(l[2]), bf2_bits(l[3]));
+        }
     }
 }
 
@@ -75,19 +107,60 @@ __global__ void tc_pack_kernel(int64_t nnodes, const int64_t* __restrict__ item_
     }
 }
 
+// Basis of one (target, far node) pair: calls put(q, value) for every term q < NT, in
+// increasing q for D = 3.  U[t][q] = Yt_kh(x_t - c) (s/r)^j R_kj(r).
+template <int D, int P, class F>
+__device__ __forceinline__ void far_basis(const float4& xt, const float4& c, float s, const KernelParams& kp,
+                                          const FarTables& T, F&& put) {
+    using Lay = Layout<D, P>;
+    const float dx = xt.x - c.x, dy = xt.y - c.y, dz = xt.z - c.z, dw = D == 4 ? xt.w - c.w : 0.f;
+    const float r2 = dx * dx + dy * dy + dz * dz + dw * dw;
+    const float rinv = rsqrtf(r2);
+    const float r = r2 * rinv;
+    const float u = s * rinv;
+    float J[P + 1];
+    kernel_jets<P>(kp, r, rinv, J);
+    float up[P + 1];
+    up[0] = 1.f;
+#pragma unroll
+    for (int j = 1; j <= P; ++j) up[j] = up[j - 1] * u;
+    float G[Lay::npairs];
+#pragma unroll
+    for (int k = 0; k <= P; ++k)
+#pragma unroll
+        for (int jj = 0; jj < Lay::nj(k); ++jj) {
+            const int j = k + 2 * jj, q = Lay::pair(k) + jj;
+            float R = 0.f;
+#pragma unroll
+            for (int m = 0; m <= j; ++m) R = fmaf(T.That[q][m], J[m], R);
+            G[q] = up[j] * R;
+        }
+    const float ux = dx * rinv, uy = dy * rinv, uz = dz * rinv, uw = dw * rinv;
+    const float u2_3 = ux * ux + uy * uy + uz * uz;
+    solid_harmonics<D, P>(ux, uy, uz, uw, u2_3, u2_3 + uw * uw, T, [&](int k, int h, float Y) {
+        const int o = Lay::off(k) + h * Lay::nj(k);
+#pragma unroll
+        for (int jj = 0; jj < Lay::nj(k); ++jj) put(o + jj, Y * G[Lay::pair(k) + jj]);
+    });
+}
+
+// Per target block: for each far entry i, the CTA writes the 128 x NTP basis tile into shared
+// memory and one thread issues the MMAs against the node's packed multipoles (bulk-copied into
+// a 2-slot ring one entry ahead).  In ROW mode each thread computes its basis row for entry i
+// in registers while the MMAs of entry i - 1 still read the tile, and stores it after they
+// complete.  Every wait is bounded; a wait that runs out sets the error word and the CTA
+// drains what it issued before leaving.
 template <int D, int P, int PREC>
 __global__ void __launch_bounds__(kTB) far_tc_kernel(MvmArgs a, KernelParams kp_all, const __grid_constant__ FarTables T,
-                                                      const unsigned char* __restrict__ image, int nr_total,
-                                                      int64_t ynear_group_stride) {
-    using Lay = Layout<D, P>;
+                                                      const unsigned char* __restrict__ image, int nr_total) {
     using S = TcShape<D, P, PREC>;
-    constexpr int NT = S::NT, NTP = S::NTP, ST = S::STAGES;
+    constexpr int NT = S::NT, NTP = S::NTP, PER16 = S::PER16;
     constexpr int APLANE = 128 * NTP * S::EL, BPLANE = kTcN * NTP * S::EL;
     constexpr uint32_t IDESC = tc::instr_desc(PREC == TC_TF32 ? 2u : 1u, 128u, (uint32_t)kTcN);
     extern __shared__ __align__(128) unsigned char tc_smem[];
-    unsigned char* Abuf = tc_smem;                                  // [ST][A_BYTES]
-    unsigned char* Bbuf = tc_smem + ST * S::A_BYTES;                // [ST][B_BYTES]
-    __shared__ __align__(8) uint64_t bar_b[2], bar_mma[2];
+    unsigned char* A = tc_smem;                                      // [A_BYTES]
+    unsigned char* Bbuf = tc_smem + S::A_BYTES;                      // [2][B_BYTES]
+    __shared__ __align__(8) uint64_t bar_b[2], bar_mma;
     __shared__ uint32_t tmem_base;
     __shared__ int s_fail;
     const int tl = threadIdx.x, warp = tl >> 5;
@@ -100,10 +173,9 @@ __global__ void __launch_bounds__(kTB) far_tc_kernel(MvmArgs a, KernelParams kp_
     const int64_t e0 = a.far_off[blk], e1 = a.far_off[blk + 1];
     const int ne = (int)(e1 - e0);
     if (tl == 0) {
-        for (int s = 0; s < 2; ++s) {
-            ptx::mbar_init(&bar_b[s], 1);
-            ptx::mbar_init(&bar_mma[s], 1);
-        }
+        ptx::mbar_init(&bar_b[0], 1);
+        ptx::mbar_init(&bar_b[1], 1);
+        ptx::mbar_init(&bar_mma, 1);
         ptx::fence_mbar_init();
         s_fail = 0;
     }
@@ -115,64 +187,63 @@ __global__ void __launch_bounds__(kTB) far_tc_kernel(MvmArgs a, KernelParams kp_
     __syncthreads();
     tc::fence_after_sync();
     const uint32_t tmem = tmem_base;
+    // thread 0's bookkeeping of what it issued (to drain on failure)
+    int nb_issued = 0, nb_done = 0, n_commit = 0;
+    auto issue_b = [&](int i) {
+        const int slot = i & 1;
+        ptx::mbar_arrive_expect_tx(&bar_b[slot], (uint32_t)S::B_BYTES);
+        ptx::bulk_g2s(Bbuf + slot * S::B_BYTES, image + (int64_t)a.far_ent[e0 + i].x * S::B_BYTES,
+                      (uint32_t)S::B_BYTES, &bar_b[slot]);
+        ++nb_issued;
+    };
+    if (tl == 0 && ne > 0) issue_b(0);
     bool ok = true;
-    for (int i = 0; i < ne && ok; ++i) {
-        const int s = i % ST;
-        unsigned char* A = Abuf + s * S::A_BYTES;
-        unsigned char* B = Bbuf + s * S::B_BYTES;
-        if (i >= ST) ok = ptx::mbar_wait_bounded(&bar_mma[s], (uint32_t)(((i / ST) - 1) & 1), kWaitCycles);
-        if (!__syncthreads_and(ok)) { ok = false; break; }
+    for (int i = 0; i < ne; ++i) {
         const int2 ent = a.far_ent[e0 + i];
-        if (tl == 0) {
-            ptx::fence_proxy_async_smem();
-            ptx::mbar_arrive_expect_tx(&bar_b[s], (uint32_t)S::B_BYTES);
-            ptx::bulk_g2s(B, image + (int64_t)ent.x * S::B_BYTES, (uint32_t)S::B_BYTES, &bar_b[s]);
-        }
-        // basis row of this target for node ent.x (zeros when the entry does not apply to it)
         const bool active = valid && entry_active(ent.y, a.masks, tl);
-        if (active) {
-            const float4 c = a.nd_cf[ent.x];
-            const float dx = xt.x - c.x, dy = xt.y - c.y, dz = xt.z - c.z, dw = D == 4 ? xt.w - c.w : 0.f;
-            const float r2 = dx * dx + dy * dy + dz * dz + dw * dw;
-            const float rinv = rsqrtf(r2);
-            const float r = r2 * rinv;
-            const float u = a.nd_scale[ent.x] * rinv;
-            float J[P + 1];
-            kernel_jets<P>(kp, r, rinv, J);
-            float up[P + 1];
-            up[0] = 1.f;
+        float U[S::ROW ? NTP : 1];
+        if constexpr (S::ROW) {
+            if (active) {  // inactive rows are stored as zeros below, without a basis
+                far_basis<D, P>(xt, a.nd_cf[ent.x], a.nd_scale[ent.x], kp, T, [&](int q, float v) { U[q] = v; });
 #pragma unroll
-            for (int j = 1; j <= P; ++j) up[j] = up[j - 1] * u;
-            float G[Lay::npairs];
+                for (int q = NT; q < NTP; ++q) U[q] = 0.f;
+            }
+        }
+        // the MMAs of entry i - 1 are done: the tile and the other multipole slot are free
+        if (i > 0) ok = ptx::mbar_wait_bounded(&bar_mma, (uint32_t)((i - 1) & 1), kWaitCycles);
+        if (!__syncthreads_and(ok && !s_fail)) { ok = false; break; }
+        if (tl == 0 && i + 1 < ne) issue_b(i + 1);
+        if constexpr (S::ROW) {
+            if (active) {
 #pragma unroll
-            for (int k = 0; k <= P; ++k)
+                for (int g = 0; g < NTP / PER16; ++g)
+                    tc_store_row16<PREC>(A, APLANE, S::off(tl, g * PER16), U + g * PER16);
+            } else {
 #pragma unroll
-                for (int jj = 0; jj < Lay::nj(k); ++jj) {
-                    const int j = k + 2 * jj, q = Lay::pair(k) + jj;
-                    float R = 0.f;
+                for (int g = 0; g < NTP / PER16; ++g)
 #pragma unroll
-                    for (int m = 0; m <= j; ++m) R = fmaf(T.That[q][m], J[m], R);
-                    G[q] = up[j] * R;
-                }
-            const float ux = dx * rinv, uy = dy * rinv, uz = dz * rinv, uw = dw * rinv;
-            const float u2_3 = ux * ux + uy * uy + uz * uz;
-            solid_harmonics<D, P>(ux, uy, uz, uw, u2_3, u2_3 + uw * uw, T, [&](int k, int h, float Y) {
-                const int o = Lay::off(k) + h * Lay::nj(k);
-#pragma unroll
-                for (int jj = 0; jj < Lay::nj(k); ++jj) tc_store<PREC>(A, APLANE, S::off(tl, o + jj), Y * G[Lay::pair(k) + jj]);
-            });
-#pragma unroll
-            for (int q = NT; q < NTP; ++q) tc_store<PREC>(A, APLANE, S::off(tl, q), 0.f);
+                    for (int pl = 0; pl < S::PLANES; ++pl)
+                        *reinterpret_cast<uint4*>(A + pl * APLANE + S::off(tl, g * PER16)) = make_uint4(0u, 0u, 0u, 0u);
+            }
         } else {
+            if (active) {
+                far_basis<D, P>(xt, a.nd_cf[ent.x], a.nd_scale[ent.x], kp, T,
+                                [&](int q, float v) { tc_store<PREC>(A, APLANE, S::off(tl, q), v); });
+#pragma unroll
+                for (int q = NT; q < NTP; ++q) tc_store<PREC>(A, APLANE, S::off(tl, q), 0.f);
+            } else {
 #pragma unroll 4
-            for (int q = 0; q < NTP; ++q) tc_store<PREC>(A, APLANE, S::off(tl, q), 0.f);
+                for (int q = 0; q < NTP; ++q) tc_store<PREC>(A, APLANE, S::off(tl, q), 0.f);
+            }
         }
         ptx::fence_proxy_async_smem();  // generic-proxy stores -> visible to the tensor core
         __syncthreads();
         if (tl == 0) {
-            bool got = ptx::mbar_wait_bounded(&bar_b[s], (uint32_t)((i / ST) & 1), kWaitCycles);
+            const bool got = ptx::mbar_wait_bounded(&bar_b[i & 1], (uint32_t)((i >> 1) & 1), kWaitCycles);
             if (got) {
+                ++nb_done;
                 tc::fence_after_sync();
+                const unsigned char* B = Bbuf + (i & 1) * S::B_BYTES;
                 constexpr int KSTEP_BYTES = 256;  // one MMA consumes 2 core matrices (32 bytes) of K
                 constexpr int NSTEP = PREC == TC_TF32 ? NTP / 8 : NTP / 16;
 #pragma unroll 1
@@ -195,17 +266,13 @@ __global__ void __launch_bounds__(kTB) far_tc_kernel(MvmArgs a, KernelParams kp_
             } else {
                 s_fail = 1;
             }
-            tc::commit(&bar_mma[s]);  // arrives when the MMAs above (if any) are done
+            tc::commit(&bar_mma);  // arrives when the MMAs above (if any) are done
+            ++n_commit;
         }
-        __syncthreads();
-        if (s_fail) ok = false;
     }
     // wait for the last MMA group, then read the accumulator rows
-    if (ne > 0 && ok) {
-        const int last = ne - 1;
-        ok = ptx::mbar_wait_bounded(&bar_mma[last % ST], (uint32_t)((last / ST) & 1), kWaitCycles);
-    }
-    const bool all_ok = __syncthreads_and(ok) != 0;
+    if (ok && ne > 0) ok = ptx::mbar_wait_bounded(&bar_mma, (uint32_t)((ne - 1) & 1), kWaitCycles);
+    const bool all_ok = __syncthreads_and(ok && !s_fail) != 0;
     tc::fence_after_sync();
     float acc[kTcN];
 #pragma unroll
@@ -217,20 +284,16 @@ __global__ void __launch_bounds__(kTB) far_tc_kernel(MvmArgs a, KernelParams kp_
     }
     if (!all_ok && tl == 0) {
         atomicExch(a.err, 1);
-        // let any bulk copies and MMAs still in flight finish before the CTA leaves (bounded)
-        for (int s = 0; s < ST; ++s) {
-            ptx::mbar_wait_bounded(&bar_b[s], 0, kWaitCycles);
-            ptx::mbar_wait_bounded(&bar_mma[s], 0, kWaitCycles);
-        }
+        // let the bulk copies and MMAs still in flight finish before the CTA leaves (bounded)
+        for (int j = nb_done; j < nb_issued; ++j)
+            ptx::mbar_wait_bounded(&bar_b[j & 1], (uint32_t)((j >> 1) & 1), kWaitCycles);
+        if (n_commit > 0) ptx::mbar_wait_bounded(&bar_mma, (uint32_t)((n_commit - 1) & 1), kWaitCycles);
     }
     tc::fence_before_sync();
     __syncthreads();
     if (warp == 0) tc::dealloc(tmem, 32);
-    if (valid && all_ok) {
-        const int64_t o = a.perm[t];
-        for (int r = 0; r < nr_total; ++r)
-            a.y[(int64_t)r * a.N + o] = a.ynear[(int64_t)(r / 8) * ynear_group_stride + (int64_t)(r % 8) * a.N + t] + acc[r];
-    }
+    if (valid && all_ok)
+        for (int r = 0; r < nr_total; ++r) a.yfar[(int64_t)r * a.N + t] = acc[r];  // tree order, coalesced
 }
 
 }  // namespace fkt
@@ -243,7 +306,6 @@ struct TcLaunch {
     const FarTables* T;
     int64_t nblocks, nnodes;
     int64_t group_stride;        // floats between right-hand-side groups of the multipoles
-    int64_t ynear_group_stride;  // floats between right-hand-side groups of the near result
     int nr_total;                // right-hand sides in this pass (<= kTcN)
     unsigned char* image;        // packed B operands, [nodes][B_BYTES]
     cudaStream_t s_pack, s_far;
@@ -275,8 +337,7 @@ int launch_tc_far_t(const TcLaunch& L) {
                                               (int)smem));
             attr = true;
         }
-        far_tc_kernel<D, P, PREC><<<(unsigned)L.nblocks, kTB, smem, L.s_far>>>(*L.a, *L.kp, *L.T, L.image, L.nr_total,
-                                                                                L.ynear_group_stride);
+        far_tc_kernel<D, P, PREC><<<(unsigned)L.nblocks, kTB, smem, L.s_far>>>(*L.a, *L.kp, *L.T, L.image, L.nr_total);
         FKT_CUDA_TRY(cudaGetLastError());
         return FKT_OK;
     }

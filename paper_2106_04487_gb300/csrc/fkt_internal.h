@@ -97,6 +97,7 @@ struct fkt_plan_s {
     int cap_rhs = 0;
     float4* rec = nullptr;         // source records (point + weights) in tree order, per group
     float* ynear = nullptr;        // near-field result, sorted [nrhs][N]
+    float* yfar = nullptr;         // far-field result, sorted [nrhs][N]
     float* mult = nullptr;         // multipoles [nodes][nterms][nrhs]
     float* s2m_part = nullptr;     // per-item partial multipoles [items][nterms][nrhs]
     unsigned char* tc_image = nullptr;  // packed tensor-core operands of the multipoles
@@ -123,7 +124,7 @@ struct fkt_plan_s {
     float* cg_z = nullptr;         // [nrhs][N] preconditioned residual
     double* cg_s = nullptr;        // scalars: [8][kMaxRhs]
     cudaStream_t stream2 = nullptr;
-    cudaEvent_t ev[8] = {};
+    cudaEvent_t ev[10] = {};
     // batch of independent problems merged into one plan (empty for a single problem)
     int nprob = 0;
     std::vector<int64_t> prob_off;          // first point of each problem, nprob + 1 entries
@@ -159,17 +160,25 @@ struct MvmArgs;
 // Work buffers of one MVM call (fkt_mvm: plan-owned; fkt_mvm_noalloc: the static scratch).
 struct MvmBuffers {
     float4* rec;
-    float* ynear;
+    float* ynear;          // near-field result, tree order
     float* mult;
     float* part;
     unsigned char* image;  // tensor-core operand image of the multipoles (far_precision != fp32)
+    float* yfar;           // far-field result, tree order
 };
-// Floats each buffer needs for nrhs right-hand sides (each rounded up to 64 floats).
-void mvm_buffer_floats(const fkt_plan_s* P, int nrhs, size_t out[5]);
+constexpr int kMvmBufs = 6;
+// Floats each buffer needs for nrhs right-hand sides (each rounded up to 64 floats), in the
+// order rec, ynear, mult, part, image, yfar.
+void mvm_buffer_floats(const fkt_plan_s* P, int nrhs, size_t out[kMvmBufs]);
 int run_mvm(fkt_plan_s* P, const MvmBuffers& B, const float* w, float* y, int nrhs, bool timing);
 int launch_mvm(fkt_plan_s* P, const float* w, float* y, int nrhs);
 int launch_dense(fkt_plan_s* P, const float* w, float* y, int nrhs);
 int ensure_rhs_capacity(fkt_plan_s* P, int nrhs);
+
+// The plan's second stream (s2m and the far field), non-blocking.  (A higher priority for it
+// makes the far field overlap the near field but gives no net speed-up: both stages compete for
+// the same SM resources.)
+int create_far_stream(cudaStream_t* s);
 
 // stage launch helpers shared with batch.cu
 void launch_near_stage(fkt_plan_s* P, MvmArgs& a, int nrb, int tpt, cudaStream_t st);

@@ -222,11 +222,14 @@ struct MvmArgs {
     const int64_t* s2m_item_off;
     int64_t nnodes;
     // per pass (one group of NR right-hand sides)
-    const float4* rec;         // source records in tree order: rec4 float4 per point (point, then weights)
+    const float4* rec;         // source records in tree order: rec_f4 float4 per point (point, then weights)
+    int rec_f4;                // float4s per source record
+    int woff;                  // float index, within a record, of this group's first weight (s2m)
     float* ynear;              // sorted near-field result of this group, [NR][N]
     float* mult;               // multipoles of this group, [nodes][nterms][NR]
     float* part;               // s2m partials, [items][nterms][NR]
     float* y;                  // output (original order), [nrhs][N]; this group starts at y
+    float* yfar;               // far-field result of this group (tree order), [NR][N]
     int nr;                    // right-hand sides actually present in this group (<= NR)
     int* err;                  // device error word: 1 = a bounded wait ran out
     // batches of independent problems (all null for a single problem)
@@ -253,6 +256,7 @@ struct Rec {
 };
 
 inline int rec_f4(int d, int nrb) { return (d == 3 && nrb == 1) ? 1 : (4 + nrb + 3) / 4; }
+inline int rec_woff(int d, int nrb) { return (d == 3 && nrb == 1) ? 3 : 4; }
 
 __device__ __forceinline__ bool entry_active(int mask, const uint32_t* __restrict__ masks, int t) {
     return mask < 0 || ((__ldg(&masks[(int64_t)mask * kMaskWords + (t >> 5)]) >> (t & 31)) & 1u);

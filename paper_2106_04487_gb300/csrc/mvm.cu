@@ -1,7 +1,10 @@
 // Host orchestration of one FKT matrix-vector product (Algorithm 1) on the GPU:
 //   permute w -> [s2m -> s2m_reduce] (second stream)  ||  near field (plan stream)
 //   -> far field + combine + scatter to the caller's order.
-// Right-hand sides are processed in groups of 8 (or 1 for a single right-hand side).
+// Right-hand sides are processed in passes of up to 32: one permute and one near-field launch
+// per pass (the kernel value of a pair serves every right-hand side of the pass), s2m and the
+// float32 far field per group of 8 (or 1 for a single right-hand side), the tensor-core far
+// field once per pass.
 #include <algorithm>
 
 #include "mvm_kernels.cuh"
@@ -21,6 +24,9 @@ FKT_DECL_RANGE(4, 0, 4)
 FKT_DECL_RANGE(4, 5, 6)
 FKT_DECL_RANGE(4, 7, 8)
 #undef FKT_DECL_RANGE
+
+void launch_near_d3(int nw, int tpt, int kind, unsigned grid, cudaStream_t st, const MvmArgs& a, const KernelParams& kp);
+void launch_near_d4(int nw, int tpt, int kind, unsigned grid, cudaStream_t st, const MvmArgs& a, const KernelParams& kp);
 
 int launch_tc_d3_p0_6(int p, int prec, bool far, const TcLaunch& L);
 int launch_tc_d3_p7_10(int p, int prec, bool far, const TcLaunch& L);
@@ -62,41 +68,29 @@ static int launch_far_any(int d, int p, int nrb, const FarLaunch& L) {
 
 namespace {
 
-template <int D, int NR, int T>
-void launch_near_t(int kind, unsigned grid, cudaStream_t st, const MvmArgs& a, const KernelParams& kp) {
-    constexpr int TH = NearShape<D, NR, T>::THREADS;
-    switch (kind) {
-    case FKT_GAUSSIAN: near_kernel<D, FKT_GAUSSIAN, NR, T><<<grid, TH, 0, st>>>(a, kp); break;
-    case FKT_EXPONENTIAL: near_kernel<D, FKT_EXPONENTIAL, NR, T><<<grid, TH, 0, st>>>(a, kp); break;
-    case FKT_MATERN32: near_kernel<D, FKT_MATERN32, NR, T><<<grid, TH, 0, st>>>(a, kp); break;
-    case FKT_MATERN52: near_kernel<D, FKT_MATERN52, NR, T><<<grid, TH, 0, st>>>(a, kp); break;
-    case FKT_CAUCHY: near_kernel<D, FKT_CAUCHY, NR, T><<<grid, TH, 0, st>>>(a, kp); break;
-    case FKT_RATQUAD: near_kernel<D, FKT_RATQUAD, NR, T><<<grid, TH, 0, st>>>(a, kp); break;
-    default: near_kernel<D, FKT_LAPLACE, NR, T><<<grid, TH, 0, st>>>(a, kp); break;
-    }
-}
-
-// Near field launch: targets per thread tpt = 2 or 4 (4 only for one right-hand side).
-void launch_near(int d, int nrb, int tpt, int kind, unsigned grid, cudaStream_t st, const MvmArgs& a,
+// Near field launch: nw right-hand sides per pass (1, 8, 16, 32); targets per thread tpt = 2 or 4
+// (4 only for one right-hand side).
+void launch_near(int d, int nw, int tpt, int kind, unsigned grid, cudaStream_t st, const MvmArgs& a,
                  const KernelParams& kp) {
-    if (d == 3) {
-        if (nrb == 1) tpt == 4 ? launch_near_t<3, 1, 4>(kind, grid, st, a, kp) : launch_near_t<3, 1, 2>(kind, grid, st, a, kp);
-        else launch_near_t<3, 8, 2>(kind, grid, st, a, kp);
-    } else {
-        if (nrb == 1) tpt == 4 ? launch_near_t<4, 1, 4>(kind, grid, st, a, kp) : launch_near_t<4, 1, 2>(kind, grid, st, a, kp);
-        else launch_near_t<4, 8, 2>(kind, grid, st, a, kp);
+    if (d == 3) launch_near_d3(nw, tpt, kind, grid, st, a, kp);
+    else launch_near_d4(nw, tpt, kind, grid, st, a, kp);
+}
+
+template <int D>
+void launch_permute_dim(int nw, unsigned grid, cudaStream_t st, int64_t N, const int32_t* perm, const float4* xs,
+                        const float* w, int nr, float sig, const float* pt_sig, float4* rec) {
+    switch (nw) {
+    case 1: permute_kernel<D, 1><<<grid, 256, 0, st>>>(N, perm, xs, w, nr, sig, pt_sig, rec); break;
+    case 8: permute_kernel<D, 8><<<grid, 256, 0, st>>>(N, perm, xs, w, nr, sig, pt_sig, rec); break;
+    case 16: permute_kernel<D, 16><<<grid, 256, 0, st>>>(N, perm, xs, w, nr, sig, pt_sig, rec); break;
+    default: permute_kernel<D, 32><<<grid, 256, 0, st>>>(N, perm, xs, w, nr, sig, pt_sig, rec); break;
     }
 }
 
-void launch_permute(int d, int nrb, unsigned grid, cudaStream_t st, int64_t N, const int32_t* perm, const float4* xs,
+void launch_permute(int d, int nw, unsigned grid, cudaStream_t st, int64_t N, const int32_t* perm, const float4* xs,
                     const float* w, int nr, float sig, const float* pt_sig, float4* rec) {
-    if (d == 3) {
-        if (nrb == 1) permute_kernel<3, 1><<<grid, 256, 0, st>>>(N, perm, xs, w, nr, sig, pt_sig, rec);
-        else permute_kernel<3, 8><<<grid, 256, 0, st>>>(N, perm, xs, w, nr, sig, pt_sig, rec);
-    } else {
-        if (nrb == 1) permute_kernel<4, 1><<<grid, 256, 0, st>>>(N, perm, xs, w, nr, sig, pt_sig, rec);
-        else permute_kernel<4, 8><<<grid, 256, 0, st>>>(N, perm, xs, w, nr, sig, pt_sig, rec);
-    }
+    if (d == 3) launch_permute_dim<3>(nw, grid, st, N, perm, xs, w, nr, sig, pt_sig, rec);
+    else launch_permute_dim<4>(nw, grid, st, N, perm, xs, w, nr, sig, pt_sig, rec);
 }
 
 MvmArgs base_args(fkt_plan_s* P) {
@@ -151,40 +145,50 @@ void launch_near_stage(fkt_plan_s* P, MvmArgs& a, int nrb, int tpt, cudaStream_t
     a.blk_list = P->far_list;  // the far stage that follows walks all blocks, most work first
 }
 
-// Right-hand sides per pass of the s2m / near kernels: 1 for a single right-hand side on the
+// Right-hand sides per s2m / float32 far-field group: 1 for a single right-hand side on the
 // float32 far path, 8 otherwise (the tensor-core far field always consumes groups of 8).
 static int rhs_block(const fkt_plan_s* P, int nrhs) { return (nrhs == 1 && P->far_precision == FAR_FP32) ? 1 : 8; }
 
-void mvm_buffer_floats(const fkt_plan_s* P, int nrhs, size_t out[5]) {
+// Right-hand sides per near-field pass of npass (<= kPass) right-hand sides.
+static int near_width(int nrb, int npass) { return nrb == 1 ? 1 : npass <= 8 ? 8 : npass <= 16 ? 16 : 32; }
+
+constexpr int kPass = 32;  // right-hand sides per pass (= the tensor-core far field's N)
+static_assert(kPass == kTcN, "a pass feeds one tensor-core far-field launch");
+
+void mvm_buffer_floats(const fkt_plan_s* P, int nrhs, size_t out[kMvmBufs]) {
     const int nrb = rhs_block(P, nrhs);
+    const int nw = near_width(nrb, std::min(nrhs, kPass));
     const size_t groups = (size_t)(nrhs + nrb - 1) / nrb;
     const size_t N = (size_t)P->N, NT = (size_t)P->nterms;
     const size_t nodes = std::max<int64_t>(P->nnodes, 1), items = std::max<int64_t>(P->n_s2m_items, 1);
-    out[0] = round64(groups * N * 4 * (size_t)rec_f4(P->d, nrb));  // records
-    out[1] = round64(groups * nrb * N);                             // near result
-    out[2] = round64(groups * nrb * NT * nodes);                    // multipoles
-    out[3] = round64(groups * nrb * NT * items);                    // s2m partials
+    out[0] = round64(N * 4 * (size_t)rec_f4(P->d, nw));  // records of one pass (reused by every pass)
+    out[1] = round64(groups * nrb * N);                  // near result
+    out[2] = round64(groups * nrb * NT * nodes);         // multipoles
+    out[3] = round64(groups * nrb * NT * items);         // s2m partials
     out[4] = P->far_precision == FAR_FP32 ? 0
              : round64(nodes * (size_t)tc_b_bytes(P->d, P->p, tc_prec_of(P->far_precision)) / 4);
+    out[5] = round64(groups * nrb * N);                  // far result
 }
 
 int ensure_rhs_capacity(fkt_plan_s* P, int nrhs) {
     const int nrb = rhs_block(P, nrhs);
     const int cap = nrb == 1 ? 1 : (nrhs + 7) / 8 * 8;
-    size_t f[5];
+    size_t f[kMvmBufs];
     mvm_buffer_floats(P, cap, f);
     if (cap > P->cap_rhs) {
         cudaFree(P->rec);
         cudaFree(P->ynear);
+        cudaFree(P->yfar);
         cudaFree(P->mult);
         cudaFree(P->s2m_part);
         P->rec = nullptr;
-        P->ynear = P->mult = P->s2m_part = nullptr;
+        P->ynear = P->yfar = P->mult = P->s2m_part = nullptr;
         P->cap_rhs = 0;
         FKT_CUDA_TRY(cudaMalloc(&P->rec, sizeof(float) * f[0]));
         FKT_CUDA_TRY(cudaMalloc(&P->ynear, sizeof(float) * f[1]));
         FKT_CUDA_TRY(cudaMalloc(&P->mult, sizeof(float) * f[2]));
         FKT_CUDA_TRY(cudaMalloc(&P->s2m_part, sizeof(float) * f[3]));
+        FKT_CUDA_TRY(cudaMalloc(&P->yfar, sizeof(float) * f[5]));
         P->cap_rhs = cap;
     }
     if (f[4] && P->cap_tc != P->far_precision + 1) {
@@ -197,57 +201,10 @@ int ensure_rhs_capacity(fkt_plan_s* P, int nrhs) {
     return FKT_OK;
 }
 
-// One product on the plan's stream with the given work buffers: per group of right-hand sides
-//   permute -> fork [s2m -> reduce on stream2] || near field -> join -> far field (+ combine).
-static int run_mvm_tc(fkt_plan_s* P, const MvmBuffers& B, const float* w, float* y, int nrhs, bool timing);
-static int finish_timing(fkt_plan_s* P);
-
-int run_mvm(fkt_plan_s* P, const MvmBuffers& B, const float* w, float* y, int nrhs, bool timing) {
-    if (P->far_precision != FAR_FP32) return run_mvm_tc(P, B, w, y, nrhs, timing);
-    const int nrb = rhs_block(P, nrhs);
-    const int groups = (nrhs + nrb - 1) / nrb;
-    cudaStream_t st = P->stream, st2 = P->stream2;
-    const int64_t N = P->N;
-    const size_t NT = (size_t)P->nterms;
-    const size_t rec_group = (size_t)N * rec_f4(P->d, nrb);
-    const size_t nodes = std::max<int64_t>(P->nnodes, 1), items = std::max<int64_t>(P->n_s2m_items, 1);
-    if (timing) FKT_CUDA_TRY(cudaEventRecord(P->ev[0], st));
-    for (int g = 0; g < groups; ++g) {
-        const int nr = std::min(nrb, nrhs - g * nrb);
-        MvmArgs a = base_args(P);
-        float4* rec = B.rec + (size_t)g * rec_group;
-        a.rec = rec;
-        a.ynear = B.ynear + (size_t)g * nrb * N;
-        a.mult = B.mult + (size_t)g * nrb * NT * nodes;
-        a.part = B.part + (size_t)g * nrb * NT * items;
-        a.y = y + (size_t)g * nrb * N;
-        a.nr = nr;
-        launch_permute(P->d, nrb, (unsigned)((N + 255) / 256), st, N, P->perm, P->xs, w + (size_t)g * nrb * N, nr,
-                       P->kp.sig, P->pt_sig, rec);
-        FKT_CUDA_TRY(cudaGetLastError());
-        // fork: s2m on the second stream while the near field runs on the plan stream
-        FKT_CUDA_TRY(cudaEventRecord(P->ev[1], st));
-        FKT_CUDA_TRY(cudaStreamWaitEvent(st2, P->ev[1], 0));
-        FarLaunch L{&a, &P->kp, &P->tabs, P->nblocks, P->n_s2m_items, P->nnodes, st, st2};
-        if (timing) FKT_CUDA_TRY(cudaEventRecord(P->ev[2], st2));
-        int rc = launch_s2m_any(P->d, P->p, nrb, L);
-        if (rc) return rc;
-        if (timing) FKT_CUDA_TRY(cudaEventRecord(P->ev[3], st2));
-        FKT_CUDA_TRY(cudaEventRecord(P->ev[4], st2));
-        if (timing) FKT_CUDA_TRY(cudaEventRecord(P->ev[5], st));
-        launch_near_stage(P, a, nrb, P->near_tpt, st);
-        FKT_CUDA_TRY(cudaGetLastError());
-        if (timing) FKT_CUDA_TRY(cudaEventRecord(P->ev[6], st));
-        FKT_CUDA_TRY(cudaStreamWaitEvent(st, P->ev[4], 0));  // join
-        rc = launch_far_any(P->d, P->p, nrb, L);
-        if (rc) return rc;
-    }
-    if (timing) return finish_timing(P);
-    return FKT_OK;
-}
-
-// Stage times of the last product from the plan's events: 0 start, 2-3 s2m (second stream),
-// 5-6 near field, 7 end; "far" is 6 -> 7 and includes any wait for s2m.
+// Stage times of the last product from the plan's events: 0 start, 7 end (plan stream);
+// 2-3 s2m and 8-9 far field (second stream); 5-6 near field (plan stream).  The near and far
+// stages run concurrently.  With more than one pass each interval spans from the first pass's
+// launch to the last one's end.
 static int finish_timing(fkt_plan_s* P) {
     FKT_CUDA_TRY(cudaEventRecord(P->ev[7], P->stream));
     FKT_CUDA_TRY(cudaEventSynchronize(P->ev[7]));
@@ -255,7 +212,7 @@ static int finish_timing(fkt_plan_s* P) {
     cudaEventElapsedTime(&t_tot, P->ev[0], P->ev[7]);
     cudaEventElapsedTime(&t_s2m, P->ev[2], P->ev[3]);
     cudaEventElapsedTime(&t_near, P->ev[5], P->ev[6]);
-    cudaEventElapsedTime(&t_far, P->ev[6], P->ev[7]);
+    cudaEventElapsedTime(&t_far, P->ev[8], P->ev[9]);
     P->stats.last_total_ms = t_tot;
     P->stats.last_s2m_ms = t_s2m;
     P->stats.last_near_ms = t_near;
@@ -263,65 +220,100 @@ static int finish_timing(fkt_plan_s* P) {
     return FKT_OK;
 }
 
-// Tensor-core far field: passes of up to kTcN right-hand sides; within a pass, groups of 8 run
-// permute / s2m / near as usual, then the multipoles of the pass are packed into the operand
-// image and one far_tc launch accumulates every far node into TMEM and writes y.
-static int run_mvm_tc(fkt_plan_s* P, const MvmBuffers& B, const float* w, float* y, int nrhs, bool timing) {
+// One product on the plan's stream with the given work buffers.  Per pass of up to 32
+// right-hand sides:
+//   plan stream:    permute -> near field (whole pass) -----------------> wait -> unpermute(near + far)
+//   second stream:            s2m + reduce per group -> far field (float32 per group, or pack +
+//                             one tensor-core launch) -> event
+// The near and far fields are independent until the final sum, so they share the SMs.  Passes
+// reuse one record buffer: the next pass's permute is ordered after this pass's unpermute on the
+// plan stream, which itself waited for this pass's s2m and far field.
+int run_mvm(fkt_plan_s* P, const MvmBuffers& B, const float* w, float* y, int nrhs, bool timing) {
+    const bool tc = P->far_precision != FAR_FP32;
+    const int nrb = rhs_block(P, nrhs);
     cudaStream_t st = P->stream, st2 = P->stream2;
-    if (timing) FKT_CUDA_TRY(cudaEventRecord(P->ev[0], st));
     const int64_t N = P->N;
     const size_t NT = (size_t)P->nterms;
-    const size_t rec_group = (size_t)N * rec_f4(P->d, 8);
     const size_t nodes = std::max<int64_t>(P->nnodes, 1), items = std::max<int64_t>(P->n_s2m_items, 1);
-    const int prec = tc_prec_of(P->far_precision);
-    for (int r0 = 0; r0 < nrhs; r0 += kTcN) {
-        const int npass = std::min(kTcN, nrhs - r0);
-        const int g0 = r0 / 8, ng = (npass + 7) / 8;
+    const unsigned pgrid = (unsigned)((N + 255) / 256);
+    if (timing) FKT_CUDA_TRY(cudaEventRecord(P->ev[0], st));
+    for (int r0 = 0; r0 < nrhs; r0 += kPass) {
+        const int npass = std::min(kPass, nrhs - r0);
+        const int nw = near_width(nrb, npass);
+        const int g0 = r0 / nrb, ng = (npass + nrb - 1) / nrb;
+        const bool first = r0 == 0;
         MvmArgs a = base_args(P);
+        a.rec = B.rec;
+        a.rec_f4 = rec_f4(P->d, nw);
+        launch_permute(P->d, nw, pgrid, st, N, P->perm, P->xs, w + (size_t)r0 * N, npass, P->kp.sig, P->pt_sig, B.rec);
+        FKT_CUDA_TRY(cudaGetLastError());
+        // fork: s2m and the far field on the second stream, the near field on the plan stream
+        FKT_CUDA_TRY(cudaEventRecord(P->ev[1], st));
+        FKT_CUDA_TRY(cudaStreamWaitEvent(st2, P->ev[1], 0));
+        if (timing && first) FKT_CUDA_TRY(cudaEventRecord(P->ev[2], st2));
         for (int gi = 0; gi < ng; ++gi) {
             const int g = g0 + gi;
-            const int nr = std::min(8, nrhs - g * 8);
-            float4* rec = B.rec + (size_t)g * rec_group;
-            a.rec = rec;
-            a.ynear = B.ynear + (size_t)g * 8 * N;
-            a.mult = B.mult + (size_t)g * 8 * NT * nodes;
-            a.part = B.part + (size_t)g * 8 * NT * items;
-            a.nr = nr;
-            launch_permute(P->d, 8, (unsigned)((N + 255) / 256), st, N, P->perm, P->xs, w + (size_t)g * 8 * N, nr,
-                           P->kp.sig, P->pt_sig, rec);
-            FKT_CUDA_TRY(cudaGetLastError());
-            FKT_CUDA_TRY(cudaEventRecord(P->ev[1], st));
-            FKT_CUDA_TRY(cudaStreamWaitEvent(st2, P->ev[1], 0));
-            FarLaunch L{&a, &P->kp, &P->tabs, P->nblocks, P->n_s2m_items, P->nnodes, st, st2};
-            if (timing && r0 == 0 && gi == 0) FKT_CUDA_TRY(cudaEventRecord(P->ev[2], st2));
-            int rc = launch_s2m_any(P->d, P->p, 8, L);
+            MvmArgs ag = a;
+            ag.woff = rec_woff(P->d, nw) + gi * nrb;
+            ag.mult = B.mult + (size_t)g * nrb * NT * nodes;
+            ag.part = B.part + (size_t)g * nrb * NT * items;
+            ag.nr = std::min(nrb, nrhs - g * nrb);
+            FarLaunch L{&ag, &P->kp, &P->tabs, P->nblocks, P->n_s2m_items, P->nnodes, st2, st2};
+            int rc = launch_s2m_any(P->d, P->p, nrb, L);
             if (rc) return rc;
-            if (timing) FKT_CUDA_TRY(cudaEventRecord(P->ev[3], st2));
-            if (timing && r0 == 0 && gi == 0) FKT_CUDA_TRY(cudaEventRecord(P->ev[5], st));
-            launch_near_stage(P, a, 8, 2, st);
-            FKT_CUDA_TRY(cudaGetLastError());
-            if (timing) FKT_CUDA_TRY(cudaEventRecord(P->ev[6], st));
         }
-        a.mult = B.mult + (size_t)g0 * 8 * NT * nodes;
-        a.ynear = B.ynear + (size_t)g0 * 8 * N;
-        a.y = y + (size_t)r0 * N;
-        TcLaunch T{&a, &P->kp, &P->tabs, P->nblocks, P->nnodes, (int64_t)(8 * NT * nodes), (int64_t)(8 * N), npass,
-                   B.image, st2, st};
-        int rc = launch_tc_any(P->d, P->p, prec, false, T);  // pack on the s2m stream
-        if (rc) return rc;
+        if (timing) FKT_CUDA_TRY(cudaEventRecord(P->ev[3], st2));
+        if (timing && first) FKT_CUDA_TRY(cudaEventRecord(P->ev[8], st2));
+        MvmArgs af = a;
+        af.blk_list = P->nprob ? P->far_list : nullptr;  // most work first
+        if (!tc) {
+            for (int gi = 0; gi < ng; ++gi) {
+                const int g = g0 + gi;
+                MvmArgs ag = af;
+                ag.mult = B.mult + (size_t)g * nrb * NT * nodes;
+                ag.yfar = B.yfar + (size_t)g * nrb * N;
+                ag.nr = std::min(nrb, nrhs - g * nrb);
+                FarLaunch L{&ag, &P->kp, &P->tabs, P->nblocks, P->n_s2m_items, P->nnodes, st2, st2};
+                int rc = launch_far_any(P->d, P->p, nrb, L);
+                if (rc) return rc;
+            }
+        } else {
+            af.mult = B.mult + (size_t)g0 * 8 * NT * nodes;
+            af.yfar = B.yfar + (size_t)r0 * N;
+            TcLaunch T{&af, &P->kp, &P->tabs, P->nblocks, P->nnodes, (int64_t)(8 * NT * nodes), npass, B.image, st2, st2};
+            int rc = launch_tc_any(P->d, P->p, tc_prec_of(P->far_precision), false, T);  // pack
+            if (rc) return rc;
+            rc = launch_tc_any(P->d, P->p, tc_prec_of(P->far_precision), true, T);
+            if (rc) return rc;
+        }
+        if (timing) FKT_CUDA_TRY(cudaEventRecord(P->ev[9], st2));
         FKT_CUDA_TRY(cudaEventRecord(P->ev[4], st2));
+        // near field of the whole pass on the plan stream
+        if (timing && first) FKT_CUDA_TRY(cudaEventRecord(P->ev[5], st));
+        a.ynear = B.ynear + (size_t)r0 * N;
+        a.nr = npass;
+        launch_near_stage(P, a, nw, P->near_tpt, st);
+        FKT_CUDA_TRY(cudaGetLastError());
+        if (timing) FKT_CUDA_TRY(cudaEventRecord(P->ev[6], st));
+        // join, then near + far back to the caller's order
         FKT_CUDA_TRY(cudaStreamWaitEvent(st, P->ev[4], 0));
-        rc = launch_tc_any(P->d, P->p, prec, true, T);
-        if (rc) return rc;
+        unpermute_kernel<><<<pgrid, 256, 0, st>>>(N, npass, P->perm, B.ynear + (size_t)r0 * N, B.yfar + (size_t)r0 * N,
+                                                   y + (size_t)r0 * N);
+        FKT_CUDA_TRY(cudaGetLastError());
     }
     if (timing) return finish_timing(P);
+    return FKT_OK;
+}
+
+int create_far_stream(cudaStream_t* s) {
+    FKT_CUDA_TRY(cudaStreamCreateWithFlags(s, cudaStreamNonBlocking));
     return FKT_OK;
 }
 
 int launch_mvm(fkt_plan_s* P, const float* w, float* y, int nrhs) {
     int rc = ensure_rhs_capacity(P, nrhs);
     if (rc) return rc;
-    MvmBuffers B{P->rec, P->ynear, P->mult, P->s2m_part, P->tc_image};
+    MvmBuffers B{P->rec, P->ynear, P->mult, P->s2m_part, P->tc_image, P->yfar};
     return run_mvm(P, B, w, y, nrhs, P->timing);
 }
 
@@ -337,21 +329,21 @@ int launch_dense(fkt_plan_s* P, const float* w, float* y, int nrhs) {
         FKT_CUDA_TRY(cudaGetLastError());
     }
     const int nrb = rhs_block(P, nrhs);
-    const int groups = (nrhs + nrb - 1) / nrb;
     const int64_t N = P->N;
-    const size_t rec_group = (size_t)N * rec_f4(P->d, nrb);
     const unsigned pg = (unsigned)((N + 255) / 256);
-    for (int g = 0; g < groups; ++g) {
-        const int nr = std::min(nrb, nrhs - g * nrb);
+    for (int r0 = 0; r0 < nrhs; r0 += kPass) {
+        const int npass = std::min(kPass, nrhs - r0);
+        const int nw = near_width(nrb, npass);
         MvmArgs a = base_args(P);
         a.near_off = P->dense_off;
         a.near_ent = P->dense_ent;
-        float4* rec = P->rec + (size_t)g * rec_group;
-        a.rec = rec;
-        a.ynear = P->ynear + (size_t)g * nrb * N;
-        launch_permute(P->d, nrb, pg, st, N, P->perm, P->xs, w + (size_t)g * nrb * N, nr, P->kp.sig, P->pt_sig, rec);
-        launch_near_stage(P, a, nrb, P->near_tpt, st);
-        unpermute_kernel<><<<pg, 256, 0, st>>>(N, nr, P->perm, a.ynear, y + (size_t)g * nrb * N);
+        a.rec = P->rec;
+        a.rec_f4 = rec_f4(P->d, nw);
+        a.ynear = P->ynear + (size_t)r0 * N;
+        a.nr = npass;
+        launch_permute(P->d, nw, pg, st, N, P->perm, P->xs, w + (size_t)r0 * N, npass, P->kp.sig, P->pt_sig, P->rec);
+        launch_near_stage(P, a, nw, P->near_tpt, st);
+        unpermute_kernel<><<<pg, 256, 0, st>>>(N, npass, P->perm, a.ynear, nullptr, y + (size_t)r0 * N);
         FKT_CUDA_TRY(cudaGetLastError());
     }
     return FKT_OK;

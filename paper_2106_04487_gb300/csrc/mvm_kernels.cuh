@@ -4,9 +4,12 @@
 //   s2m_reduce       per node: sum of its chunks' partials (deterministic order)
 //   near_kernel      per target block: dense K(near, leaf) * w[leaf] over the near leaves
 //                    (also the exact all-pairs product, with the root as the only "near leaf")
-//   far_kernel       per target block: m2t * multipole over the far nodes, plus the near
-//                    result, scattered back to the caller's order (far_mr_kernel: 8 RHS)
+//   far_kernel       per target block: m2t * multipole over the far nodes (far_mr_kernel: 8 RHS),
+//                    written in tree order; unpermute adds the near field and scatters the sum
+//                    back to the caller's order
 #pragma once
+
+#include <type_traits>
 
 #include "fkt_kernels.cuh"
 #include "ptx.cuh"
@@ -36,13 +39,18 @@ __global__ void permute_kernel(int64_t N, const int32_t* __restrict__ perm, cons
     for (int q = 0; q < R::F4; ++q) rec[i * R::F4 + q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
 }
 
+// y[r][perm[i]] = ys[r][i] (+ yadd[r][i]): back to the caller's order, adding the far field
+// to the near field when yadd is given.
 template <int Unused = 0>
 __global__ void unpermute_kernel(int64_t N, int nr, const int32_t* __restrict__ perm, const float* __restrict__ ys,
-                                 float* __restrict__ y) {
+                                 const float* __restrict__ yadd, float* __restrict__ y) {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= N) return;
     const int64_t o = perm[i];
-    for (int r = 0; r < nr; ++r) y[r * N + o] = ys[r * N + i];
+    if (yadd)
+        for (int r = 0; r < nr; ++r) y[r * N + o] = ys[r * N + i] + yadd[r * N + i];
+    else
+        for (int r = 0; r < nr; ++r) y[r * N + o] = ys[r * N + i];
 }
 
 // ------------------------------------------------------------------- s2m
@@ -97,8 +105,7 @@ s2m_kernel(MvmArgs a, const __grid_constant__ FarTables T) {
         });
 #pragma unroll
         for (int r = 0; r < NR; ++r)
-            wt[lane * NR + r] = ok ? reinterpret_cast<const float*>(a.rec + (int64_t)s * Rec<D, NR>::F4)[Rec<D, NR>::WOFF + r]
-                                   : 0.f;
+            wt[lane * NR + r] = ok ? reinterpret_cast<const float*>(a.rec + (int64_t)s * a.rec_f4)[a.woff + r] : 0.f;
         __syncwarp();
 #pragma unroll 4
         for (int row = 0; row < 32; ++row) {
@@ -184,22 +191,164 @@ __device__ __forceinline__ float kval(float q, const KernelParams& kp) {
 constexpr long long kWaitCycles = 2000000000;  // ~1 s at 2 GHz: a wait this long is a fault
 
 // T targets per thread (128 / T threads per 128-target block); ST-stage ring of CH-point chunks.
+// Thread tl owns targets tl + (128 / T) j, so the targets of slot j of one warp form one
+// 32-target group -- one word of an entry's mask.  Accumulators hold pairs of right-hand sides
+// (float2, packed FMA) when NR >= 8.  Passes of 16 or 32 right-hand sides (SEL) zero the
+// kernel value of a target outside an entry's mask instead of keeping a second set of
+// per-entry accumulators.
 template <int D, int NR, int T>
 struct NearShape {
     static constexpr int F4 = Rec<D, NR>::F4;
     static constexpr int THREADS = kTB / T;
-    static constexpr int CH = F4 == 1 ? 256 : 128;
+    static constexpr int CH = F4 == 1 ? 256 : (F4 >= 9 ? 64 : 128);
     static constexpr int ST = T >= 4 ? 2 : 3;
+    static constexpr bool SEL = NR >= 16;
+    static constexpr bool PAIRS = NR >= 8;
+    static constexpr int NA = PAIRS ? NR / 2 : NR;  // accumulators per target
+    using Acc = typename std::conditional<PAIRS, float2, float>::type;
+    static constexpr int MINB = 1;
 };
 
-// Near field of one target block: for each near entry (leaf, mask), every point of the leaf is
-// streamed through shared memory by the bulk-copy engine (3-stage mbarrier ring, issued by
-// thread 0) and each thread accumulates K(|x_t - x_s|) w_s for its two targets.
-template <int D, int KIND, int NR, int T>
-__global__ void __launch_bounds__(NearShape<D, NR, T>::THREADS) near_kernel(MvmArgs a, KernelParams kp_all) {
+__device__ __forceinline__ float2 ffma2(float a, float2 w, float2 c) { return __ffma2_rn(make_float2(a, a), w, c); }
+
+// One staged chunk of n source records against this thread's targets.  Slot j takes part only
+// when bit j of JM is set (its warp's 32-target group has an active target for this entry);
+// within a slot, act[j] gates the target itself.
+template <int D, int KIND, int NR, int T, unsigned JM>
+__device__ __forceinline__ void near_chunk(const float4* __restrict__ sb, int n, const float (&tx)[T][4],
+                                           const bool (&act)[T], typename NearShape<D, NR, T>::Acc (&acc)[T][NearShape<D, NR, T>::NA],
+                                           const KernelParams& kp) {
     using R = Rec<D, NR>;
     using Sh = NearShape<D, NR, T>;
-    constexpr int F4 = R::F4, CH = Sh::CH, ST = Sh::ST, NTH = Sh::THREADS;
+    constexpr int F4 = R::F4;
+    auto kvalue = [&](const float4& sx, int j) {
+        const float dx = tx[j][0] - sx.x, dy = tx[j][1] - sx.y, dz = tx[j][2] - sx.z;
+        float q = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+        if (D == 4) { const float dw = tx[j][3] - sx.w; q = fmaf(dw, dw, q); }
+        return kval<KIND>(q, kp);
+    };
+    if constexpr (Sh::SEL) {
+        // One kernel value per (target, source) serves all NR right-hand sides.  Sources go in
+        // batches of KB: the KB kernel values (independent dependency chains through the MUFU)
+        // first, then the packed FMAs, so that neither waits on the other's latency.
+        constexpr int KB = 8;
+        auto fmas = [&](int i, const float (&kv)[T]) {
+            const float4* wv = sb + i * F4 + 1;
+#pragma unroll
+            for (int r4 = 0; r4 < NR / 4; ++r4) {
+                const float4 w4 = wv[r4];
+                const float2 wa = make_float2(w4.x, w4.y), wb = make_float2(w4.z, w4.w);
+#pragma unroll
+                for (int j = 0; j < T; ++j)
+                    if ((JM >> j) & 1u) {
+                        acc[j][2 * r4] = ffma2(kv[j], wa, acc[j][2 * r4]);
+                        acc[j][2 * r4 + 1] = ffma2(kv[j], wb, acc[j][2 * r4 + 1]);
+                    }
+            }
+        };
+        const int nfull = n & ~(KB - 1);
+#pragma unroll 1
+        for (int i0 = 0; i0 < nfull; i0 += KB) {
+            float kb[KB][T];
+#pragma unroll
+            for (int b = 0; b < KB; ++b) {
+                const float4 sx = sb[(i0 + b) * F4];
+#pragma unroll
+                for (int j = 0; j < T; ++j)
+                    if ((JM >> j) & 1u) kb[b][j] = act[j] ? kvalue(sx, j) : 0.0f;
+            }
+#pragma unroll
+            for (int b = 0; b < KB; ++b) fmas(i0 + b, kb[b]);
+        }
+#pragma unroll 1
+        for (int i = nfull; i < n; ++i) {
+            const float4 sx = sb[i * F4];
+            float kv[T];
+#pragma unroll
+            for (int j = 0; j < T; ++j)
+                if ((JM >> j) & 1u) kv[j] = act[j] ? kvalue(sx, j) : 0.0f;
+            fmas(i, kv);
+        }
+    } else if constexpr (Sh::PAIRS) {
+        float2 ea[T][Sh::NA];
+#pragma unroll
+        for (int j = 0; j < T; ++j)
+#pragma unroll
+            for (int r = 0; r < Sh::NA; ++r) ea[j][r] = make_float2(0.f, 0.f);
+#pragma unroll 4
+        for (int i = 0; i < n; ++i) {
+            const float4 sx = sb[i * F4];
+            float kv[T];
+#pragma unroll
+            for (int j = 0; j < T; ++j)
+                if ((JM >> j) & 1u) kv[j] = kvalue(sx, j);
+            const float4* wv = sb + i * F4 + 1;
+#pragma unroll
+            for (int r4 = 0; r4 < NR / 4; ++r4) {
+                const float4 w4 = wv[r4];
+                const float2 wa = make_float2(w4.x, w4.y), wb = make_float2(w4.z, w4.w);
+#pragma unroll
+                for (int j = 0; j < T; ++j)
+                    if ((JM >> j) & 1u) {
+                        ea[j][2 * r4] = ffma2(kv[j], wa, ea[j][2 * r4]);
+                        ea[j][2 * r4 + 1] = ffma2(kv[j], wb, ea[j][2 * r4 + 1]);
+                    }
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < T; ++j)
+            if (((JM >> j) & 1u) && act[j])
+#pragma unroll
+                for (int r = 0; r < Sh::NA; ++r) {
+                    acc[j][r].x += ea[j][r].x;
+                    acc[j][r].y += ea[j][r].y;
+                }
+    } else {
+        float ea[T][NR];
+#pragma unroll
+        for (int j = 0; j < T; ++j)
+#pragma unroll
+            for (int r = 0; r < NR; ++r) ea[j][r] = 0.f;
+#pragma unroll 4
+        for (int i = 0; i < n; ++i) {
+            const float4 sx = sb[i * F4];
+            float kv[T];
+#pragma unroll
+            for (int j = 0; j < T; ++j)
+                if ((JM >> j) & 1u) kv[j] = kvalue(sx, j);
+            if (D == 3 && NR == 1) {
+#pragma unroll
+                for (int j = 0; j < T; ++j)
+                    if ((JM >> j) & 1u) ea[j][0] = fmaf(kv[j], sx.w, ea[j][0]);
+            } else {
+                const float* wv = reinterpret_cast<const float*>(sb + i * F4) + R::WOFF;
+#pragma unroll
+                for (int r = 0; r < NR; ++r) {
+                    const float wr = wv[r];
+#pragma unroll
+                    for (int j = 0; j < T; ++j)
+                        if ((JM >> j) & 1u) ea[j][r] = fmaf(kv[j], wr, ea[j][r]);
+                }
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < T; ++j)
+            if (((JM >> j) & 1u) && act[j])
+#pragma unroll
+                for (int r = 0; r < NR; ++r) acc[j][r] += ea[j][r];
+    }
+}
+
+// Near field of one target block: for each near entry (leaf, mask), every point of the leaf is
+// streamed through shared memory by the bulk-copy engine (ST-stage mbarrier ring, issued by
+// thread 0) and each thread accumulates K(|x_t - x_s|) w_s for its T targets.
+template <int D, int KIND, int NR, int T>
+__global__ void __launch_bounds__(NearShape<D, NR, T>::THREADS, NearShape<D, NR, T>::MINB) near_kernel(MvmArgs a, KernelParams kp_all) {
+    using R = Rec<D, NR>;
+    using Sh = NearShape<D, NR, T>;
+    constexpr int F4 = R::F4, CH = Sh::CH, ST = Sh::ST, NTH = Sh::THREADS, NA = Sh::NA;
+    static_assert(!Sh::PAIRS || (R::WOFF == 4 && NR % 4 == 0), "multi-RHS passes read whole float4s of weights");
+    using Acc = typename Sh::Acc;
     __shared__ __align__(128) float4 buf[ST][CH * F4];
     __shared__ __align__(8) uint64_t full[ST];
     const int tl = threadIdx.x;
@@ -215,11 +364,14 @@ __global__ void __launch_bounds__(NearShape<D, NR, T>::THREADS) near_kernel(MvmA
         const float4 x = valid[j] ? a.xs[t] : make_float4(0.f, 0.f, 0.f, 0.f);
         tx[j][0] = x.x * kp.sig; tx[j][1] = x.y * kp.sig; tx[j][2] = x.z * kp.sig; tx[j][3] = x.w * kp.sig;
     }
-    float acc[T][NR];
+    Acc acc[T][NA];
 #pragma unroll
     for (int j = 0; j < T; ++j)
 #pragma unroll
-        for (int r = 0; r < NR; ++r) acc[j][r] = 0.f;
+        for (int r = 0; r < NA; ++r) {
+            if constexpr (Sh::PAIRS) acc[j][r] = make_float2(0.f, 0.f);
+            else acc[j][r] = 0.f;
+        }
     const int64_t e0 = a.near_off[blk], e1 = a.near_off[blk + 1];
     bool ok_all = true;
     if (e0 < e1) {
@@ -254,49 +406,26 @@ __global__ void __launch_bounds__(NearShape<D, NR, T>::THREADS) near_kernel(MvmA
         for (int64_t e = e0; e < e1 && ok_all; ++e) {
             const int2 ent = a.near_ent[e];
             bool act[T];
+            unsigned jm = 0;  // slots whose 32-target group has an active target (warp-uniform)
 #pragma unroll
-            for (int j = 0; j < T; ++j) act[j] = valid[j] && entry_active(ent.y, a.masks, tl + NTH * j);
+            for (int j = 0; j < T; ++j) {
+                act[j] = valid[j] && entry_active(ent.y, a.masks, tl + NTH * j);
+                if (__any_sync(0xffffffffu, act[j])) jm |= 1u << j;
+            }
             const int s0 = a.nd_begin[ent.x], s1 = a.nd_end[ent.x];
             for (int cb = s0; cb < s1; cb += CH, ++k) {
                 const int n = min(CH, s1 - cb);
                 const int stage = k % ST;
                 const bool ok = ptx::mbar_wait_bounded(&full[stage], (uint32_t)((k / ST) & 1), kWaitCycles);
                 if (ok) {
-                    float ea[T][NR];
-#pragma unroll
-                    for (int j = 0; j < T; ++j)
-#pragma unroll
-                        for (int r = 0; r < NR; ++r) ea[j][r] = 0.f;
                     const float4* sb = &buf[stage][0];
-#pragma unroll 4
-                    for (int i = 0; i < n; ++i) {
-                        const float4 sx = sb[i * F4];
-                        float kv[T];
-#pragma unroll
-                        for (int j = 0; j < T; ++j) {
-                            const float dx = tx[j][0] - sx.x, dy = tx[j][1] - sx.y, dz = tx[j][2] - sx.z;
-                            float q = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-                            if (D == 4) { const float dw = tx[j][3] - sx.w; q = fmaf(dw, dw, q); }
-                            kv[j] = kval<KIND>(q, kp);
-                        }
-                        if (D == 3 && NR == 1) {
-#pragma unroll
-                            for (int j = 0; j < T; ++j) ea[j][0] = fmaf(kv[j], sx.w, ea[j][0]);
-                        } else {
-                            const float* wv = reinterpret_cast<const float*>(sb + i * F4) + R::WOFF;
-#pragma unroll
-                            for (int r = 0; r < NR; ++r) {
-                                const float wr = wv[r];
-#pragma unroll
-                                for (int j = 0; j < T; ++j) ea[j][r] = fmaf(kv[j], wr, ea[j][r]);
-                            }
-                        }
+                    if constexpr (T == 2) {
+                        if (jm == 3u) near_chunk<D, KIND, NR, T, 3u>(sb, n, tx, act, acc, kp);
+                        else if (jm == 1u) near_chunk<D, KIND, NR, T, 1u>(sb, n, tx, act, acc, kp);
+                        else if (jm == 2u) near_chunk<D, KIND, NR, T, 2u>(sb, n, tx, act, acc, kp);
+                    } else {
+                        if (jm != 0u) near_chunk<D, KIND, NR, T, (1u << T) - 1u>(sb, n, tx, act, acc, kp);
                     }
-#pragma unroll
-                    for (int j = 0; j < T; ++j)
-                        if (act[j])
-#pragma unroll
-                            for (int r = 0; r < NR; ++r) acc[j][r] += ea[j][r];
                 }
                 ok_all = __syncthreads_and(ok) != 0;  // every thread is done with this stage
                 if (!ok_all) break;
@@ -319,9 +448,316 @@ __global__ void __launch_bounds__(NearShape<D, NR, T>::THREADS) near_kernel(MvmA
 #pragma unroll
     for (int j = 0; j < T; ++j) {
         const int t = rg.x + tl + NTH * j;
+        if (valid[j]) {
+#pragma unroll
+            for (int r = 0; r < NR; ++r) {
+                float v;
+                if constexpr (Sh::PAIRS) v = (r & 1) ? acc[j][r / 2].y : acc[j][r / 2].x;
+                else v = acc[j][r];
+                a.ynear[(int64_t)r * a.N + t] = v * kp.scale;
+            }
+        }
+    }
+}
+
+// Multi-RHS near field (passes of 8, 16 or 32 right-hand sides).  One warp per CTA handles 32 T
+// targets of a target block -- T 32-target groups, i.e. T words of every entry's mask -- with
+// its own ST-stage bulk-copy ring.  An entry whose mask leaves all its groups empty is
+// skipped outright (no copy, no wait), and no warp waits for another: the per-target near sets
+// of a block differ, so a block-wide pipeline would make every warp wait through entries that
+// only its neighbours need.
+template <int D, int NR>
+struct NearWideShape {
+    static constexpr int T = NR >= 32 ? 1 : 2;     // targets per lane (32-target groups per CTA)
+    static constexpr int F4 = Rec<D, NR>::F4;
+    static constexpr int SPLIT = kTB / (32 * T);   // CTAs per 128-target block
+    static constexpr int CH = F4 >= 9 ? 32 : 64;   // sources per stage
+    static constexpr int ST = 3;
+};
+
+template <int D, int KIND, int NR>
+__global__ void __launch_bounds__(32, 20) near_wide_kernel(MvmArgs a, KernelParams kp_all) {
+    using R = Rec<D, NR>;
+    using W = NearWideShape<D, NR>;
+    using Sh = NearShape<D, NR, W::T>;
+    constexpr int T = W::T, F4 = R::F4, CH = W::CH, ST = W::ST, NA = Sh::NA;
+    static_assert(Sh::PAIRS, "multi-RHS passes only");
+    __shared__ __align__(128) float4 buf[ST][CH * F4];
+    __shared__ __align__(8) uint64_t full[ST];
+    const int lane = threadIdx.x;
+    const int64_t gi = blockIdx.x / W::SPLIT;
+    const int w0 = (blockIdx.x % W::SPLIT) * T;  // first mask word (32-target group) of this CTA
+    const int64_t blk = a.blk_list ? (int64_t)a.blk_list[gi] : gi;
+    const KernelParams kp = block_params(a, blk, kp_all);
+    const int2 rg = a.blk[blk];
+    float tx[T][4];
+    bool valid[T];
+#pragma unroll
+    for (int j = 0; j < T; ++j) {
+        const int t = rg.x + 32 * (w0 + j) + lane;
+        valid[j] = t < rg.y;
+        const float4 x = valid[j] ? a.xs[t] : make_float4(0.f, 0.f, 0.f, 0.f);
+        tx[j][0] = x.x * kp.sig; tx[j][1] = x.y * kp.sig; tx[j][2] = x.z * kp.sig; tx[j][3] = x.w * kp.sig;
+    }
+    // bit j: group w0 + j has an active target for the entry with this mask (uniform over the warp)
+    auto groups = [&](int mask) -> unsigned {
+        unsigned m = 0;
+#pragma unroll
+        for (int j = 0; j < T; ++j) {
+            const bool any = mask < 0 ? (rg.x + 32 * (w0 + j) < rg.y)
+                                      : (__ldg(&a.masks[(int64_t)mask * kMaskWords + w0 + j]) != 0u);
+            if (any) m |= 1u << j;
+        }
+        return m;
+    };
+    typename Sh::Acc acc[T][NA];
+#pragma unroll
+    for (int j = 0; j < T; ++j)
+#pragma unroll
+        for (int r = 0; r < NA; ++r) acc[j][r] = make_float2(0.f, 0.f);
+    const int64_t e0 = a.near_off[blk], e1 = a.near_off[blk + 1];
+    if (lane == 0) {
+#pragma unroll
+        for (int s = 0; s < ST; ++s) ptx::mbar_init(&full[s], 1);
+        ptx::fence_mbar_init();
+    }
+    __syncwarp();
+    // producer cursor (lane 0): entry pe, next source pcb; entries without an active group are passed over
+    int64_t pe = e0;
+    int pcb = 0;
+    int issued = 0;
+    auto settle = [&]() {
+        while (pe < e1 && groups(a.near_ent[pe].y) == 0u) ++pe;
+        if (pe < e1) pcb = a.nd_begin[a.near_ent[pe].x];
+    };
+    auto issue = [&](int stage) {
+        while (pe < e1) {
+            const int s1 = a.nd_end[a.near_ent[pe].x];
+            if (pcb < s1) {
+                const int n = min(CH, s1 - pcb);
+                const uint32_t bytes = (uint32_t)n * F4 * 16u;
+                ptx::mbar_arrive_expect_tx(&full[stage], bytes);
+                ptx::bulk_g2s(&buf[stage][0], a.rec + (int64_t)pcb * F4, bytes, &full[stage]);
+                pcb += n;
+                ++issued;
+                return;
+            }
+            ++pe;
+            settle();
+        }
+    };
+    if (lane == 0) {
+        settle();
+        for (int s = 0; s < ST; ++s) issue(s);
+    }
+    int k = 0;
+    bool ok_all = true;
+    for (int64_t e = e0; e < e1 && ok_all; ++e) {
+        const int2 ent = a.near_ent[e];
+        const unsigned jm = groups(ent.y);
+        if (jm == 0u) continue;
+        bool act[T];
+#pragma unroll
+        for (int j = 0; j < T; ++j) act[j] = valid[j] && entry_active(ent.y, a.masks, 32 * (w0 + j) + lane);
+        const int s0 = a.nd_begin[ent.x], s1 = a.nd_end[ent.x];
+        for (int cb = s0; cb < s1; cb += CH, ++k) {
+            const int n = min(CH, s1 - cb);
+            const int stage = k % ST;
+            const bool ok = ptx::mbar_wait_bounded(&full[stage], (uint32_t)((k / ST) & 1), kWaitCycles);
+            ok_all = __all_sync(0xffffffffu, ok);
+            if (!ok_all) break;
+            const float4* sb = &buf[stage][0];
+            if constexpr (T == 1) {
+                near_chunk<D, KIND, NR, T, 1u>(sb, n, tx, act, acc, kp);
+            } else {
+                if (jm == 3u) near_chunk<D, KIND, NR, T, 3u>(sb, n, tx, act, acc, kp);
+                else if (jm == 1u) near_chunk<D, KIND, NR, T, 1u>(sb, n, tx, act, acc, kp);
+                else near_chunk<D, KIND, NR, T, 2u>(sb, n, tx, act, acc, kp);
+            }
+            __syncwarp();  // every lane is done with this stage
+            if (lane == 0) {
+                ptx::fence_proxy_async_smem();
+                issue(stage);
+            }
+        }
+    }
+    if (!ok_all) {
+        // A wait ran out: record it, let the copies still in flight land (bounded), stop.
+        if (lane == 0) {
+            atomicExch(a.err, 1);
+            for (int q = k; q < issued; ++q)
+                ptx::mbar_wait_bounded(&full[q % ST], (uint32_t)((q / ST) & 1), kWaitCycles);
+        }
+        return;
+    }
+#pragma unroll
+    for (int j = 0; j < T; ++j) {
+        const int t = rg.x + 32 * (w0 + j) + lane;
         if (valid[j])
 #pragma unroll
-            for (int r = 0; r < NR; ++r) a.ynear[(int64_t)r * a.N + t] = acc[j][r] * kp.scale;
+            for (int r = 0; r < NR; ++r)
+                a.ynear[(int64_t)r * a.N + t] = ((r & 1) ? acc[j][r / 2].y : acc[j][r / 2].x) * kp.scale;
+    }
+}
+
+// Near field of 16- and 32-wide passes as a register-tiled product.  One warp per CTA handles one
+// 32-target group (one word of every entry's mask) with its own ST-stage bulk-copy ring, so a
+// warp passes over the entries its group does not need without waiting for anyone.  Per batch
+// of KB staged sources:
+//   A: lane = target: KB kernel values K[b][lane] (zero outside the entry's mask) -> shared tile;
+//   B: lane = (i, j): targets 4i..4i+3 x right-hand sides (NR/4) j..: acc += K[b][4i..] w[b][..]
+//      (packed FMAs, 4 x NR/4 independent accumulators per lane).
+template <int D, int NR>
+struct NearTileShape {
+    static constexpr int F4 = Rec<D, NR>::F4;
+    static constexpr int SPLIT = kTB / 32;          // CTAs per 128-target block
+    static constexpr int CH = F4 >= 9 ? 16 : 32;    // sources per stage (small: ~8 KB of shared
+    static constexpr int ST = 3;                    // memory per CTA keeps ~25 warps per SM)
+    static constexpr int KB = 8;                    // sources per kernel-value batch
+    static constexpr int RL = NR / 4;               // right-hand sides per lane
+};
+
+template <int D, int KIND, int NR>
+__global__ void __launch_bounds__(32) near_tile_kernel(MvmArgs a, KernelParams kp_all) {
+    using R = Rec<D, NR>;
+    using S = NearTileShape<D, NR>;
+    constexpr int F4 = R::F4, CH = S::CH, ST = S::ST, KB = S::KB, RL = S::RL;
+    static_assert(R::WOFF == 4 && NR % 8 == 0, "whole float4s of weights, pairs per lane");
+    __shared__ __align__(128) float4 buf[ST][CH * F4];
+    __shared__ __align__(16) float Ks[KB][32];
+    __shared__ __align__(8) uint64_t full[ST];
+    const int lane = threadIdx.x;
+    const int ti = lane >> 2, rj = lane & 3;        // phase-B tile coordinates
+    const int64_t gi = blockIdx.x / S::SPLIT;
+    const int grp = blockIdx.x % S::SPLIT;          // the 32-target group (mask word) of this CTA
+    const int64_t blk = a.blk_list ? (int64_t)a.blk_list[gi] : gi;
+    const KernelParams kp = block_params(a, blk, kp_all);
+    const int2 rg = a.blk[blk];
+    const int t0 = rg.x + 32 * grp;                 // first target of the group
+    const bool valid = t0 + lane < rg.y;
+    float tx[4];
+    {
+        const float4 x = valid ? a.xs[t0 + lane] : make_float4(0.f, 0.f, 0.f, 0.f);
+        tx[0] = x.x * kp.sig; tx[1] = x.y * kp.sig; tx[2] = x.z * kp.sig; tx[3] = x.w * kp.sig;
+    }
+    auto group_on = [&](int mask) -> bool {
+        return mask < 0 ? (t0 < rg.y) : (__ldg(&a.masks[(int64_t)mask * kMaskWords + grp]) != 0u);
+    };
+    float2 acc[4][RL / 2];
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+#pragma unroll
+        for (int r = 0; r < RL / 2; ++r) acc[q][r] = make_float2(0.f, 0.f);
+    const int64_t e0 = a.near_off[blk], e1 = a.near_off[blk + 1];
+    if (lane == 0) {
+#pragma unroll
+        for (int s = 0; s < ST; ++s) ptx::mbar_init(&full[s], 1);
+        ptx::fence_mbar_init();
+    }
+    __syncwarp();
+    int64_t pe = e0;
+    int pcb = 0;
+    int issued = 0;
+    auto settle = [&]() {
+        while (pe < e1 && !group_on(a.near_ent[pe].y)) ++pe;
+        if (pe < e1) pcb = a.nd_begin[a.near_ent[pe].x];
+    };
+    auto issue = [&](int stage) {
+        while (pe < e1) {
+            const int s1 = a.nd_end[a.near_ent[pe].x];
+            if (pcb < s1) {
+                const int n = min(CH, s1 - pcb);
+                const uint32_t bytes = (uint32_t)n * F4 * 16u;
+                ptx::mbar_arrive_expect_tx(&full[stage], bytes);
+                ptx::bulk_g2s(&buf[stage][0], a.rec + (int64_t)pcb * F4, bytes, &full[stage]);
+                pcb += n;
+                ++issued;
+                return;
+            }
+            ++pe;
+            settle();
+        }
+    };
+    if (lane == 0) {
+        settle();
+        for (int s = 0; s < ST; ++s) issue(s);
+    }
+    int k = 0;
+    bool ok_all = true;
+    for (int64_t e = e0; e < e1 && ok_all; ++e) {
+        const int2 ent = a.near_ent[e];
+        if (!group_on(ent.y)) continue;
+        const bool act = valid && entry_active(ent.y, a.masks, 32 * grp + lane);
+        const int s0 = a.nd_begin[ent.x], s1 = a.nd_end[ent.x];
+        for (int cb = s0; cb < s1; cb += CH, ++k) {
+            const int n = min(CH, s1 - cb);
+            const int stage = k % ST;
+            const bool ok = ptx::mbar_wait_bounded(&full[stage], (uint32_t)((k / ST) & 1), kWaitCycles);
+            ok_all = __all_sync(0xffffffffu, ok);
+            if (!ok_all) break;
+            const float4* sb = &buf[stage][0];
+            for (int i0 = 0; i0 < n; i0 += KB) {
+                const int nb = min(KB, n - i0);
+                // A: kernel values of this lane's target against the batch
+#pragma unroll
+                for (int b = 0; b < KB; ++b) {
+                    float kv = 0.0f;
+                    if (b < nb && act) {
+                        const float4 sx = sb[(i0 + b) * F4];
+                        const float dx = tx[0] - sx.x, dy = tx[1] - sx.y, dz = tx[2] - sx.z;
+                        float q = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+                        if (D == 4) { const float dw = tx[3] - sx.w; q = fmaf(dw, dw, q); }
+                        kv = kval<KIND>(q, kp);
+                    }
+                    Ks[b][lane] = kv;
+                }
+                __syncwarp();
+                // B: 4 targets x RL right-hand sides per lane
+#pragma unroll
+                for (int b = 0; b < KB; ++b) {
+                    if (b < nb) {
+                        const float4 kk = *reinterpret_cast<const float4*>(&Ks[b][4 * ti]);
+                        const float4* wv = sb + (i0 + b) * F4 + 1 + rj * (RL / 4);
+#pragma unroll
+                        for (int r4 = 0; r4 < RL / 4; ++r4) {
+                            const float4 w4 = wv[r4];
+                            const float2 wa = make_float2(w4.x, w4.y), wb = make_float2(w4.z, w4.w);
+                            acc[0][2 * r4] = ffma2(kk.x, wa, acc[0][2 * r4]);
+                            acc[0][2 * r4 + 1] = ffma2(kk.x, wb, acc[0][2 * r4 + 1]);
+                            acc[1][2 * r4] = ffma2(kk.y, wa, acc[1][2 * r4]);
+                            acc[1][2 * r4 + 1] = ffma2(kk.y, wb, acc[1][2 * r4 + 1]);
+                            acc[2][2 * r4] = ffma2(kk.z, wa, acc[2][2 * r4]);
+                            acc[2][2 * r4 + 1] = ffma2(kk.z, wb, acc[2][2 * r4 + 1]);
+                            acc[3][2 * r4] = ffma2(kk.w, wa, acc[3][2 * r4]);
+                            acc[3][2 * r4 + 1] = ffma2(kk.w, wb, acc[3][2 * r4 + 1]);
+                        }
+                    }
+                }
+                __syncwarp();  // Ks is rewritten by the next batch
+            }
+            if (lane == 0) {
+                ptx::fence_proxy_async_smem();
+                issue(stage);
+            }
+        }
+    }
+    if (!ok_all) {
+        if (lane == 0) {
+            atomicExch(a.err, 1);
+            for (int q = k; q < issued; ++q)
+                ptx::mbar_wait_bounded(&full[q % ST], (uint32_t)((q / ST) & 1), kWaitCycles);
+        }
+        return;
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const int t = t0 + 4 * ti + q;
+        if (t < rg.y)
+#pragma unroll
+            for (int r = 0; r < RL; ++r) {
+                const float v = (r & 1) ? acc[q][r / 2].y : acc[q][r / 2].x;
+                a.ynear[(int64_t)(rj * RL + r) * a.N + t] = v * kp.scale;
+            }
     }
 }
 
@@ -410,10 +846,9 @@ __global__ void __launch_bounds__(kTB) far_kernel(MvmArgs a, KernelParams kp_all
         }
     }
     if (valid) {
-        const int64_t o = a.perm[t];
 #pragma unroll
         for (int r = 0; r < NR; ++r)
-            if (r < a.nr) a.y[(int64_t)r * a.N + o] = a.ynear[(int64_t)r * a.N + t] + acc[r];
+            if (r < a.nr) a.yfar[(int64_t)r * a.N + t] = acc[r];
     }
 }
 
@@ -507,10 +942,9 @@ __global__ void __launch_bounds__(kTB) far_mr_kernel(MvmArgs a, KernelParams kp_
         }
     }
     if (valid) {
-        const int64_t o = a.perm[t];
 #pragma unroll
         for (int r = 0; r < 8; ++r)
-            if (r < a.nr) a.y[(int64_t)r * a.N + o] = a.ynear[(int64_t)r * a.N + t] + acc[r];
+            if (r < a.nr) a.yfar[(int64_t)r * a.N + t] = acc[r];
     }
 }
 

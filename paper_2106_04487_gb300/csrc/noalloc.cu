@@ -44,9 +44,11 @@ int scratch_for_current_device(float** out) {
 extern "C" int fkt_mvm_noalloc(fkt_plan_t plan, const float* w, float* y, int nrhs) {
     using namespace fkt;
     if (!plan || !w || !y || nrhs < 1 || nrhs > kMaxRhs || w == y) return FKT_ERR_INVALID_ARG;
-    size_t f[5];
+    size_t f[kMvmBufs];
     mvm_buffer_floats(plan, nrhs, f);   // each part is already a multiple of 64 floats (256 bytes)
-    if (f[0] + f[1] + f[2] + f[3] + f[4] > kScratchFloats) return FKT_ERR_SCRATCH_LIMIT;
+    size_t total = 0;
+    for (size_t v : f) total += v;
+    if (total > kScratchFloats) return FKT_ERR_SCRATCH_LIMIT;
     float* base = nullptr;
     int rc = scratch_for_current_device(&base);
     if (rc) return rc;
@@ -57,5 +59,6 @@ extern "C" int fkt_mvm_noalloc(fkt_plan_t plan, const float* w, float* y, int nr
     B.mult = (q += f[1]);
     B.part = (q += f[2]);
     B.image = reinterpret_cast<unsigned char*>(q += f[3]);
+    B.yfar = (q += f[4]);
     return run_mvm(plan, B, w, y, nrhs, false);
 }

@@ -54,7 +54,7 @@ def test_noalloc_matches_fkt_mvm_on_two_calls(fkt, nrhs):
 def test_noalloc_rejects_requests_beyond_its_scratch(fkt):
     import torch
 
-    n = 300000                                        # 64 right-hand sides need > 32 MiB
+    n = 300000                                        # 64 right-hand sides need > 48 MiB
     X = torch.from_numpy(inputs.uniform_cube(n, 3, seed=24)).cuda()
     plan = fkt.Plan(X, "gaussian", lengthscale=0.1, p=2, leaf_size=512, theta=0.5)
     w = torch.zeros((64, n), device="cuda")
