@@ -38,6 +38,16 @@ from paper_2106_04487_gb300 import inputs  # noqa: E402
 KERNELS = {"matern32": ("matern32", 0.2), "cauchy": ("cauchy", 0.05)}
 PASS = 32  # right-hand sides per pass of the library
 
+# DRAM bytes (read + write) per launch of a kernel from one ncu capture, keyed by kernel and
+# workload (kernel, p, theta, leaf, nrhs, N); see profiles/near_tile_matern1m_p6_theta0375_nrhs32.md.
+# Any other workload reports null.
+PROFILED_TRAFFIC = {("near_tile_kernel<3,matern32,32>", "matern32", 6, 0.375, 256, 32, 1_000_000): 1.339e9 + 0.136e9}
+
+
+def near_kernel_name(kname: str, nw: int) -> str:
+    base = "near_kernel" if nw == 1 else "near_wide_kernel" if nw == 8 else "near_tile_kernel"
+    return f"{base}<3,{kname},{nw}>"
+
 
 def launches_per_step(nrhs: int, far_precision: str) -> int:
     """Kernels the library launches per fkt_mvm.  Per pass of up to 32 right-hand sides: permute
@@ -322,8 +332,11 @@ def run_ours(a):
     peak_pairs = nsm * sm_max * 1e6 / slots_per_pair
     near_pairs = stats["near_pairs"] * passes  # one launch per pass; its kernel value serves the pass
     near_ach = near_pairs / (head["near_ms"] / 1e3)
-    near_roof = {"kernel": f"near_kernel<3,{kname},{nw}>", "bound": "alu", "achieved": near_ach / 1e9,
-                 "peak": peak_pairs / 1e9, "unit": "Gpair/s", "frac": near_ach / peak_pairs, "traffic": None,
+    near_name = near_kernel_name(kname, nw)
+    traffic = PROFILED_TRAFFIC.get((near_name, kname, a.p, a.theta, a.leaf, a.nrhs, a.n))
+    near_roof = {"kernel": near_name, "bound": "alu", "achieved": near_ach / 1e9,
+                 "peak": peak_pairs / 1e9, "unit": "Gpair/s", "frac": near_ach / peak_pairs, "traffic": traffic,
+                 "traffic_unit": "bytes per launch (ncu dram__bytes_read + write)",
                  "ms_per_step": head["near_ms"],
                  "peak_source": f"{nsm} SMs x {sm_max:.0f} MHz / max({fp32_ops}/128 FP32, {mufu_ops}/16 MUFU) "
                                 f"SM-clocks per pair ({src} clock)"}
