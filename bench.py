@@ -11,7 +11,8 @@ flushed between timed steps (a 256 MiB write outside the timed events).  Prints 
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
                     [--kernel matern32|cauchy] [--p P] [--theta T] [--leaf M] [--nrhs R]
-                    [--far-precision bf16x3|tf32|bf16|fp32] [--compare fp32|none]
+                    [--far-precision bf16x3|tf32|bf16|fp32] [--near-precision tf32x3|fp32]
+                    [--compare fp32|none]
 
 --impl reference times the CPU float64 oracle (the slow reference program) on a bounded sample
 of the same workload.  Multi-GPU runs are independent replicas (one plan per rank, no
@@ -39,12 +40,15 @@ KERNELS = {"matern32": ("matern32", 0.2), "cauchy": ("cauchy", 0.05)}
 PASS = 32  # right-hand sides per pass of the library
 
 # DRAM bytes (read + write) per launch of a kernel from one ncu capture, keyed by kernel and
-# workload (kernel, p, theta, leaf, nrhs, N); see profiles/near_tile_matern1m_p6_theta0375_nrhs32.md.
+# workload (kernel, p, theta, leaf, nrhs, N); see profiles/near_tc_matern1m_p6_theta0375_nrhs32.md.
 # Any other workload reports null.
-PROFILED_TRAFFIC = {("near_tile_kernel<3,matern32,32>", "matern32", 6, 0.375, 256, 32, 1_000_000): 1.339e9 + 0.136e9}
+PROFILED_TRAFFIC = {("near_tile_kernel<3,matern32,32>", "matern32", 6, 0.375, 256, 32, 1_000_000): 1.339e9 + 0.136e9,
+                    ("near_tc_kernel<3,matern32>", "matern32", 6, 0.375, 256, 32, 1_000_000): 0.899e9 + 0.130e9}
 
 
-def near_kernel_name(kname: str, nw: int) -> str:
+def near_kernel_name(kname: str, nw: int, near_precision: str = "fp32") -> str:
+    if nw == 32 and near_precision == "tf32x3":
+        return f"near_tc_kernel<3,{kname}>"
     base = "near_kernel" if nw == 1 else "near_wide_kernel" if nw == 8 else "near_tile_kernel"
     return f"{base}<3,{kname},{nw}>"
 
@@ -76,8 +80,10 @@ def parse():
     ap.add_argument("--nrhs", type=int, default=32)
     ap.add_argument("--near-tpt", type=int, default=2, choices=[2, 4])
     ap.add_argument("--far-precision", default="bf16x3", choices=["bf16x3", "tf32", "bf16", "fp32"])
+    ap.add_argument("--near-precision", default="tf32x3", choices=["tf32x3", "fp32"],
+                    help="near-field contraction of 32-wide passes: tensor cores (TF32 hi/lo) or CUDA cores")
     ap.add_argument("--compare", default="fp32", choices=["fp32", "none"],
-                    help="far-field form timed beside the headline one on the same plan")
+                    help="plain float32 form (near and far on the CUDA cores) timed beside the headline one")
     ap.add_argument("--second-kernel", default="cauchy", choices=list(KERNELS) + ["none"])
     ap.add_argument("--n", type=int, default=1_000_000)
     ap.add_argument("--err-targets", type=int, default=10000)
@@ -88,7 +94,7 @@ def parse():
 def workload_name(a, kernel=None):
     k, ell = KERNELS[kernel or a.kernel]
     return (f"{k} l={ell} d=3 N={a.n} gaussian-mixture(10 comps, std 0.05) p={a.p} leaf={a.leaf} "
-            f"theta={a.theta} nrhs={a.nrhs} near_tpt={a.near_tpt} far={a.far_precision}")
+            f"theta={a.theta} nrhs={a.nrhs} near={a.near_precision} far={a.far_precision}")
 
 
 def load_peaks():
@@ -154,16 +160,18 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def near_pair_cost(kernel: str, nw: int):
+def near_pair_cost(kernel: str, nw: int, tensor: bool = False):
     """Lower bound on SM issue slots per near-field pair for a pass of nw right-hand sides:
     (FP32-pipe lane-ops, MUFU lane-ops).
 
     Per pair the method needs d = 3 subtractions, |x|^2 (1 MUL + 2 FMA), the kernel value and
     one FMA per right-hand side.  Matern-3/2: sqrt (MUFU), (1 + u ln2) (FMA), 2^-u (MUFU ex2),
-    product (MUL).  Cauchy: 1 + q (ADD), reciprocal (MUFU)."""
+    product (MUL).  Cauchy: 1 + q (ADD), reciprocal (MUFU).  With the contraction on the tensor
+    cores (tensor=True) the per-right-hand-side FMAs leave the FP32 pipe."""
+    fma = 0 if tensor else nw
     if kernel == "matern32":
-        return 3 + 3 + 2 + nw, 2
-    return 3 + 3 + 1 + nw, 1
+        return 3 + 3 + 2 + fma, 2
+    return 3 + 3 + 1 + fma, 1
 
 
 def nterms(d: int, p: int) -> int:
@@ -228,6 +236,7 @@ def run_ours(a):
     plan.set_option("timing", "1")
     plan.set_option("near_targets_per_thread", str(a.near_tpt))
     plan.set_option("far_precision", a.far_precision)
+    plan.set_option("near_precision", a.near_precision)
     stats = plan.stats()
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     stream = torch.cuda.current_stream()
@@ -259,12 +268,14 @@ def run_ours(a):
 
     # the plain float32 form on the same plan
     comp = None
-    if a.compare != "none" and a.far_precision != a.compare:
-        plan.set_option("far_precision", a.compare)
+    if a.compare != "none" and (a.far_precision, a.near_precision) != ("fp32", "fp32"):
+        plan.set_option("far_precision", "fp32")
+        plan.set_option("near_precision", "fp32")
         comp = time_form(plan, Wd, Yd, max(3, a.steps // 2), 3, flush, stream)
         plan.check()
         y_comp = Yd.cpu().numpy().astype(np.float64)
         plan.set_option("far_precision", a.far_precision)
+        plan.set_option("near_precision", a.near_precision)
 
     # end to end through the host-buffer entry point (copies inside the timed region)
     Wh = torch.from_numpy(W).pin_memory()
@@ -293,8 +304,13 @@ def run_ours(a):
         p2.set_option("near_targets_per_thread", str(a.near_tpt))
         second = {"kernel": f"{k2} l={ell2}"}
         ys = {}
-        for form in [a.far_precision] + ([a.compare] if comp is not None else []):
-            p2.set_option("far_precision", form)
+        head_form = f"near {a.near_precision}, far {a.far_precision}"
+        forms = {head_form: (a.near_precision, a.far_precision)}
+        if comp is not None:
+            forms["near fp32, far fp32"] = ("fp32", "fp32")
+        for form, (npr, fpr) in forms.items():
+            p2.set_option("near_precision", npr)
+            p2.set_option("far_precision", fpr)
             r = time_form(p2, Wd, Yd, max(3, a.steps // 4), 3, flush, stream)
             p2.check()
             second[form] = {"value": a.nrhs / (np.mean(r["step_ms"]) / 1e3), "ms_per_step": float(np.mean(r["step_ms"]))}
@@ -327,12 +343,13 @@ def run_ours(a):
     nsm = torch.cuda.get_device_properties(local).multi_processor_count
     nw = 1 if (a.nrhs == 1 and a.far_precision == "fp32") else (8 if a.nrhs <= 8 else 16 if a.nrhs <= 16 else 32)
     passes = (a.nrhs + PASS - 1) // PASS
-    fp32_ops, mufu_ops = near_pair_cost(kname, nw)
+    near_tc = nw == 32 and a.near_precision == "tf32x3"
+    fp32_ops, mufu_ops = near_pair_cost(kname, nw, near_tc)
     slots_per_pair = max(fp32_ops / 128.0, mufu_ops / 16.0)  # SM clocks per pair (128 FP32, 16 MUFU lanes/SM)
     peak_pairs = nsm * sm_max * 1e6 / slots_per_pair
     near_pairs = stats["near_pairs"] * passes  # one launch per pass; its kernel value serves the pass
     near_ach = near_pairs / (head["near_ms"] / 1e3)
-    near_name = near_kernel_name(kname, nw)
+    near_name = near_kernel_name(kname, nw, a.near_precision)
     traffic = PROFILED_TRAFFIC.get((near_name, kname, a.p, a.theta, a.leaf, a.nrhs, a.n))
     near_roof = {"kernel": near_name, "bound": "alu", "achieved": near_ach / 1e9,
                  "peak": peak_pairs / 1e9, "unit": "Gpair/s", "frac": near_ach / peak_pairs, "traffic": traffic,
@@ -356,7 +373,7 @@ def run_ours(a):
                                      f" far stage time (far_tc launch + wait for pack)"})
     roofs.sort(key=lambda r: -r["ms_per_step"])
     out = {
-        "metric": f"FKT MVMs/s at N=1M, d=3 ({kname}, {a.far_precision} far field, "
+        "metric": f"FKT MVMs/s at N=1M, d=3 ({kname}, near {a.near_precision}, far {a.far_precision}, "
                   f"rel.err vs FP64 dense {max(err_head):.1e})",
         "value": value,
         "unit": "MVM/s",
@@ -367,7 +384,8 @@ def run_ours(a):
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
-        "dtype": "f32" if a.far_precision == "fp32" else f"f32 near + {a.far_precision} far (f32 accumulate)",
+        "dtype": (f"f32 kernel values, {'tf32x3 tensor-core' if near_tc else 'f32'} near contraction, "
+                  f"{a.far_precision} far contraction, f32 accumulate"),
         "data": "synthetic",
         "config": {"workload": workload_name(a), "l2": "flushed between steps (256 MiB write)",
                    "rel_err_max": max(err_head), "rel_err_median": float(np.median(err_head)),
@@ -385,7 +403,7 @@ def run_ours(a):
     }
     if comp is not None:
         cv = a.nrhs * len(comp["step_ms"]) / (sum(comp["step_ms"]) / 1e3)
-        out["compare_form"] = {"far_precision": a.compare, "value": cv, "unit": "MVM/s",
+        out["compare_form"] = {"form": "plain float32 (near and far on the CUDA cores)", "value": cv, "unit": "MVM/s",
                                "ms_per_step": float(np.mean(comp["step_ms"])), "rel_err_max": max(err_comp),
                                "rel_err_median": float(np.median(err_comp)),
                                "stage_ms": {"near": comp["near_ms"], "far+wait": comp["far_ms"], "s2m": comp["s2m_ms"]},

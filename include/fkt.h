@@ -265,7 +265,13 @@ int fkt_autotune_leaf(const float* points, int64_t N, int d, fkt_kernel kernel, 
  *               contraction: fp32 on CUDA cores; otherwise on the tensor cores (tcgen05.mma,
  *               float32 accumulation in tensor memory) with operands in TF32, BF16, or BF16
  *               split into hi + lo parts (three products, about 16 significant bits); the
- *               near field always stays float32.  Right-hand sides go 32 per pass.
+ *               near field's kernel values stay float32.  Right-hand sides go 32 per pass.
+ *   "near_precision"  "fp32" (default) | "tf32x3"  arithmetic of the near-field contraction of
+ *               passes of 17-32 right-hand sides: fp32 on CUDA cores, or on the tensor cores
+ *               (tcgen05.mma kind::tf32, A = float32 kernel values in tensor memory) with each
+ *               factor split into TF32 hi + lo parts (three products, about 20 significant bits
+ *               per product) and the accumulator added into float32 registers every 128 sources;
+ *               kernel values are float32 either way.  fkt_dense_mvm always uses fp32.
  *   "preconditioner" "block_jacobi" (default) | "learned" | "none"   preconditioner of fkt_solve;
  *               "learned" needs fkt_precond_learn first and falls back to block_jacobi when
  *               CG with the correction does not converge (fkt_solve_info.used_fallback)

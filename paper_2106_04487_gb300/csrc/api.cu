@@ -212,6 +212,12 @@ int fkt_set_option(fkt_plan_t plan, const char* key, const char* value) {
         else return FKT_ERR_INVALID_ARG;
         return FKT_OK;
     }
+    if (!strcmp(key, "near_precision")) {
+        if (!strcmp(value, "fp32")) plan->near_precision = fkt::NEAR_FP32;
+        else if (!strcmp(value, "tf32x3")) plan->near_precision = fkt::NEAR_TF32X3;
+        else return FKT_ERR_INVALID_ARG;
+        return FKT_OK;
+    }
     if (!strcmp(key, "far_precision")) {
         if (!strcmp(value, "fp32")) plan->far_precision = fkt::FAR_FP32;
         else if (!strcmp(value, "tf32")) plan->far_precision = fkt::FAR_TF32;

@@ -44,6 +44,7 @@ struct KernelParams {
 };
 
 enum FarPrecision { FAR_FP32 = 0, FAR_TF32 = 1, FAR_BF16 = 2, FAR_BF16X3 = 3 };
+enum NearPrecision { NEAR_FP32 = 0, NEAR_TF32X3 = 1 };
 
 }  // namespace fkt
 
@@ -59,6 +60,7 @@ struct fkt_plan_s {
     bool timing = false;
     int far_precision = fkt::FAR_FP32;
     int near_tpt = 2;              // near-field targets per thread (2 or 4)
+    int near_precision = fkt::NEAR_FP32;  // near-field contraction of 32-wide passes
     // bounding cube
     double lo[4] = {0, 0, 0, 0};
     double L = 1.0;
@@ -181,7 +183,7 @@ int ensure_rhs_capacity(fkt_plan_s* P, int nrhs);
 int create_far_stream(cudaStream_t* s);
 
 // stage launch helpers shared with batch.cu
-void launch_near_stage(fkt_plan_s* P, MvmArgs& a, int nrb, int tpt, cudaStream_t st);
+void launch_near_stage(fkt_plan_s* P, MvmArgs& a, int nrb, int tpt, cudaStream_t st, bool exact = false);
 int free_batch_arrays(fkt_plan_s* P);
 
 // solve.cu

@@ -27,6 +27,8 @@ FKT_DECL_RANGE(4, 7, 8)
 
 void launch_near_d3(int nw, int tpt, int kind, unsigned grid, cudaStream_t st, const MvmArgs& a, const KernelParams& kp);
 void launch_near_d4(int nw, int tpt, int kind, unsigned grid, cudaStream_t st, const MvmArgs& a, const KernelParams& kp);
+void launch_near_tc_d3(int kind, unsigned grid, cudaStream_t st, const MvmArgs& a, const KernelParams& kp);
+void launch_near_tc_d4(int kind, unsigned grid, cudaStream_t st, const MvmArgs& a, const KernelParams& kp);
 
 int launch_tc_d3_p0_6(int p, int prec, bool far, const TcLaunch& L);
 int launch_tc_d3_p7_10(int p, int prec, bool far, const TcLaunch& L);
@@ -69,9 +71,14 @@ static int launch_far_any(int d, int p, int nrb, const FarLaunch& L) {
 namespace {
 
 // Near field launch: nw right-hand sides per pass (1, 8, 16, 32); targets per thread tpt = 2 or 4
-// (4 only for one right-hand side).
-void launch_near(int d, int nw, int tpt, int kind, unsigned grid, cudaStream_t st, const MvmArgs& a,
+// (4 only for one right-hand side); tc: the 32-wide pass on the tensor cores (TF32 hi/lo split).
+void launch_near(int d, int nw, int tpt, bool tc, int kind, unsigned grid, cudaStream_t st, const MvmArgs& a,
                  const KernelParams& kp) {
+    if (tc && nw == 32) {
+        if (d == 3) launch_near_tc_d3(kind, grid, st, a, kp);
+        else launch_near_tc_d4(kind, grid, st, a, kp);
+        return;
+    }
     if (d == 3) launch_near_d3(nw, tpt, kind, grid, st, a, kp);
     else launch_near_d4(nw, tpt, kind, grid, st, a, kp);
 }
@@ -130,17 +137,19 @@ __global__ void dense_lists_kernel(int64_t nblocks, int64_t* off, int2* ent) {
 }  // namespace
 
 // Near field of every target block: one launch, or for a batch one launch per kernel kind over
-// that kind's blocks (largest first, so uneven problems balance across the SMs).
-void launch_near_stage(fkt_plan_s* P, MvmArgs& a, int nrb, int tpt, cudaStream_t st) {
+// that kind's blocks (largest first, so uneven problems balance across the SMs).  exact: keep
+// the float32 CUDA-core kernels whatever near_precision says (the exact dense product).
+void launch_near_stage(fkt_plan_s* P, MvmArgs& a, int nrb, int tpt, cudaStream_t st, bool exact) {
+    const bool tc = !exact && P->near_precision == NEAR_TF32X3;
     if (P->nprob == 0) {
         a.blk_list = nullptr;
-        launch_near(P->d, nrb, tpt, P->kernel.kind, (unsigned)P->nblocks, st, a, P->kp);
+        launch_near(P->d, nrb, tpt, tc, P->kernel.kind, (unsigned)P->nblocks, st, a, P->kp);
         return;
     }
     for (size_t i = 0; i < P->kind_list.size(); ++i) {
         if (P->kind_list_n[i] == 0) continue;
         a.blk_list = P->kind_list[i];
-        launch_near(P->d, nrb, tpt, P->kind_of_list[i], (unsigned)P->kind_list_n[i], st, a, P->kp);
+        launch_near(P->d, nrb, tpt, tc, P->kind_of_list[i], (unsigned)P->kind_list_n[i], st, a, P->kp);
     }
     a.blk_list = P->far_list;  // the far stage that follows walks all blocks, most work first
 }
@@ -342,7 +351,7 @@ int launch_dense(fkt_plan_s* P, const float* w, float* y, int nrhs) {
         a.ynear = P->ynear + (size_t)r0 * N;
         a.nr = npass;
         launch_permute(P->d, nw, pg, st, N, P->perm, P->xs, w + (size_t)r0 * N, npass, P->kp.sig, P->pt_sig, P->rec);
-        launch_near_stage(P, a, nw, P->near_tpt, st);
+        launch_near_stage(P, a, nw, P->near_tpt, st, true);
         unpermute_kernel<><<<pg, 256, 0, st>>>(N, npass, P->perm, a.ynear, nullptr, y + (size_t)r0 * N);
         FKT_CUDA_TRY(cudaGetLastError());
     }

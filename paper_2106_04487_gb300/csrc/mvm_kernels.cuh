@@ -596,7 +596,7 @@ __global__ void __launch_bounds__(32, 20) near_wide_kernel(MvmArgs a, KernelPara
         if (valid[j])
 #pragma unroll
             for (int r = 0; r < NR; ++r)
-                a.ynear[(int64_t)r * a.N + t] = ((r & 1) ? acc[j][r / 2].y : acc[j][r / 2].x) * kp.scale;
+                if (r < a.nr) a.ynear[(int64_t)r * a.N + t] = ((r & 1) ? acc[j][r / 2].y : acc[j][r / 2].x) * kp.scale;
     }
 }
 
@@ -756,7 +756,7 @@ __global__ void __launch_bounds__(32) near_tile_kernel(MvmArgs a, KernelParams k
 #pragma unroll
             for (int r = 0; r < RL; ++r) {
                 const float v = (r & 1) ? acc[q][r / 2].y : acc[q][r / 2].x;
-                a.ynear[(int64_t)(rj * RL + r) * a.N + t] = v * kp.scale;
+                if (rj * RL + r < a.nr) a.ynear[(int64_t)(rj * RL + r) * a.N + t] = v * kp.scale;
             }
     }
 }

@@ -1,0 +1,420 @@
+// Near field of 32-wide passes on the 5th-generation tensor cores.
+//
+// For one block of 128 targets and one chunk of up to 32 sources of a near leaf the near field is
+// the dense product (Algorithm 1, the near-field sum of eq. nbody over the leaf)
+//     z[t][r] += sum_s K(|x_t - x_s|) w[s][r]        (128 x 32) += (128 x 32) (32 x 32).
+// The CUDA cores evaluate the kernel values in float32, one target row per thread, and write the
+// row straight into tensor memory as the A operand (tcgen05.st); the chunk's weights, bulk-copied
+// as source records, are rearranged in shared memory into the B operand; one thread issues
+// tcgen05.mma (kind::tf32, A from tensor memory, M = 128 targets, N = 32 right-hand sides, K = 8
+// sources per instruction) into a float32 accumulator in tensor memory.
+//
+// float32 accuracy from TF32 operands: every factor v is split into hi = v rounded to TF32 (10
+// mantissa bits) and lo = v - hi (exact in float32, |lo| <= 2^-11 |v|); the tensor core adds
+// hi*hi + hi*lo + lo*hi.  The dropped lo*lo and the truncation of lo to TF32 leave at most about
+// 2^-20 of each product, with random sign.  The tensor core's own float32 accumulation is not
+// round-to-nearest: summed over the thousands of MMAs of a target block it drifts by about 2^-24
+// per MMA in one direction (measured: 2e-5 relative after ~600 MMAs).  So each chunk's MMAs start
+// a fresh accumulator, and each thread adds the chunk's partial row into float32 registers
+// (round-to-nearest) once the chunk's MMAs are done.
+#pragma once
+
+#include "mvm_kernels.cuh"
+
+namespace fkt {
+
+struct NearTcShape {
+    static constexpr int NR = 32;                     // right-hand sides (the MMA's N)
+    static constexpr int CH = 32;                     // sources per chunk (4 MMA K-steps)
+    static constexpr int ST = 4;                      // record stages in flight
+    static constexpr int F4 = (4 + NR + 3) / 4;       // float4s per source record (point + weights)
+    static constexpr int TMEM_COLS = 128;             // accumulator 32 + A hi 32 + A lo 32 columns
+    static constexpr int COL_AHI = 32, COL_ALO = 64;
+};
+
+namespace tc {
+
+// D[tmem] (+)= A[tmem] * B[smem]^T (TF32 operands), issued by one thread.
+__device__ __forceinline__ void mma_tf32_ts(uint32_t d_tmem, uint32_t a_tmem, uint64_t b, uint32_t idesc,
+                                            bool accumulate) {
+    asm volatile(
+        "{\n"
+        ".reg .pred p;\n"
+        "setp.ne.b32 p, %4, 0;\n"
+        "tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, p;\n"
+        "}\n" ::"r"(d_tmem),
+        "r"(a_tmem), "l"(b), "r"(idesc), "r"((uint32_t)accumulate)
+        : "memory");
+}
+
+// 32 consecutive 32-bit columns of this thread's TMEM lane (warp w owns lanes 32(w%4)..+31).
+__device__ __forceinline__ void st32(uint32_t taddr, const uint32_t v[32]) {
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31, %32};" ::"r"(taddr),
+        "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7]), "r"(v[8]), "r"(v[9]),
+        "r"(v[10]), "r"(v[11]), "r"(v[12]), "r"(v[13]), "r"(v[14]), "r"(v[15]), "r"(v[16]), "r"(v[17]), "r"(v[18]),
+        "r"(v[19]), "r"(v[20]), "r"(v[21]), "r"(v[22]), "r"(v[23]), "r"(v[24]), "r"(v[25]), "r"(v[26]), "r"(v[27]),
+        "r"(v[28]), "r"(v[29]), "r"(v[30]), "r"(v[31])
+        : "memory");
+}
+// 16 consecutive 32-bit columns of this thread's TMEM lane.
+__device__ __forceinline__ void st16(uint32_t taddr, const uint32_t v[16]) {
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15, %16};" ::"r"(taddr),
+        "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7]), "r"(v[8]), "r"(v[9]),
+        "r"(v[10]), "r"(v[11]), "r"(v[12]), "r"(v[13]), "r"(v[14]), "r"(v[15])
+        : "memory");
+}
+
+// Zero 32 consecutive 32-bit columns of this thread's TMEM lane.
+__device__ __forceinline__ void st32_zero(uint32_t taddr) {
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, "
+        "%1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1};" ::"r"(taddr),
+        "r"(0u)
+        : "memory");
+}
+__device__ __forceinline__ void wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
+
+// D[tmem] += A[tmem] * B[smem]^T (TF32 operands) leaving the accumulator rows (TMEM lanes) whose
+// bit is set in off[0..3] (lane i: bit i % 32 of off[i / 32]) untouched.
+__device__ __forceinline__ void mma_tf32_ts_masked(uint32_t d_tmem, uint32_t a_tmem, uint64_t b, uint32_t idesc,
+                                                   const uint32_t off[4]) {
+    asm volatile(
+        "{\n"
+        ".reg .pred p;\n"
+        "setp.ne.b32 p, 1, 0;\n"
+        "tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, {%4, %5, %6, %7}, p;\n"
+        "}\n" ::"r"(d_tmem),
+        "r"(a_tmem), "l"(b), "r"(idesc), "r"(off[0]), "r"(off[1]), "r"(off[2]), "r"(off[3])
+        : "memory");
+}
+
+}  // namespace tc
+
+// v = hi + lo with hi representable in TF32 (round half away from zero on the 13 dropped bits).
+__device__ __forceinline__ void split_tf32(float v, uint32_t& hi, uint32_t& lo) {
+    const uint32_t h = (__float_as_uint(v) + 0x1000u) & 0xFFFFE000u;
+    hi = h;
+    lo = __float_as_uint(v - __uint_as_float(h));
+}
+
+// Kernel values of two pairs at once (the same formulas as kval, with the non-MUFU arithmetic on
+// packed float32 pairs); q = squared distances in the kernel's own units.
+template <int KIND>
+__device__ __forceinline__ float2 kval2(float2 q, const KernelParams& kp) {
+    constexpr float kLn2 = 0.69314718055994531f;
+    if (KIND == FKT_GAUSSIAN) {
+        return make_float2(ptx::ex2(-q.x), ptx::ex2(-q.y));
+    } else if (KIND == FKT_EXPONENTIAL) {
+        return make_float2(ptx::ex2(-ptx::sqrt_approx(q.x)), ptx::ex2(-ptx::sqrt_approx(q.y)));
+    } else if (KIND == FKT_MATERN32) {
+        const float2 u = make_float2(ptx::sqrt_approx(q.x), ptx::sqrt_approx(q.y));
+        const float2 e = make_float2(ptx::ex2(-u.x), ptx::ex2(-u.y));
+        return __fmul2_rn(__ffma2_rn(u, make_float2(kLn2, kLn2), make_float2(1.f, 1.f)), e);
+    } else if (KIND == FKT_MATERN52) {
+        const float2 u = make_float2(ptx::sqrt_approx(q.x), ptx::sqrt_approx(q.y));
+        const float2 e = make_float2(ptx::ex2(-u.x), ptx::ex2(-u.y));
+        const float2 t = __fmul2_rn(u, make_float2(kLn2, kLn2));
+        const float2 poly = __ffma2_rn(t, __ffma2_rn(t, make_float2(1.f / 3.f, 1.f / 3.f), make_float2(1.f, 1.f)),
+                                       make_float2(1.f, 1.f));
+        return __fmul2_rn(poly, e);
+    } else if (KIND == FKT_CAUCHY) {
+        const float2 b = __fadd2_rn(q, make_float2(1.f, 1.f));
+        return make_float2(ptx::rcp_approx(b.x), ptx::rcp_approx(b.y));
+    } else if (KIND == FKT_RATQUAD) {
+        const float2 b = __fadd2_rn(q, make_float2(1.f, 1.f));
+        if (kp.alpha == 1.0f) return make_float2(ptx::rcp_approx(b.x), ptx::rcp_approx(b.y));
+        return make_float2(ptx::ex2(-kp.alpha * ptx::lg2(b.x)), ptx::ex2(-kp.alpha * ptx::lg2(b.y)));
+    } else {
+        return make_float2(q.x > 0.0f ? ptx::rsqrt_approx(q.x) : 0.0f, q.y > 0.0f ? ptx::rsqrt_approx(q.y) : 0.0f);
+    }
+}
+
+// Two kernel values -> their TF32 hi parts (bits) and float32 lo = v - hi.
+__device__ __forceinline__ void split2(float2 v, uint32_t& h0, uint32_t& h1, uint32_t& l0, uint32_t& l1) {
+    h0 = (__float_as_uint(v.x) + 0x1000u) & 0xFFFFE000u;
+    h1 = (__float_as_uint(v.y) + 0x1000u) & 0xFFFFE000u;
+    const float2 lo = __ffma2_rn(make_float2(__uint_as_float(h0), __uint_as_float(h1)), make_float2(-1.f, -1.f), v);
+    l0 = __float_as_uint(lo.x);
+    l1 = __float_as_uint(lo.y);
+}
+
+// acc[r] += this thread's accumulator row (32 columns at taddr).
+__device__ __forceinline__ void add_partial(uint32_t taddr, float acc[32]) {
+    float d[32];
+    tc::ld16(taddr, d);
+    tc::ld16(taddr + 16, d + 16);
+#pragma unroll
+    for (int r = 0; r < 32; ++r) acc[r] += d[r];
+}
+
+// Walks the (near leaf, chunk of <= CH sources) sequence of one target block.
+struct NearChunks {
+    int64_t e, e1;
+    int cb, s1;
+    __device__ __forceinline__ void settle(const MvmArgs& a) {
+        while (e < e1 && cb >= s1) {
+            if (++e < e1) {
+                const int leaf = a.near_ent[e].x;
+                cb = a.nd_begin[leaf];
+                s1 = a.nd_end[leaf];
+            }
+        }
+    }
+    __device__ __forceinline__ void start(const MvmArgs& a, int64_t e0, int64_t e_end) {
+        e = e0;
+        e1 = e_end;
+        cb = s1 = 0;
+        if (e < e1) {
+            const int leaf = a.near_ent[e].x;
+            cb = a.nd_begin[leaf];
+            s1 = a.nd_end[leaf];
+        }
+        settle(a);
+    }
+    __device__ __forceinline__ bool done() const { return e >= e1; }
+    __device__ __forceinline__ int count() const { return min(NearTcShape::CH, s1 - cb); }
+    __device__ __forceinline__ void next(const MvmArgs& a) {
+        cb += NearTcShape::CH;
+        settle(a);
+    }
+};
+
+// One CTA per 128-target block (thread = target = TMEM lane).  Per chunk c:
+//   wait for its records and for the MMAs of chunk c-1 (the A columns and the B planes are
+//   free); every kFlush chunks add the accumulator rows into float32 registers and zero them
+//   -> B planes of chunk c from the staged weights -> kernel values of this row (float32,
+//      split hi/lo) into tensor memory as the A rows
+//   -> barrier -> thread 0 issues 3 MMAs per 8 sources with the rows of targets outside the
+//      entry's mask disabled, commits them to an mbarrier and refills the record stage of
+//      chunk c with chunk c+ST.
+// A warp none of whose targets uses the entry neither evaluates the kernel nor writes its A
+// rows (the MMA leaves its accumulator rows alone).  Every wait is bounded; a wait that runs
+// out sets the error word and the CTA drains what it issued before leaving.
+template <int D, int KIND>
+__global__ void __launch_bounds__(kTB, 4) near_tc_kernel(MvmArgs a, KernelParams kp_all) {
+    using S = NearTcShape;
+    constexpr int CH = S::CH, ST = S::ST, F4 = S::F4, NR = S::NR;
+    constexpr int kFlush = 4;  // chunks (12 MMAs each) per float32 flush of the accumulator
+    constexpr uint32_t IDESC = tc::instr_desc(2u, 128u, (uint32_t)NR);
+    __shared__ __align__(128) float4 stage[ST][CH * F4];
+    __shared__ __align__(128) float bpl[2][CH * NR];  // B operand hi / lo: K-major core matrices
+    __shared__ __align__(8) uint64_t full[ST];
+    __shared__ __align__(8) uint64_t bar_mma;
+    __shared__ uint32_t tmem_base;
+    __shared__ uint32_t s_valid[kMaskWords];
+    __shared__ __align__(16) float s_src[kMaskWords][4][CH];  // per warp: -x, -y, -z, -u of the chunk (SoA)
+    const int tl = threadIdx.x, warp = tl >> 5, lane = tl & 31;
+    const int64_t blk = cta_block(a);
+    const KernelParams kp = block_params(a, blk, kp_all);
+    const int2 rg = a.blk[blk];
+    const int t = rg.x + tl;
+    const bool valid = t < rg.y;
+    const uint32_t vword = __ballot_sync(0xffffffffu, valid);
+    float2 tx2[4];  // this target (scaled by sigma), duplicated for the packed pair arithmetic
+    {
+        const float4 x = valid ? a.xs[t] : make_float4(0.f, 0.f, 0.f, 0.f);
+        tx2[0] = make_float2(x.x * kp.sig, x.x * kp.sig);
+        tx2[1] = make_float2(x.y * kp.sig, x.y * kp.sig);
+        tx2[2] = make_float2(x.z * kp.sig, x.z * kp.sig);
+        tx2[3] = make_float2(x.w * kp.sig, x.w * kp.sig);
+    }
+    const int64_t e0 = a.near_off[blk], e1 = a.near_off[blk + 1];
+    if (tl == 0) {
+#pragma unroll
+        for (int s = 0; s < ST; ++s) ptx::mbar_init(&full[s], 1);
+        ptx::mbar_init(&bar_mma, 1);
+        ptx::fence_mbar_init();
+    }
+    if (lane == 0) s_valid[warp] = vword;
+    if (warp == 0) {
+        tc::alloc(&tmem_base, S::TMEM_COLS);
+        tc::relinquish();
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tmem = tmem_base;
+    const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
+    tc::st32_zero(tmem + lane_base);  // accumulator rows start at zero; every MMA accumulates
+    tc::wait_st();
+
+    // producer state (thread 0): chunks issued so far
+    NearChunks pit;
+    int issued = 0;
+    auto issue = [&]() {
+        if (pit.done()) return;
+        const int n = pit.count();
+        const int slot = issued % ST;
+        const uint32_t bytes = (uint32_t)n * F4 * 16u;
+        ptx::mbar_arrive_expect_tx(&full[slot], bytes);
+        ptx::bulk_g2s(&stage[slot][0], a.rec + (int64_t)pit.cb * F4, bytes, &full[slot]);
+        ++issued;
+        pit.next(a);
+    };
+    NearChunks it;
+    it.start(a, e0, e1);
+    if (tl == 0) {
+        pit = it;
+        for (int s = 0; s < ST; ++s) issue();
+    }
+    float acc[NR];
+#pragma unroll
+    for (int r = 0; r < NR; ++r) acc[r] = 0.f;
+    bool ok = true;
+    bool dirty = false;  // this warp's accumulator rows hold products not yet added to acc
+    int c = 0;
+    int waited = 0;      // thread 0: chunks whose records it has seen land
+    for (; !it.done(); it.next(a), ++c) {
+        const int slot = c % ST;
+        const int n = it.count();
+        const int mask = a.near_ent[it.e].y;
+        const uint32_t mword = (mask < 0 ? 0xFFFFFFFFu : __ldg(&a.masks[(int64_t)mask * kMaskWords + warp])) & vword;
+        // 1. records of chunk c
+        ok = ok && ptx::mbar_wait_bounded(&full[slot], (uint32_t)((c / ST) & 1), kWaitCycles);
+        if (tl == 0 && ok) waited = c + 1;
+        // 2. the MMAs of chunk c - 1 are done: the A columns and the B planes are free
+        bool stored = false;
+        if (c > 0) {
+            ok = ok && ptx::mbar_wait_bounded(&bar_mma, (uint32_t)((c - 1) & 1), kWaitCycles);
+            tc::fence_after_sync();
+            // 3. every kFlush chunks: accumulator rows -> float32 registers, then zero them
+            if (c % kFlush == 0 && dirty && __all_sync(0xffffffffu, ok)) {
+                add_partial(tmem + lane_base, acc);
+                tc::st32_zero(tmem + lane_base);
+                dirty = false;
+                stored = true;
+            }
+        }
+        const float4* sb = &stage[slot][0];
+        // 4. B operand of chunk c: warp w rearranges source groups w and w + 4 (4 sources each);
+        //    lane = right-hand side.  Element (n, k) sits at float (k/4)*128 + n*4 + k%4.
+#pragma unroll
+        for (int kg = warp; kg < CH / 4; kg += 4) {
+            uint32_t h[4], l[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const int k = 4 * kg + i;
+                const float v = k < n ? reinterpret_cast<const float*>(sb + k * F4)[4 + lane] : 0.f;
+                split_tf32(v, h[i], l[i]);
+            }
+            *reinterpret_cast<uint4*>(&bpl[0][kg * 128 + lane * 4]) = make_uint4(h[0], h[1], h[2], h[3]);
+            *reinterpret_cast<uint4*>(&bpl[1][kg * 128 + lane * 4]) = make_uint4(l[0], l[1], l[2], l[3]);
+        }
+        // 5. A operand: this row's kernel values against the chunk, 16 sources at a time, into
+        //    tensor memory (rows of targets outside the mask are computed anyway when their warp
+        //    is busy, and left out by the MMA)
+        if (mword != 0u) {
+            {   // this warp's SoA copy of the chunk's negated coordinates (zeros past the chunk's
+                // end: those columns meet zero weights in B)
+                const float4 r = lane < n ? sb[lane * F4] : make_float4(0.f, 0.f, 0.f, 0.f);
+                s_src[warp][0][lane] = -r.x;
+                s_src[warp][1][lane] = -r.y;
+                s_src[warp][2][lane] = -r.z;
+                if (D == 4) s_src[warp][3][lane] = -r.w;
+            }
+            __syncwarp();
+#pragma unroll
+            for (int h0 = 0; h0 < CH; h0 += 16) {
+                uint32_t khi[16], klo[16];
+#pragma unroll
+                for (int j4 = 0; j4 < 16; j4 += 4) {
+                    const int j = h0 + j4;
+                    const float4 X = *reinterpret_cast<const float4*>(&s_src[warp][0][j]);
+                    const float4 Y = *reinterpret_cast<const float4*>(&s_src[warp][1][j]);
+                    const float4 Z = *reinterpret_cast<const float4*>(&s_src[warp][2][j]);
+                    float2 q[2];
+#pragma unroll
+                    for (int hh = 0; hh < 2; ++hh) {
+                        const float2 dx = __fadd2_rn(tx2[0], hh ? make_float2(X.z, X.w) : make_float2(X.x, X.y));
+                        const float2 dy = __fadd2_rn(tx2[1], hh ? make_float2(Y.z, Y.w) : make_float2(Y.x, Y.y));
+                        const float2 dz = __fadd2_rn(tx2[2], hh ? make_float2(Z.z, Z.w) : make_float2(Z.x, Z.y));
+                        q[hh] = __ffma2_rn(dx, dx, __ffma2_rn(dy, dy, __fmul2_rn(dz, dz)));
+                    }
+                    if (D == 4) {
+                        const float4 W = *reinterpret_cast<const float4*>(&s_src[warp][3][j]);
+                        const float2 dw0 = __fadd2_rn(tx2[3], make_float2(W.x, W.y));
+                        const float2 dw1 = __fadd2_rn(tx2[3], make_float2(W.z, W.w));
+                        q[0] = __ffma2_rn(dw0, dw0, q[0]);
+                        q[1] = __ffma2_rn(dw1, dw1, q[1]);
+                    }
+#pragma unroll
+                    for (int hh = 0; hh < 2; ++hh) {
+                        const float2 kv = kval2<KIND>(q[hh], kp);
+                        split2(kv, khi[j4 + 2 * hh], khi[j4 + 2 * hh + 1], klo[j4 + 2 * hh], klo[j4 + 2 * hh + 1]);
+                    }
+                }
+                tc::st16(tmem + lane_base + S::COL_AHI + h0, khi);
+                tc::st16(tmem + lane_base + S::COL_ALO + h0, klo);
+            }
+            dirty = true;
+            stored = true;
+        }
+        if (stored) tc::wait_st();
+        // 6. publish (shared-memory B to the async proxy, tensor-memory A to the MMA issuer)
+        ptx::fence_proxy_async_smem();
+        tc::fence_before_sync();
+        if (!__syncthreads_and(ok)) {
+            ok = false;
+            break;
+        }
+        // 7. issue, then refill the stage of chunk c (every thread has read it) with chunk c + ST
+        if (tl == 0) {
+            tc::fence_after_sync();
+            uint32_t off[kMaskWords];  // disable-output-lane: 1 = leave the row alone
+#pragma unroll
+            for (int w = 0; w < kMaskWords; ++w)
+                off[w] = ~((mask < 0 ? 0xFFFFFFFFu : __ldg(&a.masks[(int64_t)mask * kMaskWords + w])) & s_valid[w]);
+            const int nks = (n + 7) / 8;
+#pragma unroll 1
+            for (int ks = 0; ks < nks; ++ks) {
+                const uint64_t bh = tc::smem_desc(&bpl[0][ks * 256], 512, 128);
+                const uint64_t bl = tc::smem_desc(&bpl[1][ks * 256], 512, 128);
+                const uint32_t ahi = tmem + S::COL_AHI + ks * 8, alo = tmem + S::COL_ALO + ks * 8;
+                tc::mma_tf32_ts_masked(tmem, ahi, bh, IDESC, off);
+                tc::mma_tf32_ts_masked(tmem, ahi, bl, IDESC, off);
+                tc::mma_tf32_ts_masked(tmem, alo, bh, IDESC, off);
+            }
+            tc::commit(&bar_mma);
+            ptx::fence_proxy_async_smem();
+            issue();
+        }
+    }
+    // c chunks were committed; wait for the last, then add what the accumulator rows still hold
+    if (ok && c > 0) ok = ptx::mbar_wait_bounded(&bar_mma, (uint32_t)((c - 1) & 1), kWaitCycles);
+    const bool all_ok = __syncthreads_and(ok) != 0;
+    tc::fence_after_sync();
+    if (dirty && all_ok) add_partial(tmem + lane_base, acc);
+    if (!all_ok && tl == 0) {
+        atomicExch(a.err, 1);
+        // let the copies and MMAs still in flight finish before the CTA leaves (bounded)
+        for (int j = waited; j < issued; ++j)
+            ptx::mbar_wait_bounded(&full[j % ST], (uint32_t)((j / ST) & 1), kWaitCycles);
+        if (c > 0) ptx::mbar_wait_bounded(&bar_mma, (uint32_t)((c - 1) & 1), kWaitCycles);
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    if (warp == 0) tc::dealloc(tmem, S::TMEM_COLS);
+    if (valid && all_ok)
+#pragma unroll
+        for (int r = 0; r < NR; ++r)
+            if (r < a.nr) a.ynear[(int64_t)r * a.N + t] = acc[r] * kp.scale;
+}
+
+template <int D>
+void launch_near_tc_dim(int kind, unsigned grid, cudaStream_t st, const MvmArgs& a, const KernelParams& kp) {
+    switch (kind) {
+    case FKT_GAUSSIAN: near_tc_kernel<D, FKT_GAUSSIAN><<<grid, kTB, 0, st>>>(a, kp); break;
+    case FKT_EXPONENTIAL: near_tc_kernel<D, FKT_EXPONENTIAL><<<grid, kTB, 0, st>>>(a, kp); break;
+    case FKT_MATERN32: near_tc_kernel<D, FKT_MATERN32><<<grid, kTB, 0, st>>>(a, kp); break;
+    case FKT_MATERN52: near_tc_kernel<D, FKT_MATERN52><<<grid, kTB, 0, st>>>(a, kp); break;
+    case FKT_CAUCHY: near_tc_kernel<D, FKT_CAUCHY><<<grid, kTB, 0, st>>>(a, kp); break;
+    case FKT_RATQUAD: near_tc_kernel<D, FKT_RATQUAD><<<grid, kTB, 0, st>>>(a, kp); break;
+    default: near_tc_kernel<D, FKT_LAPLACE><<<grid, kTB, 0, st>>>(a, kp); break;
+    }
+}
+
+}  // namespace fkt

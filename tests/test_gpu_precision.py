@@ -1,6 +1,8 @@
 """Precision form: the far-field contraction on the tensor cores (tcgen05.mma, float32
 accumulation in tensor memory) with TF32, BF16 or BF16 hi/lo split operands, near field in
-float32.  Each mode's error against the oracle FKT (float64) is checked against a stated bar."""
+float32 -- on the CUDA cores, or as a TF32 hi/lo split product on the tensor cores (float32
+kernel values, about 20 significant bits per product).  Each mode's error against the oracle
+FKT (float64) is checked against a stated bar."""
 import numpy as np
 import pytest
 
@@ -68,3 +70,71 @@ def test_precision_modes_d4(fkt, orc, prec):
     err = _rel(y, z)
     print(f"d=4 {prec}: rel err vs oracle {err:.3e}")
     assert err < BARS[prec], err
+
+
+# The tensor-core near field (32-wide passes) keeps the float32 bar: the hi/lo split leaves at most
+# about 2^-20 of each product.
+@pytest.mark.parametrize("far", ["fp32", "bf16x3"])
+@pytest.mark.parametrize("nrhs", [20, 32, 40])
+def test_near_tensor_core_d3(fkt, case3, far, nrhs):
+    import torch
+
+    X, W, z = case3
+    plan = fkt.Plan(torch.from_numpy(X).cuda(), "matern32", lengthscale=0.2, p=6, leaf_size=128, theta=0.5)
+    plan.set_option("far_precision", far)
+    plan.set_option("near_precision", "tf32x3")
+    y = plan.mvm(torch.from_numpy(W[:nrhs]).cuda()).cpu().numpy().astype(np.float64)
+    plan.check()
+    err = _rel(y, z[:nrhs])
+    print(f"d=3 near tf32x3, far {far}, nrhs={nrhs}: rel err vs oracle {err:.3e}")
+    assert np.isfinite(y).all()
+    assert err < BARS[far], err
+
+
+@pytest.mark.parametrize("kernel,ell,d,leaf", [("gaussian", 0.1, 3, 256), ("laplace", 1.0, 3, 64),
+                                               ("cauchy", 0.05, 3, 200), ("exponential", 0.3, 3, 96),
+                                               ("ratquad", 0.2, 3, 128), ("matern52", 0.3, 4, 128),
+                                               ("gaussian", 0.2, 4, 77)])
+def test_near_tensor_core_kernels(fkt, orc, kernel, ell, d, leaf):
+    """Every kernel kind, d = 3 and 4, ragged leaves (sizes not multiples of the 8-source MMA
+    step), duplicated points (Laplace skips r = 0 pairs) against the oracle FKT."""
+    import torch
+
+    n = 9000
+    X = inputs.gaussian_mixture(n, d, 10, 0.05, seed=44) if d == 3 else inputs.gaussian_mixture(n, d, 20, 0.05, seed=44)
+    X[:50] = X[50:100]  # exact duplicates
+    W = inputs.normal_weights(n, 32, seed=45)
+    z = orc.FKT(X, orc.kparams(kernel, ell), p=4, leaf_size=leaf, theta=0.5).mvm(W)
+    plan = fkt.Plan(torch.from_numpy(X).cuda(), kernel, lengthscale=ell, p=4, leaf_size=leaf, theta=0.5)
+    plan.set_option("near_precision", "tf32x3")
+    y = plan.mvm(torch.from_numpy(W).cuda()).cpu().numpy().astype(np.float64)
+    plan.check()
+    err = _rel(y, z)
+    print(f"{kernel} d={d} leaf={leaf} near tf32x3: rel err vs oracle {err:.3e}")
+    assert err < BARS["fp32"], err
+
+
+def test_near_tensor_core_all_near_matches_dense(fkt, orc):
+    """One leaf holding every point (leaf_size >= N): the tensor-core near field alone is the
+    dense product; compared with the float64 dense oracle."""
+    import torch
+
+    X = inputs.uniform_cube(3000, 3, seed=46)
+    W = inputs.normal_weights(3000, 32, seed=47)
+    z = orc.dense(X, orc.kparams("matern32", 0.2), W)
+    plan = fkt.Plan(torch.from_numpy(X).cuda(), "matern32", lengthscale=0.2, p=4, leaf_size=4096, theta=0.5)
+    plan.set_option("near_precision", "tf32x3")
+    y = plan.mvm(torch.from_numpy(W).cuda()).cpu().numpy().astype(np.float64)
+    plan.check()
+    err = _rel(y, z)
+    print(f"all-near tf32x3 vs dense float64: {err:.3e}")
+    assert err < 2e-6, err
+
+
+def test_near_precision_option_rejects_unknown(fkt):
+    import torch
+
+    X = inputs.uniform_cube(500, 3, seed=48)
+    plan = fkt.Plan(torch.from_numpy(X).cuda(), "gaussian", lengthscale=0.1, p=2, leaf_size=64, theta=0.5)
+    with pytest.raises(Exception):
+        plan.set_option("near_precision", "bf16")
