@@ -25,11 +25,14 @@ namespace fkt {
 
 struct NearTcShape {
     static constexpr int NR = 32;                     // right-hand sides (the MMA's N)
-    static constexpr int CH = 32;                     // sources per chunk (4 MMA K-steps)
-    static constexpr int ST = 4;                      // record stages in flight
+    static constexpr int CH = 16;                     // sources per chunk (2 MMA K-steps of 8)
+    static constexpr int ST = 6;                      // record stages in flight
     static constexpr int F4 = (4 + NR + 3) / 4;       // float4s per source record (point + weights)
-    static constexpr int TMEM_COLS = 128;             // accumulator 32 + A hi 32 + A lo 32 columns
-    static constexpr int COL_AHI = 32, COL_ALO = 64;
+    static constexpr int CONSUMERS = 4;               // warps that own the 128 TMEM lanes / targets
+    static constexpr int THREADS = 32 * (CONSUMERS + 1);  // + one producer / MMA-issuer warp
+    static constexpr int TMEM_COLS = 128;             // accumulator 32 + 2 slots x (A hi 16 + A lo 16)
+    static constexpr int COL_A = 32, SLOT_COLS = 2 * CH;
+    static constexpr int FLUSH = 8;                   // chunks (6 MMAs each) per float32 flush
 };
 
 namespace tc {
@@ -142,6 +145,8 @@ __device__ __forceinline__ void split2(float2 v, uint32_t& h0, uint32_t& h1, uin
     l1 = __float_as_uint(lo.y);
 }
 
+__device__ __forceinline__ void acc_store(const MvmArgs& a, int r, int t, float v) { a.ynear[(int64_t)r * a.N + t] = v; }
+
 // acc[r] += this thread's accumulator row (32 columns at taddr).
 __device__ __forceinline__ void add_partial(uint32_t taddr, float acc[32]) {
     float d[32];
@@ -183,53 +188,56 @@ struct NearChunks {
     }
 };
 
-// One CTA per 128-target block (thread = target = TMEM lane).  Per chunk c:
-//   wait for its records and for the MMAs of chunk c-1 (the A columns and the B planes are
-//   free); every kFlush chunks add the accumulator rows into float32 registers and zero them
-//   -> B planes of chunk c from the staged weights -> kernel values of this row (float32,
-//      split hi/lo) into tensor memory as the A rows
-//   -> barrier -> thread 0 issues 3 MMAs per 8 sources with the rows of targets outside the
-//      entry's mask disabled, commits them to an mbarrier and refills the record stage of
-//      chunk c with chunk c+ST.
-// A warp none of whose targets uses the entry neither evaluates the kernel nor writes its A
-// rows (the MMA leaves its accumulator rows alone).  Every wait is bounded; a wait that runs
-// out sets the error word and the CTA drains what it issued before leaving.
+// Per record stage: what the producer resolved for the chunk it holds.
+struct NearChunkInfo {
+    int n;                     // sources in the chunk; 0 marks the end of the block's list
+    uint32_t on[kMaskWords];   // targets (TMEM lanes) that use the chunk's leaf
+};
+
+// One CTA per 128-target block, warp-specialised:
+//   warps 0-3 (consumers, thread = target = TMEM lane): per chunk c, wait for its records and
+//     for the MMAs of chunk c-2 (A slot and B planes c%2 are free); every FLUSH chunks add the
+//     accumulator rows into float32 registers and zero them; rearrange their share of the
+//     weights into the B planes; a warp with a target in the chunk's mask evaluates its rows
+//     (float32 kernel values, split hi/lo) into its A slot; then arrive on aready[c%2].
+//   warp 4 lane 0 (producer / MMA issuer): resolves chunk metadata from the lists and
+//     bulk-copies source records ST chunks ahead; per chunk waits aready, issues 3 MMAs per 8
+//     sources (rows outside the mask disabled), commits them to mma_done[c%2], and refills the
+//     chunk's record stage.
+// The consumers touch no global memory in the loop and no CTA-wide barrier runs in it.  Every
+// wait is bounded; a wait that runs out sets s_fail and the error word, every role leaves its
+// loop, and the producer drains what it issued before the CTA frees its tensor memory.
 template <int D, int KIND>
-__global__ void __launch_bounds__(kTB, 4) near_tc_kernel(MvmArgs a, KernelParams kp_all) {
+__global__ void __launch_bounds__(NearTcShape::THREADS, 4) near_tc_kernel(MvmArgs a, KernelParams kp_all) {
     using S = NearTcShape;
-    constexpr int CH = S::CH, ST = S::ST, F4 = S::F4, NR = S::NR;
-    constexpr int kFlush = 4;  // chunks (12 MMAs each) per float32 flush of the accumulator
+    constexpr int CH = S::CH, ST = S::ST, F4 = S::F4, NR = S::NR, NC = S::CONSUMERS;
     constexpr uint32_t IDESC = tc::instr_desc(2u, 128u, (uint32_t)NR);
     __shared__ __align__(128) float4 stage[ST][CH * F4];
-    __shared__ __align__(128) float bpl[2][CH * NR];  // B operand hi / lo: K-major core matrices
-    __shared__ __align__(8) uint64_t full[ST];
-    __shared__ __align__(8) uint64_t bar_mma;
+    __shared__ __align__(128) float bpl[2][2][CH * NR];      // [slot][hi, lo]: K-major core matrices
+    __shared__ __align__(16) float s_src[NC][4][CH];        // per consumer warp: -x, -y, -z, -u (SoA)
+    __shared__ NearChunkInfo info[ST];
+    __shared__ __align__(8) uint64_t full[ST], aready[2], mma_done[2];
     __shared__ uint32_t tmem_base;
     __shared__ uint32_t s_valid[kMaskWords];
-    __shared__ __align__(16) float s_src[kMaskWords][4][CH];  // per warp: -x, -y, -z, -u of the chunk (SoA)
+    __shared__ int s_fail;
     const int tl = threadIdx.x, warp = tl >> 5, lane = tl & 31;
     const int64_t blk = cta_block(a);
     const KernelParams kp = block_params(a, blk, kp_all);
     const int2 rg = a.blk[blk];
     const int t = rg.x + tl;
-    const bool valid = t < rg.y;
+    const bool valid = warp < NC && t < rg.y;
     const uint32_t vword = __ballot_sync(0xffffffffu, valid);
-    float2 tx2[4];  // this target (scaled by sigma), duplicated for the packed pair arithmetic
-    {
-        const float4 x = valid ? a.xs[t] : make_float4(0.f, 0.f, 0.f, 0.f);
-        tx2[0] = make_float2(x.x * kp.sig, x.x * kp.sig);
-        tx2[1] = make_float2(x.y * kp.sig, x.y * kp.sig);
-        tx2[2] = make_float2(x.z * kp.sig, x.z * kp.sig);
-        tx2[3] = make_float2(x.w * kp.sig, x.w * kp.sig);
-    }
-    const int64_t e0 = a.near_off[blk], e1 = a.near_off[blk + 1];
     if (tl == 0) {
 #pragma unroll
         for (int s = 0; s < ST; ++s) ptx::mbar_init(&full[s], 1);
-        ptx::mbar_init(&bar_mma, 1);
+        ptx::mbar_init(&aready[0], NC);
+        ptx::mbar_init(&aready[1], NC);
+        ptx::mbar_init(&mma_done[0], 1);
+        ptx::mbar_init(&mma_done[1], 1);
         ptx::fence_mbar_init();
+        s_fail = 0;
     }
-    if (lane == 0) s_valid[warp] = vword;
+    if (warp < NC && lane == 0) s_valid[warp] = vword;
     if (warp == 0) {
         tc::alloc(&tmem_base, S::TMEM_COLS);
         tc::relinquish();
@@ -238,182 +246,218 @@ __global__ void __launch_bounds__(kTB, 4) near_tc_kernel(MvmArgs a, KernelParams
     __syncthreads();
     tc::fence_after_sync();
     const uint32_t tmem = tmem_base;
-    const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
-    tc::st32_zero(tmem + lane_base);  // accumulator rows start at zero; every MMA accumulates
-    tc::wait_st();
 
-    // producer state (thread 0): chunks issued so far
-    NearChunks pit;
-    int issued = 0;
-    auto issue = [&]() {
-        if (pit.done()) return;
-        const int n = pit.count();
-        const int slot = issued % ST;
-        const uint32_t bytes = (uint32_t)n * F4 * 16u;
-        ptx::mbar_arrive_expect_tx(&full[slot], bytes);
-        ptx::bulk_g2s(&stage[slot][0], a.rec + (int64_t)pit.cb * F4, bytes, &full[slot]);
-        ++issued;
-        pit.next(a);
-    };
-    NearChunks it;
-    it.start(a, e0, e1);
-    if (tl == 0) {
-        pit = it;
-        for (int s = 0; s < ST; ++s) issue();
-    }
-    float acc[NR];
+    if (warp == NC) {
+        // ---------------------------------------------------------------- producer / issuer
+        if (lane == 0) {
+            NearChunks pit;
+            pit.start(a, a.near_off[blk], a.near_off[blk + 1]);
+            int issued = 0;   // chunks (and the end marker) handed to stages
+            int nchunks = -1; // known once the end marker is written
+            auto produce = [&]() {
+                const int slot = issued % ST;
+                NearChunkInfo& in = info[slot];
+                if (pit.done()) {
+                    in.n = 0;
+                    nchunks = issued;
+                    ptx::mbar_arrive(&full[slot]);
+                } else {
+                    const int n = pit.count();
+                    const int mask = a.near_ent[pit.e].y;
+                    in.n = n;
 #pragma unroll
-    for (int r = 0; r < NR; ++r) acc[r] = 0.f;
-    bool ok = true;
-    bool dirty = false;  // this warp's accumulator rows hold products not yet added to acc
-    int c = 0;
-    int waited = 0;      // thread 0: chunks whose records it has seen land
-    for (; !it.done(); it.next(a), ++c) {
-        const int slot = c % ST;
-        const int n = it.count();
-        const int mask = a.near_ent[it.e].y;
-        const uint32_t mword = (mask < 0 ? 0xFFFFFFFFu : __ldg(&a.masks[(int64_t)mask * kMaskWords + warp])) & vword;
-        // 1. records of chunk c
-        ok = ok && ptx::mbar_wait_bounded(&full[slot], (uint32_t)((c / ST) & 1), kWaitCycles);
-        if (tl == 0 && ok) waited = c + 1;
-        // 2. the MMAs of chunk c - 1 are done: the A columns and the B planes are free
-        bool stored = false;
-        if (c > 0) {
-            ok = ok && ptx::mbar_wait_bounded(&bar_mma, (uint32_t)((c - 1) & 1), kWaitCycles);
+                    for (int w = 0; w < kMaskWords; ++w)
+                        in.on[w] = (mask < 0 ? 0xFFFFFFFFu : __ldg(&a.masks[(int64_t)mask * kMaskWords + w])) & s_valid[w];
+                    const uint32_t bytes = (uint32_t)n * F4 * 16u;
+                    ptx::mbar_arrive_expect_tx(&full[slot], bytes);
+                    ptx::bulk_g2s(&stage[slot][0], a.rec + (int64_t)pit.cb * F4, bytes, &full[slot]);
+                    pit.next(a);
+                }
+                ++issued;
+            };
+            for (int s = 0; s < ST && nchunks < 0; ++s) produce();
+            int c = 0;
+            bool ok = true;
+            for (; nchunks < 0 || c < nchunks; ++c) {
+                const int slot = c % ST, ab = c & 1;
+                ok = ptx::mbar_wait_bounded(&aready[ab], (uint32_t)((c >> 1) & 1), kWaitCycles) && !s_fail;
+                if (!ok) break;
+                tc::fence_after_sync();
+                const NearChunkInfo in = info[slot];
+                const uint32_t off[kMaskWords] = {~in.on[0], ~in.on[1], ~in.on[2], ~in.on[3]};
+                const int nks = (in.n + 7) / 8;
+                for (int ks = 0; ks < nks; ++ks) {
+                    const uint64_t bh = tc::smem_desc(&bpl[ab][0][ks * 256], 512, 128);
+                    const uint64_t bl = tc::smem_desc(&bpl[ab][1][ks * 256], 512, 128);
+                    const uint32_t ahi = tmem + S::COL_A + ab * S::SLOT_COLS + ks * 8, alo = ahi + CH;
+                    tc::mma_tf32_ts_masked(tmem, ahi, bh, IDESC, off);
+                    tc::mma_tf32_ts_masked(tmem, ahi, bl, IDESC, off);
+                    tc::mma_tf32_ts_masked(tmem, alo, bh, IDESC, off);
+                }
+                tc::commit(&mma_done[ab]);
+                // every consumer has read stage `slot`: refill it ST chunks ahead
+                if (nchunks < 0) {
+                    ptx::fence_proxy_async_smem();
+                    produce();
+                }
+            }
+            if (!ok) {
+                s_fail = 1;
+                atomicExch(a.err, 1);
+                // let the copies and MMAs in flight finish before the CTA leaves (bounded)
+                for (int j = c; j < issued; ++j)
+                    ptx::mbar_wait_bounded(&full[j % ST], (uint32_t)((j / ST) & 1), kWaitCycles);
+                if (c >= 1) ptx::mbar_wait_bounded(&mma_done[(c - 1) & 1], (uint32_t)(((c - 1) >> 1) & 1), kWaitCycles);
+                if (c >= 2) ptx::mbar_wait_bounded(&mma_done[c & 1], (uint32_t)(((c - 2) >> 1) & 1), kWaitCycles);
+            }
+        }
+    } else {
+        // ---------------------------------------------------------------- consumers
+        const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
+        float2 tx2[4];  // this target (scaled by sigma), duplicated for the packed pair arithmetic
+        {
+            const float4 x = valid ? a.xs[t] : make_float4(0.f, 0.f, 0.f, 0.f);
+            tx2[0] = make_float2(x.x * kp.sig, x.x * kp.sig);
+            tx2[1] = make_float2(x.y * kp.sig, x.y * kp.sig);
+            tx2[2] = make_float2(x.z * kp.sig, x.z * kp.sig);
+            tx2[3] = make_float2(x.w * kp.sig, x.w * kp.sig);
+        }
+        tc::st32_zero(tmem + lane_base);  // accumulator rows start at zero; every MMA accumulates
+        tc::wait_st();
+        float acc[NR];
+#pragma unroll
+        for (int r = 0; r < NR; ++r) acc[r] = 0.f;
+        bool ok = true;
+        bool dirty = false;  // this warp's accumulator rows hold products not yet added to acc
+        int c = 0;
+        for (;; ++c) {
+            const int slot = c % ST, ab = c & 1;
+            ok = ptx::mbar_wait_bounded(&full[slot], (uint32_t)((c / ST) & 1), kWaitCycles);
+            if (!__all_sync(0xffffffffu, ok) || s_fail) { ok = false; break; }
+            const int n = info[slot].n;
+            if (n == 0) break;
+            const uint32_t mword = info[slot].on[warp];
+            // MMAs of chunk c-2 done: A slot and B planes ab are free
+            if (c >= 2) {
+                ok = ptx::mbar_wait_bounded(&mma_done[ab], (uint32_t)(((c - 2) >> 1) & 1), kWaitCycles);
+                if (!__all_sync(0xffffffffu, ok)) break;
+            }
+            bool stored = false;
+            if (c > 0 && c % S::FLUSH == 0) {
+                // every FLUSH chunks: wait for chunk c-1 too, then accumulator rows -> registers
+                ok = ptx::mbar_wait_bounded(&mma_done[(c - 1) & 1], (uint32_t)(((c - 1) >> 1) & 1), kWaitCycles);
+                if (!__all_sync(0xffffffffu, ok)) break;
+                if (dirty) {
+                    tc::fence_after_sync();
+                    add_partial(tmem + lane_base, acc);
+                    tc::st32_zero(tmem + lane_base);
+                    dirty = false;
+                    stored = true;
+                }
+            }
             tc::fence_after_sync();
-            // 3. every kFlush chunks: accumulator rows -> float32 registers, then zero them
-            if (c % kFlush == 0 && dirty && __all_sync(0xffffffffu, ok)) {
-                add_partial(tmem + lane_base, acc);
-                tc::st32_zero(tmem + lane_base);
-                dirty = false;
-                stored = true;
+            const float4* sb = &stage[slot][0];
+            {   // B operand: consumer warp w rearranges sources 4w..4w+3; lane = right-hand side.
+                // Element (n, k) sits at float (k/4)*128 + n*4 + k%4.
+                uint32_t h[4], l[4];
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    const int k = 4 * warp + i;
+                    const float v = k < n ? reinterpret_cast<const float*>(sb + k * F4)[4 + lane] : 0.f;
+                    split_tf32(v, h[i], l[i]);
+                }
+                *reinterpret_cast<uint4*>(&bpl[ab][0][warp * 128 + lane * 4]) = make_uint4(h[0], h[1], h[2], h[3]);
+                *reinterpret_cast<uint4*>(&bpl[ab][1][warp * 128 + lane * 4]) = make_uint4(l[0], l[1], l[2], l[3]);
             }
-        }
-        const float4* sb = &stage[slot][0];
-        // 4. B operand of chunk c: warp w rearranges source groups w and w + 4 (4 sources each);
-        //    lane = right-hand side.  Element (n, k) sits at float (k/4)*128 + n*4 + k%4.
-#pragma unroll
-        for (int kg = warp; kg < CH / 4; kg += 4) {
-            uint32_t h[4], l[4];
-#pragma unroll
-            for (int i = 0; i < 4; ++i) {
-                const int k = 4 * kg + i;
-                const float v = k < n ? reinterpret_cast<const float*>(sb + k * F4)[4 + lane] : 0.f;
-                split_tf32(v, h[i], l[i]);
-            }
-            *reinterpret_cast<uint4*>(&bpl[0][kg * 128 + lane * 4]) = make_uint4(h[0], h[1], h[2], h[3]);
-            *reinterpret_cast<uint4*>(&bpl[1][kg * 128 + lane * 4]) = make_uint4(l[0], l[1], l[2], l[3]);
-        }
-        // 5. A operand: this row's kernel values against the chunk, 16 sources at a time, into
-        //    tensor memory (rows of targets outside the mask are computed anyway when their warp
-        //    is busy, and left out by the MMA)
-        if (mword != 0u) {
-            {   // this warp's SoA copy of the chunk's negated coordinates (zeros past the chunk's
-                // end: those columns meet zero weights in B)
-                const float4 r = lane < n ? sb[lane * F4] : make_float4(0.f, 0.f, 0.f, 0.f);
-                s_src[warp][0][lane] = -r.x;
-                s_src[warp][1][lane] = -r.y;
-                s_src[warp][2][lane] = -r.z;
-                if (D == 4) s_src[warp][3][lane] = -r.w;
-            }
-            __syncwarp();
-#pragma unroll
-            for (int h0 = 0; h0 < CH; h0 += 16) {
-                uint32_t khi[16], klo[16];
-#pragma unroll
-                for (int j4 = 0; j4 < 16; j4 += 4) {
-                    const int j = h0 + j4;
-                    const float4 X = *reinterpret_cast<const float4*>(&s_src[warp][0][j]);
-                    const float4 Y = *reinterpret_cast<const float4*>(&s_src[warp][1][j]);
-                    const float4 Z = *reinterpret_cast<const float4*>(&s_src[warp][2][j]);
-                    float2 q[2];
-#pragma unroll
-                    for (int hh = 0; hh < 2; ++hh) {
-                        const float2 dx = __fadd2_rn(tx2[0], hh ? make_float2(X.z, X.w) : make_float2(X.x, X.y));
-                        const float2 dy = __fadd2_rn(tx2[1], hh ? make_float2(Y.z, Y.w) : make_float2(Y.x, Y.y));
-                        const float2 dz = __fadd2_rn(tx2[2], hh ? make_float2(Z.z, Z.w) : make_float2(Z.x, Z.y));
-                        q[hh] = __ffma2_rn(dx, dx, __ffma2_rn(dy, dy, __fmul2_rn(dz, dz)));
-                    }
-                    if (D == 4) {
-                        const float4 W = *reinterpret_cast<const float4*>(&s_src[warp][3][j]);
-                        const float2 dw0 = __fadd2_rn(tx2[3], make_float2(W.x, W.y));
-                        const float2 dw1 = __fadd2_rn(tx2[3], make_float2(W.z, W.w));
-                        q[0] = __ffma2_rn(dw0, dw0, q[0]);
-                        q[1] = __ffma2_rn(dw1, dw1, q[1]);
-                    }
-#pragma unroll
-                    for (int hh = 0; hh < 2; ++hh) {
-                        const float2 kv = kval2<KIND>(q[hh], kp);
-                        split2(kv, khi[j4 + 2 * hh], khi[j4 + 2 * hh + 1], klo[j4 + 2 * hh], klo[j4 + 2 * hh + 1]);
+            if (mword != 0u) {
+                {   // this warp's SoA copy of the chunk's negated coordinates (zeros past the
+                    // chunk's end: those columns meet zero weights in B)
+                    const float4 r = lane < n ? sb[lane * F4] : make_float4(0.f, 0.f, 0.f, 0.f);
+                    if (lane < CH) {
+                        s_src[warp][0][lane] = -r.x;
+                        s_src[warp][1][lane] = -r.y;
+                        s_src[warp][2][lane] = -r.z;
+                        if (D == 4) s_src[warp][3][lane] = -r.w;
                     }
                 }
-                tc::st16(tmem + lane_base + S::COL_AHI + h0, khi);
-                tc::st16(tmem + lane_base + S::COL_ALO + h0, klo);
-            }
-            dirty = true;
-            stored = true;
-        }
-        if (stored) tc::wait_st();
-        // 6. publish (shared-memory B to the async proxy, tensor-memory A to the MMA issuer)
-        ptx::fence_proxy_async_smem();
-        tc::fence_before_sync();
-        if (!__syncthreads_and(ok)) {
-            ok = false;
-            break;
-        }
-        // 7. issue, then refill the stage of chunk c (every thread has read it) with chunk c + ST
-        if (tl == 0) {
-            tc::fence_after_sync();
-            uint32_t off[kMaskWords];  // disable-output-lane: 1 = leave the row alone
+                __syncwarp();
+                uint32_t khi[CH], klo[CH];
 #pragma unroll
-            for (int w = 0; w < kMaskWords; ++w)
-                off[w] = ~((mask < 0 ? 0xFFFFFFFFu : __ldg(&a.masks[(int64_t)mask * kMaskWords + w])) & s_valid[w]);
-            const int nks = (n + 7) / 8;
-#pragma unroll 1
-            for (int ks = 0; ks < nks; ++ks) {
-                const uint64_t bh = tc::smem_desc(&bpl[0][ks * 256], 512, 128);
-                const uint64_t bl = tc::smem_desc(&bpl[1][ks * 256], 512, 128);
-                const uint32_t ahi = tmem + S::COL_AHI + ks * 8, alo = tmem + S::COL_ALO + ks * 8;
-                tc::mma_tf32_ts_masked(tmem, ahi, bh, IDESC, off);
-                tc::mma_tf32_ts_masked(tmem, ahi, bl, IDESC, off);
-                tc::mma_tf32_ts_masked(tmem, alo, bh, IDESC, off);
+                for (int j4 = 0; j4 < CH; j4 += 4) {
+                    if (j4 < 8 || n > 8) {  // the second MMA K-step only when the chunk has one
+                        const float4 X = *reinterpret_cast<const float4*>(&s_src[warp][0][j4]);
+                        const float4 Y = *reinterpret_cast<const float4*>(&s_src[warp][1][j4]);
+                        const float4 Z = *reinterpret_cast<const float4*>(&s_src[warp][2][j4]);
+                        float2 q[2];
+#pragma unroll
+                        for (int hh = 0; hh < 2; ++hh) {
+                            const float2 dx = __fadd2_rn(tx2[0], hh ? make_float2(X.z, X.w) : make_float2(X.x, X.y));
+                            const float2 dy = __fadd2_rn(tx2[1], hh ? make_float2(Y.z, Y.w) : make_float2(Y.x, Y.y));
+                            const float2 dz = __fadd2_rn(tx2[2], hh ? make_float2(Z.z, Z.w) : make_float2(Z.x, Z.y));
+                            q[hh] = __ffma2_rn(dx, dx, __ffma2_rn(dy, dy, __fmul2_rn(dz, dz)));
+                        }
+                        if (D == 4) {
+                            const float4 W = *reinterpret_cast<const float4*>(&s_src[warp][3][j4]);
+                            const float2 dw0 = __fadd2_rn(tx2[3], make_float2(W.x, W.y));
+                            const float2 dw1 = __fadd2_rn(tx2[3], make_float2(W.z, W.w));
+                            q[0] = __ffma2_rn(dw0, dw0, q[0]);
+                            q[1] = __ffma2_rn(dw1, dw1, q[1]);
+                        }
+#pragma unroll
+                        for (int hh = 0; hh < 2; ++hh) {
+                            const float2 kv = kval2<KIND>(q[hh], kp);
+                            split2(kv, khi[j4 + 2 * hh], khi[j4 + 2 * hh + 1], klo[j4 + 2 * hh], klo[j4 + 2 * hh + 1]);
+                        }
+                    } else {
+#pragma unroll
+                        for (int i = 0; i < 4; ++i) khi[j4 + i] = klo[j4 + i] = 0u;
+                    }
+                }
+                const uint32_t acol = tmem + lane_base + S::COL_A + ab * S::SLOT_COLS;
+                tc::st16(acol, khi);
+                tc::st16(acol + CH, klo);
+                dirty = true;
+                stored = true;
             }
-            tc::commit(&bar_mma);
+            if (stored) tc::wait_st();
+            // publish: B planes to the async proxy, A rows to the issuer
             ptx::fence_proxy_async_smem();
-            issue();
+            tc::fence_before_sync();
+            __syncwarp();
+            if (lane == 0) ptx::mbar_arrive(&aready[ab]);
         }
-    }
-    // c chunks were committed; wait for the last, then add what the accumulator rows still hold
-    if (ok && c > 0) ok = ptx::mbar_wait_bounded(&bar_mma, (uint32_t)((c - 1) & 1), kWaitCycles);
-    const bool all_ok = __syncthreads_and(ok) != 0;
-    tc::fence_after_sync();
-    if (dirty && all_ok) add_partial(tmem + lane_base, acc);
-    if (!all_ok && tl == 0) {
-        atomicExch(a.err, 1);
-        // let the copies and MMAs still in flight finish before the CTA leaves (bounded)
-        for (int j = waited; j < issued; ++j)
-            ptx::mbar_wait_bounded(&full[j % ST], (uint32_t)((j / ST) & 1), kWaitCycles);
-        if (c > 0) ptx::mbar_wait_bounded(&bar_mma, (uint32_t)((c - 1) & 1), kWaitCycles);
+        // chunks 0..c-1 were handed to the issuer; wait for the last two, then add what the
+        // accumulator rows still hold
+        if (ok && c >= 1) ok = ptx::mbar_wait_bounded(&mma_done[(c - 1) & 1], (uint32_t)(((c - 1) >> 1) & 1), kWaitCycles);
+        if (ok && c >= 2) ok = ptx::mbar_wait_bounded(&mma_done[c & 1], (uint32_t)(((c - 2) >> 1) & 1), kWaitCycles);
+        ok = __all_sync(0xffffffffu, ok);
+        if (!ok) {
+            s_fail = 1;
+            if (lane == 0) atomicExch(a.err, 1);
+        }
+        tc::fence_after_sync();
+        if (ok && dirty) add_partial(tmem + lane_base, acc);
+        __syncwarp();
+        if (ok && valid)
+#pragma unroll
+            for (int r = 0; r < NR; ++r)
+                if (r < a.nr) acc_store(a, r, t, acc[r] * kp.scale);
     }
     tc::fence_before_sync();
     __syncthreads();
     if (warp == 0) tc::dealloc(tmem, S::TMEM_COLS);
-    if (valid && all_ok)
-#pragma unroll
-        for (int r = 0; r < NR; ++r)
-            if (r < a.nr) a.ynear[(int64_t)r * a.N + t] = acc[r] * kp.scale;
 }
 
 template <int D>
 void launch_near_tc_dim(int kind, unsigned grid, cudaStream_t st, const MvmArgs& a, const KernelParams& kp) {
     switch (kind) {
-    case FKT_GAUSSIAN: near_tc_kernel<D, FKT_GAUSSIAN><<<grid, kTB, 0, st>>>(a, kp); break;
-    case FKT_EXPONENTIAL: near_tc_kernel<D, FKT_EXPONENTIAL><<<grid, kTB, 0, st>>>(a, kp); break;
-    case FKT_MATERN32: near_tc_kernel<D, FKT_MATERN32><<<grid, kTB, 0, st>>>(a, kp); break;
-    case FKT_MATERN52: near_tc_kernel<D, FKT_MATERN52><<<grid, kTB, 0, st>>>(a, kp); break;
-    case FKT_CAUCHY: near_tc_kernel<D, FKT_CAUCHY><<<grid, kTB, 0, st>>>(a, kp); break;
-    case FKT_RATQUAD: near_tc_kernel<D, FKT_RATQUAD><<<grid, kTB, 0, st>>>(a, kp); break;
-    default: near_tc_kernel<D, FKT_LAPLACE><<<grid, kTB, 0, st>>>(a, kp); break;
+    case FKT_GAUSSIAN: near_tc_kernel<D, FKT_GAUSSIAN><<<grid, NearTcShape::THREADS, 0, st>>>(a, kp); break;
+    case FKT_EXPONENTIAL: near_tc_kernel<D, FKT_EXPONENTIAL><<<grid, NearTcShape::THREADS, 0, st>>>(a, kp); break;
+    case FKT_MATERN32: near_tc_kernel<D, FKT_MATERN32><<<grid, NearTcShape::THREADS, 0, st>>>(a, kp); break;
+    case FKT_MATERN52: near_tc_kernel<D, FKT_MATERN52><<<grid, NearTcShape::THREADS, 0, st>>>(a, kp); break;
+    case FKT_CAUCHY: near_tc_kernel<D, FKT_CAUCHY><<<grid, NearTcShape::THREADS, 0, st>>>(a, kp); break;
+    case FKT_RATQUAD: near_tc_kernel<D, FKT_RATQUAD><<<grid, NearTcShape::THREADS, 0, st>>>(a, kp); break;
+    default: near_tc_kernel<D, FKT_LAPLACE><<<grid, NearTcShape::THREADS, 0, st>>>(a, kp); break;
     }
 }
 
