@@ -16,7 +16,7 @@
 
 #include <cuda_bf16.h>
 
-#include "mvm_kernels.cuh"
+#include "near_tc.cuh"
 
 namespace fkt {
 
@@ -296,6 +296,224 @@ __global__ void __launch_bounds__(kTB) far_tc_kernel(MvmArgs a, KernelParams kp_
         for (int r = 0; r < nr_total; ++r) a.yfar[(int64_t)r * a.N + t] = acc[r];  // tree order, coalesced
 }
 
+// ----------------------------------------------------------------------------------------
+// d = 3, BF16 / BF16 hi+lo: the basis rows go straight into tensor memory (A operand) instead
+// of shared memory, warp-specialised like the near field.
+//   warps 0-3 (thread = target = TMEM lane): per far entry i, wait for its info, then for the
+//     MMAs of entry i-1 (A columns free; every kFarFlush entries the accumulator rows are
+//     added into float32 registers and zeroed); a warp with a target in the entry's mask
+//     generates its rows 32 terms at a time and stores them as packed BF16 pairs (hi, lo
+//     planes) with tcgen05.st; arrive on aready.
+//   warp 4 lane 0: per entry, the node's centre, scale and the entry's row mask go to a stage
+//     with a bulk copy of the node's packed multipoles (ST entries ahead); waits aready,
+//     issues the MMAs (rows outside the mask disabled) and commits them to mma_done.
+// The accumulator is flushed into float32 registers because the tensor core's float32
+// accumulation drifts over thousands of MMAs.  Every wait is bounded.
+template <int P, int PREC>
+struct Tc2Shape {
+    using S = TcShape<3, P, PREC>;
+    static constexpr int NT = S::NT, NTP = S::NTP;
+    static constexpr int PLANE_COLS = NTP / 2;                     // packed BF16 pairs per plane
+    static constexpr int COL_AHI = 32, COL_ALO = 32 + PLANE_COLS;
+    static constexpr int USED = 32 + S::PLANES * PLANE_COLS;
+    static constexpr int TMEM_COLS = USED <= 32 ? 32 : USED <= 64 ? 64 : USED <= 128 ? 128 : USED <= 256 ? 256 : 512;
+    static constexpr int ST = 3;                                    // multipole stages in flight
+    static constexpr int THREADS = 160;
+    static constexpr size_t smem_bytes() { return (size_t)ST * S::B_BYTES + (size_t)kTcN * 128 * 4 + 128; }
+    static constexpr bool supported = PREC != TC_TF32 && TMEM_COLS <= 256 && smem_bytes() <= 160 * 1024;
+};
+
+struct FarTc2Info {
+    float4 c;                  // node centre
+    float s;                   // node length scale
+    uint32_t on[kMaskWords];   // targets (TMEM lanes) that use the entry
+};
+
+template <int P, int PREC>
+__global__ void __launch_bounds__(160, P <= 7 ? 3 : 2) far_tc2_kernel(MvmArgs a, KernelParams kp_all, const __grid_constant__ FarTables T,
+                                                         const unsigned char* __restrict__ image, int nr_total) {
+    using Sh = Tc2Shape<P, PREC>;
+    using S = typename Sh::S;
+    constexpr int NT = Sh::NT, NTP = Sh::NTP, ST = Sh::ST, BB = S::B_BYTES, BPLANE = kTcN * NTP * 2;
+    constexpr int kFarFlush = 4;
+    constexpr uint32_t IDESC = tc::instr_desc(1u, 128u, (uint32_t)kTcN);
+    extern __shared__ __align__(128) unsigned char tc2_smem[];
+    unsigned char* Bbuf = tc2_smem;                                  // [ST][B_BYTES]
+    float* accs = reinterpret_cast<float*>(tc2_smem + ST * BB);      // [kTcN][128] float32 sums
+    __shared__ FarTc2Info info[ST];
+    __shared__ __align__(8) uint64_t full[ST], aready, mma_done;
+    __shared__ uint32_t tmem_base;
+    __shared__ uint32_t s_valid[kMaskWords];
+    __shared__ int s_fail;
+    const int tl = threadIdx.x, warp = tl >> 5, lane = tl & 31;
+    const int64_t blk = cta_block(a);
+    const KernelParams kp = block_params(a, blk, kp_all);
+    const int2 rg = a.blk[blk];
+    const int t = rg.x + tl;
+    const bool valid = warp < 4 && t < rg.y;
+    const uint32_t vword = __ballot_sync(0xffffffffu, valid);
+    const int64_t e0 = a.far_off[blk];
+    const int ne = (int)(a.far_off[blk + 1] - e0);
+    if (tl == 0) {
+#pragma unroll
+        for (int s = 0; s < ST; ++s) ptx::mbar_init(&full[s], 1);
+        ptx::mbar_init(&aready, 4);
+        ptx::mbar_init(&mma_done, 1);
+        ptx::fence_mbar_init();
+        s_fail = 0;
+    }
+    if (warp < 4 && lane == 0) s_valid[warp] = vword;
+    if (warp == 0) {
+        tc::alloc(&tmem_base, Sh::TMEM_COLS);
+        tc::relinquish();
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tmem = tmem_base;
+
+    if (warp == 4) {
+        if (lane == 0) {
+            int issued = 0;
+            auto produce = [&]() {
+                const int slot = issued % ST;
+                const int2 ent = a.far_ent[e0 + issued];
+                FarTc2Info& in = info[slot];
+                in.c = a.nd_cf[ent.x];
+                in.s = a.nd_scale[ent.x];
+#pragma unroll
+                for (int w = 0; w < kMaskWords; ++w)
+                    in.on[w] = (ent.y < 0 ? 0xFFFFFFFFu : __ldg(&a.masks[(int64_t)ent.y * kMaskWords + w])) & s_valid[w];
+                ptx::mbar_arrive_expect_tx(&full[slot], (uint32_t)BB);
+                ptx::bulk_g2s(Bbuf + slot * BB, image + (int64_t)ent.x * BB, (uint32_t)BB, &full[slot]);
+                ++issued;
+            };
+            while (issued < ST && issued < ne) produce();
+            bool ok = true;
+            int i = 0;
+            for (; i < ne; ++i) {
+                const int slot = i % ST;
+                ok = ptx::mbar_wait_bounded(&aready, (uint32_t)(i & 1), kWaitCycles) && !s_fail;
+                if (!ok) break;
+                tc::fence_after_sync();
+                uint32_t off[kMaskWords];
+#pragma unroll
+                for (int w = 0; w < kMaskWords; ++w) off[w] = ~info[slot].on[w];
+                const unsigned char* B = Bbuf + slot * BB;
+#pragma unroll 1
+                for (int ks = 0; ks < NTP / 16; ++ks) {
+                    const uint64_t bh = tc::smem_desc(B + ks * 256, 128, S::SBO_A);
+                    const uint32_t ahi = tmem + Sh::COL_AHI + ks * 8;
+                    tc::mma_bf16_ts_masked(tmem, ahi, bh, IDESC, off);
+                    if (PREC == TC_BF16X3) {
+                        const uint64_t bl = tc::smem_desc(B + BPLANE + ks * 256, 128, S::SBO_A);
+                        tc::mma_bf16_ts_masked(tmem, ahi, bl, IDESC, off);
+                        tc::mma_bf16_ts_masked(tmem, tmem + Sh::COL_ALO + ks * 8, bh, IDESC, off);
+                    }
+                }
+                tc::commit(&mma_done);
+                // the consumers saw the MMAs of entry i-1 complete before they arrived on aready
+                // for entry i: its stage is free for entry i-1+ST
+                if (i >= 1 && issued < ne) {
+                    ptx::fence_proxy_async_smem();
+                    produce();
+                }
+            }
+            if (!ok) {
+                s_fail = 1;
+                atomicExch(a.err, 1);
+                // the last copy of each stage may still be in flight; then the last MMAs
+                for (int j = issued > ST ? issued - ST : 0; j < issued; ++j)
+                    ptx::mbar_wait_bounded(&full[j % ST], (uint32_t)((j / ST) & 1), kWaitCycles);
+                if (i >= 1) ptx::mbar_wait_bounded(&mma_done, (uint32_t)((i - 1) & 1), kWaitCycles);
+            }
+        }
+    } else {
+        const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
+        const float4 xt = valid ? a.xs[t] : make_float4(0.f, 0.f, 0.f, 0.f);
+        tc::st32_zero(tmem + lane_base);
+        tc::wait_st();
+#pragma unroll
+        for (int r = 0; r < kTcN; ++r) accs[r * 128 + tl] = 0.f;
+        // accumulator rows -> the float32 sums in shared memory (conflict-free: r-major)
+        auto flush = [&]() {
+            float d[kTcN];
+            tc::ld16(tmem + lane_base, d);
+            tc::ld16(tmem + lane_base + 16, d + 16);
+#pragma unroll
+            for (int r = 0; r < kTcN; ++r) accs[r * 128 + tl] += d[r];
+        };
+        bool ok = true, dirty = false;
+        int i = 0;
+        for (; i < ne; ++i) {
+            const int slot = i % ST;
+            ok = ptx::mbar_wait_bounded(&full[slot], (uint32_t)((i / ST) & 1), kWaitCycles);
+            if (i >= 1 && ok) ok = ptx::mbar_wait_bounded(&mma_done, (uint32_t)((i - 1) & 1), kWaitCycles);
+            if (!__all_sync(0xffffffffu, ok) || s_fail) { ok = false; break; }
+            tc::fence_after_sync();
+            bool stored = false;
+            if (i > 0 && i % kFarFlush == 0 && dirty) {
+                flush();
+                tc::st32_zero(tmem + lane_base);
+                dirty = false;
+                stored = true;
+            }
+            const uint32_t mword = info[slot].on[warp];
+            if (mword != 0u) {
+                const float4 c = info[slot].c;
+                const float sc = info[slot].s;
+                float buf[16];
+                auto store_group = [&](int g) {  // terms 16g..16g+15 as 8 packed pairs per plane
+                    uint32_t hi[8], lo[8];
+#pragma unroll
+                    for (int i2 = 0; i2 < 8; ++i2) {
+                        const __nv_bfloat162 h = __floats2bfloat162_rn(buf[2 * i2], buf[2 * i2 + 1]);
+                        hi[i2] = bf2_bits(h);
+                        if (PREC == TC_BF16X3) {
+                            const float2 f = __bfloat1622float2(h);
+                            lo[i2] = bf2_bits(__floats2bfloat162_rn(buf[2 * i2] - f.x, buf[2 * i2 + 1] - f.y));
+                        }
+                    }
+                    tc::st8(tmem + lane_base + Sh::COL_AHI + g * 8, hi);
+                    if (PREC == TC_BF16X3) tc::st8(tmem + lane_base + Sh::COL_ALO + g * 8, lo);
+                };
+                far_basis<3, P>(xt, c, sc, kp, T, [&](int q, float v) {
+                    buf[q & 15] = v;
+                    if (q == NT - 1) {
+#pragma unroll
+                        for (int z = (q & 15) + 1; z < 16; ++z) buf[z] = 0.f;
+                        store_group(q >> 4);
+                    } else if ((q & 15) == 15) {
+                        store_group(q >> 4);
+                    }
+                });
+                dirty = true;
+                stored = true;
+            }
+            if (stored) tc::wait_st();
+            tc::fence_before_sync();
+            __syncwarp();
+            if (lane == 0) ptx::mbar_arrive(&aready);
+        }
+        if (ok && i >= 1) ok = ptx::mbar_wait_bounded(&mma_done, (uint32_t)((i - 1) & 1), kWaitCycles);
+        ok = __all_sync(0xffffffffu, ok);
+        if (!ok) {
+            s_fail = 1;
+            if (lane == 0) atomicExch(a.err, 1);
+        }
+        tc::fence_after_sync();
+        if (ok && dirty) flush();
+        __syncwarp();
+        if (ok && valid)
+#pragma unroll 4
+            for (int r = 0; r < kTcN; ++r)
+                if (r < nr_total) a.yfar[(int64_t)r * a.N + t] = accs[r * 128 + tl];  // tree order, coalesced
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    if (warp == 0) tc::dealloc(tmem, Sh::TMEM_COLS);
+}
+
 }  // namespace fkt
 
 namespace fkt {
@@ -327,7 +545,19 @@ int launch_tc_t(const TcLaunch& L) {
 template <int D, int P, int PREC>
 int launch_tc_far_t(const TcLaunch& L) {
     using S = TcShape<D, P, PREC>;
-    if constexpr (!S::supported) {
+    if constexpr (D == 3 && Tc2Shape<P, PREC>::supported) {
+        using Sh = Tc2Shape<P, PREC>;
+        const size_t smem = Sh::smem_bytes();
+        static bool attr = false;
+        if (!attr) {
+            FKT_CUDA_TRY(cudaFuncSetAttribute(far_tc2_kernel<P, PREC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              (int)smem));
+            attr = true;
+        }
+        far_tc2_kernel<P, PREC><<<(unsigned)L.nblocks, Sh::THREADS, smem, L.s_far>>>(*L.a, *L.kp, *L.T, L.image, L.nr_total);
+        FKT_CUDA_TRY(cudaGetLastError());
+        return FKT_OK;
+    } else if constexpr (!S::supported) {
         return FKT_ERR_UNSUPPORTED;
     } else {
         const size_t smem = S::smem_bytes();

@@ -71,6 +71,26 @@ __device__ __forceinline__ void st16(uint32_t taddr, const uint32_t v[16]) {
         : "memory");
 }
 
+// D[tmem] += A[tmem] * B[smem]^T (BF16 operands), accumulator rows with a set bit in off[] untouched.
+__device__ __forceinline__ void mma_bf16_ts_masked(uint32_t d_tmem, uint32_t a_tmem, uint64_t b, uint32_t idesc,
+                                                   const uint32_t off[4]) {
+    asm volatile(
+        "{\n"
+        ".reg .pred p;\n"
+        "setp.ne.b32 p, 1, 0;\n"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, {%4, %5, %6, %7}, p;\n"
+        "}\n" ::"r"(d_tmem),
+        "r"(a_tmem), "l"(b), "r"(idesc), "r"(off[0]), "r"(off[1]), "r"(off[2]), "r"(off[3])
+        : "memory");
+}
+
+// 8 consecutive 32-bit columns of this thread's TMEM lane.
+__device__ __forceinline__ void st8(uint32_t taddr, const uint32_t v[8]) {
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"r"(taddr), "r"(v[0]),
+                 "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7])
+                 : "memory");
+}
+
 // Zero 32 consecutive 32-bit columns of this thread's TMEM lane.
 __device__ __forceinline__ void st32_zero(uint32_t taddr) {
     asm volatile(
