@@ -1,22 +1,30 @@
-"""Benchmark: FKT MVMs/s on one GB300 for the N = 1M, d = 3 Gaussian-mixture workload.
+"""Benchmark: FKT MVMs/s on one GB300.
 
-Headline: the precision form (far field on the tensor cores, BF16 hi/lo split with float32
-accumulation; near field float32) for 32 right-hand sides of the Matern-3/2 kernel, with the
-plain float32 form timed on the same plan beside it, the Cauchy kernel as a second line, and the
-error of every form against the float64 dense product on a 10,000-target subsample.
+Default workload (the headline): N = 1M, d = 3 Gaussian-mixture points, Matern-3/2 (l = 0.2), p = 6,
+32 right-hand sides, in the precision form (near-field contraction on the tensor cores with TF32
+hi/lo operands, far-field contraction on the tensor cores with BF16 hi/lo operands, float32 kernel
+values and accumulation), with the plain float32 form (near and far on the CUDA cores) timed on the
+same plan beside it, the Cauchy kernel (l = 0.05) as a second line, and the error of every form
+against the float64 dense product on a 10,000-target subsample.
 
-One step = one fkt_mvm call over all right-hand sides (all stages of Algorithm 1: permute, s2m,
-near field, m2t + combine) on resident device buffers; one MVM = one right-hand side.  L2 is
-flushed between timed steps (a 256 MiB write outside the timed events).  Prints ONE JSON line.
+Other workloads (--workload): gauss20k (20k uniform points, Gaussian l = 0.1, p = 4, 1 RHS),
+laplace16m (16M points half uniform / half in 100 tight clusters, Laplace 1/(4 pi r), p = 8, 4 RHS,
+BF16 far field) and batch256 (256 independent problems of 2k-200k points in the unit ball, mixed
+Gaussian / Laplace / rational-quadratic kernels, 8 RHS, one CUDA-graph launch).
+
+One step = one product over all right-hand sides (all stages of Algorithm 1: permute, s2m, near
+field, m2t, combine) on resident device buffers; one MVM = one right-hand side of one problem.  L2
+is flushed between timed steps (a 256 MiB write outside the timed events).  Prints ONE JSON line.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--workload matern1m|gauss20k|laplace16m|batch256]
                     [--kernel matern32|cauchy] [--p P] [--theta T] [--leaf M] [--nrhs R]
                     [--far-precision bf16x3|tf32|bf16|fp32] [--near-precision tf32x3|fp32]
                     [--compare fp32|none]
 
---impl reference times the CPU float64 oracle (the slow reference program) on a bounded sample
-of the same workload.  Multi-GPU runs are independent replicas (one plan per rank, no
-collective): the value is the sum over ranks.
+--impl reference times the CPU float64 oracle (the slow reference program) on a bounded sample of
+the same workload.  Multi-GPU runs are independent replicas (one plan per rank, no collective):
+the value is the sum over ranks.
 """
 from __future__ import annotations
 
@@ -36,14 +44,46 @@ sys.path.insert(0, ROOT)
 
 from paper_2106_04487_gb300 import inputs  # noqa: E402
 
-KERNELS = {"matern32": ("matern32", 0.2), "cauchy": ("cauchy", 0.05)}
+KERNELS = {"matern32": ("matern32", 0.2, 1.0, 1.0), "cauchy": ("cauchy", 0.05, 1.0, 1.0)}
 PASS = 32  # right-hand sides per pass of the library
 
+# Workloads: points, kernel (name, lengthscale, alpha, scale), order, opening parameter, leaf size,
+# right-hand sides, near / far arithmetic of the headline form, weight distribution, error targets.
+WORKLOADS = {
+    "matern1m": dict(desc="d=3 N=1000000 gaussian-mixture(10 comps, std 0.05)", n=1_000_000,
+                     points=lambda n: inputs.gaussian_mixture(n, 3, 10, 0.05), kernel=KERNELS["matern32"],
+                     p=6, theta=0.375, leaf=256, nrhs=32, near="tf32x3", far="bf16x3", weights="normal",
+                     err_targets=10000),
+    "gauss20k": dict(desc="d=3 N=20000 uniform cube", n=20000, points=lambda n: inputs.uniform_cube(n, 3),
+                     kernel=("gaussian", 0.1, 1.0, 1.0), p=4, theta=0.5, leaf=512, nrhs=1, near="fp32",
+                     far="fp32", weights="normal", err_targets=20000),
+    "laplace16m": dict(desc="d=3 N=16000000 half uniform cube + half 100 clusters (std 0.005)", n=16_000_000,
+                       points=lambda n: inputs.uniform_plus_clusters(n, 3, 100, 0.005),
+                       kernel=("laplace", 1.0, 1.0, 1.0 / (4.0 * np.pi)), p=8, theta=0.5, leaf=512, nrhs=4,
+                       near="fp32", far="bf16", weights="uniform", err_targets=400),
+    "batch256": dict(desc="256 problems, N log-uniform [2000, 200000], unit ball, kernels gaussian l=0.1 / "
+                          "laplace 1/r / ratquad alpha=1 l=0.2", n=0, points=None, kernel=None, p=4, theta=0.5,
+                     leaf=512, nrhs=8, near="fp32", far="bf16x3", weights="normal", err_targets=150),
+}
+BATCH_KERNELS = [("gaussian", 0.1, 1.0, 1.0), ("laplace", 1.0, 1.0, 1.0), ("ratquad", 0.2, 1.0, 1.0)]
+
 # DRAM bytes (read + write) per launch of a kernel from one ncu capture, keyed by kernel and
-# workload (kernel, p, theta, leaf, nrhs, N); see profiles/near_tc_matern1m_p6_theta0375_nrhs32.md.
-# Any other workload reports null.
-PROFILED_TRAFFIC = {("near_tile_kernel<3,matern32,32>", "matern32", 6, 0.375, 256, 32, 1_000_000): 1.339e9 + 0.136e9,
-                    ("near_tc_kernel<3,matern32>", "matern32", 6, 0.375, 256, 32, 1_000_000): 0.899e9 + 0.130e9}
+# workload (kernel, p, theta, leaf, nrhs, N); see profiles/.  Any other workload reports null.
+PROFILED_TRAFFIC = {
+    ("near_tc_kernel<3,matern32>", "matern32", 6, 0.375, 256, 32, 1_000_000): 0.8986e9 + 0.1293e9,
+    ("far_tc2_kernel<6,bf16x3>", "matern32", 6, 0.375, 256, 32, 1_000_000): 1.4115e9 + 0.1316e9,
+}
+
+# Per-SM lane rates of GB300 used by the ALU rooflines: FP32 pipe 128 lanes/clock; the MUFU (XU)
+# pipe 32 lanes/clock (ncu: 2 ex2/sqrt per pair at 17.6 % XU utilisation while 5.5e11 pairs/s).
+FP32_LANES, MUFU_LANES = 128.0, 32.0
+
+
+def nterms(d: int, p: int) -> int:
+    n = 1
+    for i in range(1, d + 1):
+        n = n * (p + i) // i
+    return n
 
 
 def near_kernel_name(kname: str, nw: int, near_precision: str = "fp32") -> str:
@@ -53,17 +93,49 @@ def near_kernel_name(kname: str, nw: int, near_precision: str = "fp32") -> str:
     return f"{base}<3,{kname},{nw}>"
 
 
+def far_kernel_name(p: int, far_precision: str, nrhs: int) -> str:
+    if far_precision == "fp32":
+        return f"far_kernel<3,{p},1>" if nrhs == 1 else f"far_mr_kernel<3,{p}>"
+    if far_precision == "tf32":
+        return f"far_tc_kernel<3,{p},tf32>"
+    return f"far_tc2_kernel<{p},{far_precision}>"
+
+
+def near_pair_cost(kernel: str, nw: int, tensor: bool = False):
+    """Lower bound on SM lane-ops per near-field pair for a pass of nw right-hand sides:
+    (FP32-pipe lane-ops, MUFU lane-ops).
+
+    Per pair the method needs d = 3 subtractions and |x|^2 (1 MUL + 2 FMA), the kernel value and one
+    FMA per right-hand side.  Kernel value: Gaussian 2^-q (MUFU); Matern-3/2 sqrt (MUFU),
+    1 + u ln2 (FMA), 2^-u (MUFU), product (MUL); Cauchy / rational quadratic 1 + q (ADD), reciprocal
+    (MUFU); Laplace rsqrt (MUFU) and the r = 0 test.  With the contraction on the tensor cores
+    (tensor=True) the per-right-hand-side FMAs leave the FP32 pipe."""
+    fma = 0 if tensor else nw
+    extra, mufu = {"gaussian": (0, 1), "matern32": (2, 2), "cauchy": (1, 1), "ratquad": (1, 1),
+                   "laplace": (1, 1)}.get(kernel, (2, 2))
+    return 6 + extra + fma, mufu
+
+
+def far_pair_ops(p: int) -> int:
+    """FP32 lane-ops the method needs per (target, far node) pair in d = 3 before the contraction:
+    distance and direction (~10), kernel derivatives J_m, m <= p (~3 per order), the radial sums
+    R_kj = sum_m That_kjm J_m (j + 1 FMAs per (k, j)), the powers (s/r)^j and G = (s/r)^j R (p + pairs),
+    the (p+1)^2 harmonics by recurrence (~3 each) and the products Y_kh G_kj (one per term)."""
+    pairs = [(k, j) for k in range(p + 1) for j in range(k, p + 1, 2)]
+    return 10 + 3 * (p + 1) + sum(j + 1 for _, j in pairs) + p + len(pairs) + 3 * (p + 1) ** 2 + nterms(3, p)
+
+
 def launches_per_step(nrhs: int, far_precision: str) -> int:
     """Kernels the library launches per fkt_mvm.  Per pass of up to 32 right-hand sides: permute
     and near field once; s2m + s2m_reduce per group of 8 (1 for a single right-hand side on the
     float32 path); the float32 far field once per group, the tensor-core far field (pack + far)
-    once per pass."""
+    once per pass; unpermute once."""
     total = 0
     for r0 in range(0, nrhs, PASS):
         npass = min(PASS, nrhs - r0)
         group = 1 if (nrhs == 1 and far_precision == "fp32") else 8
         groups = (npass + group - 1) // group
-        total += 2 + 2 * groups + (groups if far_precision == "fp32" else 2)
+        total += 3 + 2 * groups + (groups if far_precision == "fp32" else 2)
     return total
 
 
@@ -73,28 +145,45 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--kernel", default="matern32", choices=list(KERNELS))
-    ap.add_argument("--p", type=int, default=6)
-    ap.add_argument("--theta", type=float, default=0.375)
-    ap.add_argument("--leaf", type=int, default=256)
-    ap.add_argument("--nrhs", type=int, default=32)
-    ap.add_argument("--near-tpt", type=int, default=2, choices=[2, 4])
-    ap.add_argument("--far-precision", default="bf16x3", choices=["bf16x3", "tf32", "bf16", "fp32"])
-    ap.add_argument("--near-precision", default="tf32x3", choices=["tf32x3", "fp32"],
+    ap.add_argument("--workload", default="matern1m", choices=list(WORKLOADS))
+    ap.add_argument("--kernel", default=None, choices=list(KERNELS),
+                    help="kernel of the matern1m workload (default matern32)")
+    ap.add_argument("--p", type=int, default=None)
+    ap.add_argument("--theta", type=float, default=None)
+    ap.add_argument("--leaf", type=int, default=None)
+    ap.add_argument("--nrhs", type=int, default=None)
+    ap.add_argument("--far-precision", default=None, choices=["bf16x3", "tf32", "bf16", "fp32"])
+    ap.add_argument("--near-precision", default=None, choices=["tf32x3", "fp32"],
                     help="near-field contraction of 32-wide passes: tensor cores (TF32 hi/lo) or CUDA cores")
     ap.add_argument("--compare", default="fp32", choices=["fp32", "none"],
                     help="plain float32 form (near and far on the CUDA cores) timed beside the headline one")
-    ap.add_argument("--second-kernel", default="cauchy", choices=list(KERNELS) + ["none"])
-    ap.add_argument("--n", type=int, default=1_000_000)
-    ap.add_argument("--err-targets", type=int, default=10000)
+    ap.add_argument("--second-kernel", default="cauchy", choices=list(KERNELS) + ["none"],
+                    help="second kernel of the matern1m workload")
+    ap.add_argument("--n", type=int, default=None)
+    ap.add_argument("--err-targets", type=int, default=None)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    return ap.parse_args()
+    a = ap.parse_args()
+    w = WORKLOADS[a.workload]
+    for key, wkey in [("p", "p"), ("theta", "theta"), ("leaf", "leaf"), ("nrhs", "nrhs"), ("far_precision", "far"),
+                      ("near_precision", "near"), ("n", "n"), ("err_targets", "err_targets")]:
+        if getattr(a, key) is None:
+            setattr(a, key, w[wkey])
+    a.kern = w["kernel"]
+    if a.workload == "matern1m" and a.kernel:
+        a.kern = KERNELS[a.kernel]
+    if a.workload != "matern1m":
+        a.second_kernel = "none"
+    return a
 
 
-def workload_name(a, kernel=None):
-    k, ell = KERNELS[kernel or a.kernel]
-    return (f"{k} l={ell} d=3 N={a.n} gaussian-mixture(10 comps, std 0.05) p={a.p} leaf={a.leaf} "
-            f"theta={a.theta} nrhs={a.nrhs} near={a.near_precision} far={a.far_precision}")
+def workload_name(a, kern=None):
+    if a.workload == "batch256":
+        return (f"{WORKLOADS['batch256']['desc']}, p={a.p} leaf={a.leaf} theta={a.theta} nrhs={a.nrhs} "
+                f"near={a.near_precision} far={a.far_precision}")
+    k = kern or a.kern
+    desc = WORKLOADS[a.workload]["desc"].replace(f"N={WORKLOADS[a.workload]['n']}", f"N={a.n}")
+    return (f"{k[0]} l={k[1]}{' scale=1/(4pi)' if k[0] == 'laplace' and k[3] != 1.0 else ''} {desc} p={a.p} "
+            f"leaf={a.leaf} theta={a.theta} nrhs={a.nrhs} near={a.near_precision} far={a.far_precision}")
 
 
 def load_peaks():
@@ -160,34 +249,13 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def near_pair_cost(kernel: str, nw: int, tensor: bool = False):
-    """Lower bound on SM issue slots per near-field pair for a pass of nw right-hand sides:
-    (FP32-pipe lane-ops, MUFU lane-ops).
-
-    Per pair the method needs d = 3 subtractions, |x|^2 (1 MUL + 2 FMA), the kernel value and
-    one FMA per right-hand side.  Matern-3/2: sqrt (MUFU), (1 + u ln2) (FMA), 2^-u (MUFU ex2),
-    product (MUL).  Cauchy: 1 + q (ADD), reciprocal (MUFU).  With the contraction on the tensor
-    cores (tensor=True) the per-right-hand-side FMAs leave the FP32 pipe."""
-    fma = 0 if tensor else nw
-    if kernel == "matern32":
-        return 3 + 3 + 2 + fma, 2
-    return 3 + 3 + 1 + fma, 1
-
-
-def nterms(d: int, p: int) -> int:
-    n = 1
-    for i in range(1, d + 1):
-        n = n * (p + i) // i
-    return n
-
-
-def time_form(plan, Wd, Yd, steps, warmup, flush, stream):
-    """Per-step CUDA-event times of plan.mvm on the plan's launching stream, with the library's
-    own per-stage events (near, far + wait, s2m) read after each step."""
+def time_form(obj, Wd, Yd, steps, warmup, flush, stream, stats=True):
+    """Per-step CUDA-event times of obj.mvm on the launching stream, with the library's own
+    per-stage events (near, far + wait, s2m) read after each step when stats is set."""
     import torch
 
     for _ in range(warmup):
-        plan.mvm(Wd, out=Yd)
+        obj.mvm(Wd, out=Yd)
     torch.cuda.synchronize()
     step_ms, near_ms, far_ms, s2m_ms = [], [], [], []
     for _ in range(steps):
@@ -195,22 +263,76 @@ def time_form(plan, Wd, Yd, steps, warmup, flush, stream):
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        plan.mvm(Wd, out=Yd)
+        obj.mvm(Wd, out=Yd)
         e1.record(stream)
         e1.synchronize()
         step_ms.append(e0.elapsed_time(e1))
-        s = plan.stats()
-        near_ms.append(s["last_near_ms"])
-        far_ms.append(s["last_far_ms"])
-        s2m_ms.append(s["last_s2m_ms"])
+        if stats:
+            s = obj.stats()
+            near_ms.append(s["last_near_ms"])
+            far_ms.append(s["last_far_ms"])
+            s2m_ms.append(s["last_s2m_ms"])
     torch.cuda.synchronize()
-    return {"step_ms": step_ms, "near_ms": float(np.mean(near_ms)), "far_ms": float(np.mean(far_ms)),
-            "s2m_ms": float(np.mean(s2m_ms))}
+    mean = lambda v: float(np.mean(v)) if v else None  # noqa: E731
+    return {"step_ms": step_ms, "near_ms": mean(near_ms), "far_ms": mean(far_ms), "s2m_ms": mean(s2m_ms)}
 
 
 def rel_errs(y, z, idx):
     """Per right-hand side relative 2-norm error of y (all targets) on the sampled targets idx."""
     return [float(np.linalg.norm(y[r, idx] - z[r]) / np.linalg.norm(z[r])) for r in range(z.shape[0])]
+
+
+def make_weights(a, n):
+    if WORKLOADS[a.workload]["weights"] == "uniform":
+        return inputs.uniform_weights(n, a.nrhs)
+    return inputs.normal_weights(n, a.nrhs)
+
+
+def rooflines(a, stats, head, nsm, peaks, src, kname, passes):
+    """Roofline of the near and far kernels of the headline form, dominant first."""
+    sm_max = peaks.get("sm_max_mhz", 2070.0)
+    nw = 1 if (a.nrhs == 1 and a.far_precision == "fp32") else (8 if a.nrhs <= 8 else 16 if a.nrhs <= 16 else 32)
+    near_tc = nw == 32 and a.near_precision == "tf32x3"
+    fp32_ops, mufu_ops = near_pair_cost(kname, nw, near_tc)
+    slots = max(fp32_ops / FP32_LANES, mufu_ops / MUFU_LANES)  # SM clocks per pair
+    peak_pairs = nsm * sm_max * 1e6 / slots
+    near_pairs = stats["near_pairs"] * passes  # one launch per pass; its kernel value serves the pass
+    near_ach = near_pairs / (head["near_ms"] / 1e3)
+    near_name = near_kernel_name(kname, nw, a.near_precision)
+    key = (a.kern[0], a.p, a.theta, a.leaf, a.nrhs, a.n)
+    near_roof = {"kernel": near_name, "bound": "alu", "achieved": near_ach / 1e9, "peak": peak_pairs / 1e9,
+                 "unit": "Gpair/s", "frac": near_ach / peak_pairs,
+                 "traffic": PROFILED_TRAFFIC.get((near_name,) + key),
+                 "traffic_unit": "bytes per launch (ncu dram__bytes_read + write)", "ms_per_step": head["near_ms"],
+                 "work_per_unit": f"{fp32_ops} FP32 + {mufu_ops} MUFU lane-ops per (target, source) near pair"
+                                  f"{'; contraction on the tensor cores' if near_tc else ''}",
+                 "peak_source": f"{nsm} SMs x {sm_max:.0f} MHz / max({fp32_ops}/{FP32_LANES:.0f} FP32, "
+                                f"{mufu_ops}/{MUFU_LANES:.0f} MUFU) SM-clocks per pair ({src} clock)"}
+    roofs = [near_roof]
+    if stats["far_pairs"] > 0 and head["far_ms"]:
+        ops = far_pair_ops(a.p)
+        far_peak = nsm * sm_max * 1e6 * FP32_LANES / ops
+        far_ach = stats["far_pairs"] / (head["far_ms"] / 1e3)
+        far_name = far_kernel_name(a.p, a.far_precision, a.nrhs)
+        roof = {"kernel": far_name, "bound": "alu", "achieved": far_ach / 1e9, "peak": far_peak / 1e9,
+                "unit": "Gpair/s", "frac": far_ach / far_peak, "traffic": PROFILED_TRAFFIC.get((far_name,) + key),
+                "traffic_unit": "bytes per launch (ncu dram__bytes_read + write)", "ms_per_step": head["far_ms"],
+                "work_per_unit": f"{ops} FP32 lane-ops per (target, far node) pair (basis), "
+                                 f"+ 2 x {nterms(3, a.p)} x nrhs contraction flops",
+                "peak_source": f"{nsm} SMs x {sm_max:.0f} MHz x {FP32_LANES:.0f} lanes / {ops} ({src} clock); "
+                               f"far stage time on its stream"}
+        if a.far_precision != "fp32":
+            copies = 3 if a.far_precision == "bf16x3" else 1
+            flops = 2.0 * stats["far_pairs"] * nterms(3, a.p) * a.nrhs * copies
+            peak_tf = peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops", 1900.0))
+            if a.far_precision == "tf32":
+                peak_tf *= 0.5  # nominal TF32 : BF16 dense ratio
+            roof["tensor"] = {"achieved_tflops": flops / (head["far_ms"] / 1e3) / 1e12, "peak_tflops": peak_tf,
+                              "frac": flops / (head["far_ms"] / 1e3) / 1e12 / peak_tf,
+                              "note": f"{copies} MMA products per term (hi/lo split); {src} sustained bf16 peak"}
+        roofs.append(roof)
+    roofs.sort(key=lambda r: -(r["ms_per_step"] or 0.0))
+    return roofs
 
 
 def run_ours(a):
@@ -226,18 +348,27 @@ def run_ours(a):
         import torch.distributed as dist
 
         dist.init_process_group("nccl")
-    kname, ell = KERNELS[a.kernel]
-    X = inputs.gaussian_mixture(a.n, 3, 10, 0.05)
-    W = inputs.normal_weights(a.n, a.nrhs)
-    Xd = torch.from_numpy(X).cuda()
+    batch = a.workload == "batch256"
+    if batch:
+        sizes = inputs.batch_sizes(256, 2000, 200000)
+        probs = [(inputs.unit_ball(int(n), 3, seed=100 + i), *BATCH_KERNELS[i % 3]) for i, n in enumerate(sizes)]
+        obj = fkt.Batch(probs, p=a.p, leaf_size=a.leaf, theta=a.theta)
+        N = obj.N
+        X = None
+        stats = dict(obj.totals)
+    else:
+        N = a.n
+        X = WORKLOADS[a.workload]["points"](N)
+        kname, ell, alpha, scale = a.kern
+        obj = fkt.Plan(torch.from_numpy(X).cuda(), kname, lengthscale=ell, alpha=alpha, scale=scale, p=a.p,
+                       leaf_size=a.leaf, theta=a.theta)
+        obj.set_option("timing", "1")
+        stats = obj.stats()
+    W = make_weights(a, N)
     Wd = torch.from_numpy(W).cuda()
     Yd = torch.empty_like(Wd)
-    plan = fkt.Plan(Xd, kname, lengthscale=ell, p=a.p, leaf_size=a.leaf, theta=a.theta)
-    plan.set_option("timing", "1")
-    plan.set_option("near_targets_per_thread", str(a.near_tpt))
-    plan.set_option("far_precision", a.far_precision)
-    plan.set_option("near_precision", a.near_precision)
-    stats = plan.stats()
+    obj.set_option("far_precision", a.far_precision)
+    obj.set_option("near_precision", a.near_precision)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     stream = torch.cuda.current_stream()
 
@@ -250,12 +381,12 @@ def run_ours(a):
 
     # headline form: warm-up, then exactly K timed steps between barriers
     for _ in range(a.warmup):
-        plan.mvm(Wd, out=Yd)
+        obj.mvm(Wd, out=Yd)
     barrier()
     with ClockSampler(local) as clk:
-        head = time_form(plan, Wd, Yd, a.steps, 0, flush, stream)
+        head = time_form(obj, Wd, Yd, a.steps, 0, flush, stream, stats=not batch)
     barrier()
-    plan.check()  # raises if a bounded device-side wait ran out during the timed steps
+    obj.check()  # raises if a bounded device-side wait ran out during the timed steps
     total_ms = float(sum(head["step_ms"]))
     if world > 1:
         import torch.distributed as dist
@@ -263,49 +394,60 @@ def run_ours(a):
         t = torch.tensor([total_ms], device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         total_ms = float(t.item())
-    value = a.steps * a.nrhs * world / (total_ms / 1e3)
+    mvms_per_step = a.nrhs * (256 if batch else 1)
+    value = a.steps * mvms_per_step * world / (total_ms / 1e3)
     y_head = Yd.cpu().numpy().astype(np.float64)
 
     # the plain float32 form on the same plan
     comp = None
     if a.compare != "none" and (a.far_precision, a.near_precision) != ("fp32", "fp32"):
-        plan.set_option("far_precision", "fp32")
-        plan.set_option("near_precision", "fp32")
-        comp = time_form(plan, Wd, Yd, max(3, a.steps // 2), 3, flush, stream)
-        plan.check()
+        obj.set_option("far_precision", "fp32")
+        obj.set_option("near_precision", "fp32")
+        comp = time_form(obj, Wd, Yd, max(3, a.steps // 2), 3, flush, stream, stats=not batch)
+        obj.check()
         y_comp = Yd.cpu().numpy().astype(np.float64)
-        plan.set_option("far_precision", a.far_precision)
-        plan.set_option("near_precision", a.near_precision)
+        obj.set_option("far_precision", a.far_precision)
+        obj.set_option("near_precision", a.near_precision)
 
     # end to end through the host-buffer entry point (copies inside the timed region)
     Wh = torch.from_numpy(W).pin_memory()
     Yh = torch.empty_like(Wh).pin_memory()
-    plan.set_option("timing", "0")
-    for _ in range(2):
-        fkt.fkt_mvm_host(plan.h, Wh, Yh, a.nrhs)
-    torch.cuda.synchronize()
     e2e_steps = max(3, a.steps // 2)
+    if batch:  # the batched entry point takes device buffers: the copies are timed around it
+        def host_call():
+            Wd.copy_(Wh, non_blocking=True)
+            obj.mvm(Wd, out=Yd)
+            Yh.copy_(Yd, non_blocking=True)
+            torch.cuda.synchronize()
+    else:
+        obj.set_option("timing", "0")
+
+        def host_call():
+            fkt.fkt_mvm_host(obj.h, Wh, Yh, a.nrhs)  # H2D copy, MVM, D2H copy, stream sync
+    for _ in range(2):
+        host_call()
+    torch.cuda.synchronize()
     e2e_total = 0.0
     for _ in range(e2e_steps):
         flush.fill_(1.0)
         torch.cuda.synchronize()
         t1 = time.perf_counter()
-        fkt.fkt_mvm_host(plan.h, Wh, Yh, a.nrhs)  # H2D copy, MVM, D2H copy, stream sync
+        host_call()
         e2e_total += time.perf_counter() - t1
-    e2e_value = e2e_steps * a.nrhs / e2e_total
-    plan.close()
+    e2e_value = e2e_steps * mvms_per_step / e2e_total
+    if not batch:
+        obj.close()
 
     # second kernel of the workload (both forms, fewer steps)
     second = None
-    if a.second_kernel != "none" and a.second_kernel != a.kernel:
-        k2, ell2 = KERNELS[a.second_kernel]
-        p2 = fkt.Plan(Xd, k2, lengthscale=ell2, p=a.p, leaf_size=a.leaf, theta=a.theta)
+    if a.second_kernel != "none" and KERNELS[a.second_kernel] != a.kern:
+        k2 = KERNELS[a.second_kernel]
+        p2 = fkt.Plan(torch.from_numpy(X).cuda(), k2[0], lengthscale=k2[1], alpha=k2[2], scale=k2[3], p=a.p,
+                      leaf_size=a.leaf, theta=a.theta)
         p2.set_option("timing", "1")
-        p2.set_option("near_targets_per_thread", str(a.near_tpt))
-        second = {"kernel": f"{k2} l={ell2}"}
+        second = {"kernel": f"{k2[0]} l={k2[1]}"}
         ys = {}
-        head_form = f"near {a.near_precision}, far {a.far_precision}"
-        forms = {head_form: (a.near_precision, a.far_precision)}
+        forms = {f"near {a.near_precision}, far {a.far_precision}": (a.near_precision, a.far_precision)}
         if comp is not None:
             forms["near fp32, far fp32"] = ("fp32", "fp32")
         for form, (npr, fpr) in forms.items():
@@ -320,61 +462,48 @@ def run_ours(a):
     # accuracy of every form against the float64 dense product on sampled targets
     from oracle import oracle as O
 
-    idx = inputs.subsample(a.n, a.err_targets)
-    zd = O.dense(X, O.kparams(kname, ell), W, idx)
-    err_head = rel_errs(y_head, zd, idx)
-    if comp is not None:
-        err_comp = rel_errs(y_comp, zd, idx)
+    if batch:
+        err_head, err_comp = [], []
+        order = np.argsort(sizes)
+        for i in sorted({int(order[0]), int(order[-1]), 1, 2, 100}):
+            Xi, kn, ell, alpha, scale = probs[i]
+            lo, hi = obj.offsets[i], obj.offsets[i + 1]
+            idx = inputs.subsample(hi - lo, a.err_targets, seed=7 + i)
+            zd = O.dense(Xi, O.kparams(kn, ell, alpha=alpha, scale=scale), W[:, lo:hi], idx)
+            err_head += rel_errs(y_head[:, lo:hi], zd, idx)
+            if comp is not None:
+                err_comp += rel_errs(y_comp[:, lo:hi], zd, idx)
+        err_note = f"5 problems (smallest, largest, 3 others) x {a.err_targets} targets"
+    else:
+        idx = inputs.subsample(N, a.err_targets)
+        zd = O.dense(X, O.kparams(a.kern[0], a.kern[1], alpha=a.kern[2], scale=a.kern[3]), W, idx)
+        err_head = rel_errs(y_head, zd, idx)
+        if comp is not None:
+            err_comp = rel_errs(y_comp, zd, idx)
+        err_note = f"{len(idx)} sampled targets"
     if second is not None:
         n2 = min(2000, a.err_targets)
-        idx2 = inputs.subsample(a.n, n2, seed=7)
-        z2 = O.dense(X, O.kparams(*KERNELS[a.second_kernel]), W, idx2)
+        idx2 = inputs.subsample(N, n2, seed=7)
+        k2 = KERNELS[a.second_kernel]
+        z2 = O.dense(X, O.kparams(k2[0], k2[1], alpha=k2[2], scale=k2[3]), W, idx2)
         for form, y in ys.items():
             e = rel_errs(y, z2, idx2)
             second[form]["rel_err_max"] = max(e)
             second[form]["rel_err_median"] = float(np.median(e))
         second["err_targets"] = n2
 
-    # roofline of the dominant kernel: the near field (FP32 + MUFU pipes, ALU bound) or the
-    # tensor-core far field (its contraction on the tensor pipe)
     peaks, src = load_peaks()
     clocks = clk.summary()
-    sm_max = peaks.get("sm_max_mhz", 2070.0)
     nsm = torch.cuda.get_device_properties(local).multi_processor_count
-    nw = 1 if (a.nrhs == 1 and a.far_precision == "fp32") else (8 if a.nrhs <= 8 else 16 if a.nrhs <= 16 else 32)
     passes = (a.nrhs + PASS - 1) // PASS
-    near_tc = nw == 32 and a.near_precision == "tf32x3"
-    fp32_ops, mufu_ops = near_pair_cost(kname, nw, near_tc)
-    slots_per_pair = max(fp32_ops / 128.0, mufu_ops / 16.0)  # SM clocks per pair (128 FP32, 16 MUFU lanes/SM)
-    peak_pairs = nsm * sm_max * 1e6 / slots_per_pair
-    near_pairs = stats["near_pairs"] * passes  # one launch per pass; its kernel value serves the pass
-    near_ach = near_pairs / (head["near_ms"] / 1e3)
-    near_name = near_kernel_name(kname, nw, a.near_precision)
-    traffic = PROFILED_TRAFFIC.get((near_name, kname, a.p, a.theta, a.leaf, a.nrhs, a.n))
-    near_roof = {"kernel": near_name, "bound": "alu", "achieved": near_ach / 1e9,
-                 "peak": peak_pairs / 1e9, "unit": "Gpair/s", "frac": near_ach / peak_pairs, "traffic": traffic,
-                 "traffic_unit": "bytes per launch (ncu dram__bytes_read + write)",
-                 "ms_per_step": head["near_ms"],
-                 "peak_source": f"{nsm} SMs x {sm_max:.0f} MHz / max({fp32_ops}/128 FP32, {mufu_ops}/16 MUFU) "
-                                f"SM-clocks per pair ({src} clock)"}
-    roofs = [near_roof]
-    if a.far_precision != "fp32":
-        nt = nterms(3, a.p)
-        flops = 2.0 * stats["far_pairs"] * nt * a.nrhs  # the m2t contraction, once (not the hi/lo copies)
-        far_ms = head["far_ms"]
-        peak_tf = peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops", 1900.0))
-        if a.far_precision == "tf32":
-            peak_tf *= 0.5  # nominal TF32 : BF16 dense ratio
-        ach_tf = flops / (far_ms / 1e3) / 1e12
-        roofs.append({"kernel": f"far_tc_kernel<3,{a.p},{a.far_precision}>", "bound": "tensor", "achieved": ach_tf,
-                      "peak": peak_tf, "unit": "TFLOP/s", "frac": ach_tf / peak_tf, "traffic": None,
-                      "ms_per_step": far_ms,
-                      "peak_source": f"{src} bf16 dense (sustained){' x 0.5 for tf32' if a.far_precision == 'tf32' else ''};"
-                                     f" far stage time (far_tc launch + wait for pack)"})
-    roofs.sort(key=lambda r: -r["ms_per_step"])
+    roofs = [] if batch else rooflines(a, stats, head, nsm, peaks, src, a.kern[0], passes)
+    if batch:
+        unit_desc = "problem-MVMs/s: one MVM = one right-hand side of one of the 256 problems"
+    else:
+        unit_desc = "one MVM = one right-hand side"
     out = {
-        "metric": f"FKT MVMs/s at N=1M, d=3 ({kname}, near {a.near_precision}, far {a.far_precision}, "
-                  f"rel.err vs FP64 dense {max(err_head):.1e})",
+        "metric": f"FKT MVMs/s ({a.workload}: {'mixed kernels' if batch else a.kern[0]}, near {a.near_precision}, "
+                  f"far {a.far_precision}, rel.err vs FP64 dense {max(err_head):.1e})",
         "value": value,
         "unit": "MVM/s",
         "n_gpus": world,
@@ -384,25 +513,27 @@ def run_ours(a):
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
-        "dtype": (f"f32 kernel values, {'tf32x3 tensor-core' if near_tc else 'f32'} near contraction, "
-                  f"{a.far_precision} far contraction, f32 accumulate"),
+        "dtype": (f"f32 kernel values, {'tf32x3 tensor-core' if a.near_precision == 'tf32x3' and a.nrhs > 16 else 'f32'} "
+                  f"near contraction, {a.far_precision} far contraction, f32 accumulate"),
         "data": "synthetic",
-        "config": {"workload": workload_name(a), "l2": "flushed between steps (256 MiB write)",
+        "config": {"workload": workload_name(a), "unit_note": unit_desc, "l2": "flushed between steps (256 MiB write)",
                    "rel_err_max": max(err_head), "rel_err_median": float(np.median(err_head)),
-                   "err_targets": a.err_targets, "err_reference": "float64 dense oracle",
+                   "err_targets": err_note, "err_reference": "float64 dense oracle",
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
-                   "plan_ms": stats["plan_ms"], "near_pairs": stats["near_pairs"], "far_pairs": stats["far_pairs"],
-                   "s2m_pairs": stats["s2m_pairs"],
+                   "plan_ms": stats.get("plan_ms"), "points": int(N), "near_pairs": stats["near_pairs"],
+                   "far_pairs": stats["far_pairs"], "s2m_pairs": stats["s2m_pairs"],
                    "stage_ms": {"near": head["near_ms"], "far+wait": head["far_ms"], "s2m": head["s2m_ms"]}},
-        "roofline": roofs[0],
+        "roofline": roofs[0] if roofs else None,
         "roofline_other": roofs[1:],
         "e2e": {"value": e2e_value, "unit": "MVM/s", "h2d_bytes_per_step": int(W.nbytes),
                 "d2h_bytes_per_step": int(W.nbytes)},
-        "gpu_launches": launches_per_step(a.nrhs, a.far_precision) * a.steps,
+        "gpu_launches": (None if batch else launches_per_step(a.nrhs, a.far_precision) * a.steps),
         "clocks": clocks,
     }
+    if batch:
+        out["gpu_launches_note"] = "one CUDA graph replay per step (near field per kernel kind, far field, s2m, permutes)"
     if comp is not None:
-        cv = a.nrhs * len(comp["step_ms"]) / (sum(comp["step_ms"]) / 1e3)
+        cv = mvms_per_step * len(comp["step_ms"]) / (sum(comp["step_ms"]) / 1e3)
         out["compare_form"] = {"form": "plain float32 (near and far on the CUDA cores)", "value": cv, "unit": "MVM/s",
                                "ms_per_step": float(np.mean(comp["step_ms"])), "rel_err_max": max(err_comp),
                                "rel_err_median": float(np.median(err_comp)),
@@ -411,7 +542,7 @@ def run_ours(a):
     if second is not None:
         out["second_kernel"] = second
     if rank == 0 and not a.no_cpu_baseline:
-        out["cpu_baseline"] = cpu_baseline(a, X, W)
+        out["cpu_baseline"] = cpu_baseline(a, X, W, probs if batch else None, obj if batch else None)
     if world > 1:
         import torch.distributed as dist
 
@@ -425,43 +556,58 @@ class OracleRunner:
     one full MVM of all right-hand sides; the oracle's tree (its plan) is built once and not
     counted."""
 
-    def __init__(self, a, X):
+    def __init__(self, X, kern, p, leaf, theta, nrhs):
         from oracle import oracle as O
 
         self.O = O
-        kname, ell = KERNELS[a.kernel]
         t0 = time.perf_counter()
-        self.F = O.FKT(X, O.kparams(kname, ell), a.p, a.leaf, a.theta)
+        self.F = O.FKT(X, O.kparams(kern[0], kern[1], alpha=kern[2], scale=kern[3]), p, leaf, theta)
         self.plan_s = time.perf_counter() - t0
-        self.a = a
+        self.n, self.nrhs = len(X), nrhs
 
     def mvm_seconds(self, W, target_sample):
         import ctypes
 
-        O, a = self.O, self.a
-        idx = inputs.subsample(a.n, target_sample, seed=5)
+        O = self.O
+        idx = inputs.subsample(self.n, target_sample, seed=5)
         Wd = np.ascontiguousarray(W, dtype=np.float64)
         t1 = time.perf_counter()
-        O.lib().orc_fkt_s2m(self.F.h, Wd.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), a.nrhs)
+        O.lib().orc_fkt_s2m(self.F.h, Wd.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), self.nrhs)
         t2 = time.perf_counter()
-        out = np.zeros((a.nrhs, len(idx)))
+        out = np.zeros((self.nrhs, len(idx)))
         T = np.ascontiguousarray(idx, dtype=np.int64)
         O.lib().orc_fkt_eval(self.F.h, T.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), len(T),
                              out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
         t3 = time.perf_counter()
-        return (t2 - t1) + (t3 - t2) * a.n / len(idx), t2 - t1, t3 - t2
+        return (t2 - t1) + (t3 - t2) * self.n / len(idx), t2 - t1, t3 - t2
 
     def describe(self, s2m_s, trav_s, target_sample):
-        return (f"s2m of {self.a.nrhs} right-hand sides over all nodes ({s2m_s:.1f} s) + traversal of "
-                f"{target_sample} of {self.a.n} targets ({trav_s:.1f} s), extrapolated to all targets; "
+        return (f"s2m of {self.nrhs} right-hand sides over all nodes ({s2m_s:.1f} s) + traversal of "
+                f"{target_sample} of {self.n} targets ({trav_s:.1f} s), extrapolated to all targets; "
                 f"oracle tree ({self.plan_s:.1f} s) not counted")
 
 
-def cpu_baseline(a, X, W, target_sample: int = 2000, budget_s: float = 10.0):
-    R = OracleRunner(a, X)
+def cpu_baseline(a, X, W, probs=None, batch=None, target_sample: int = 2000, budget_s: float = 10.0):
+    from oracle import oracle as O
+
+    if probs is not None:  # a few problems of the batch, extrapolated by points
+        secs, pts, descr = 0.0, 0, []
+        for i in (0, 1, 2):
+            Xi, *kern = probs[i]
+            lo, hi = batch.offsets[i], batch.offsets[i + 1]
+            R = OracleRunner(Xi, kern, a.p, a.leaf, a.theta, a.nrhs)
+            per_mvm, s2m_s, trav_s = R.mvm_seconds(W[:, lo:hi], min(500, hi - lo))
+            secs += per_mvm
+            pts += hi - lo
+            descr.append(f"problem {i} (N={hi - lo}, {kern[0]}): {per_mvm:.2f} s per {a.nrhs} RHS")
+        per_step = secs * batch.N / pts
+        return {"value": 256 * a.nrhs / per_step, "unit": "MVM/s", "cores": O.num_threads(), "kind": "oracle",
+                "sample": "; ".join(descr) + f"; extrapolated by points to all {batch.N} points"}
+    R = OracleRunner(X, a.kern, a.p, a.leaf, a.theta, a.nrhs)
+    target_sample = min(target_sample, len(X))
     per_mvm, s2m_s, trav_s = R.mvm_seconds(W, target_sample)
-    if trav_s < budget_s / 2:  # grow the target sample to about budget_s of traversal
-        target_sample = int(min(a.n, target_sample * budget_s / max(trav_s, 1e-3)))
+    if trav_s < budget_s / 2 and target_sample < len(X):  # grow the target sample to about budget_s of traversal
+        target_sample = int(min(len(X), target_sample * budget_s / max(trav_s, 1e-3)))
         per_mvm, s2m_s, trav_s = R.mvm_seconds(W, target_sample)
     return {"value": a.nrhs / per_mvm, "unit": "MVM/s", "cores": R.O.num_threads(), "kind": "oracle",
             "sample": R.describe(s2m_s, trav_s, target_sample)}
@@ -473,22 +619,30 @@ def run_reference(a):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return None
-    X = inputs.gaussian_mixture(a.n, 3, 10, 0.05)
-    W = inputs.normal_weights(a.n, a.nrhs)
-    R = OracleRunner(a, X)
-    sample = 200
+    if a.workload == "batch256":
+        sizes = inputs.batch_sizes(256, 2000, 200000)
+        X, kern, scale_mvms = inputs.unit_ball(int(sizes[0]), 3, seed=100), BATCH_KERNELS[0], 256
+        n_total = int(sizes.sum())
+    else:
+        X, kern, scale_mvms, n_total = WORKLOADS[a.workload]["points"](a.n), a.kern, 1, a.n
+    W = make_weights(a, len(X))
+    R = OracleRunner(X, kern, a.p, a.leaf, a.theta, a.nrhs)
+    sample = min(200, len(X))
     for _ in range(a.warmup):
-        R.mvm_seconds(W, 20)
+        R.mvm_seconds(W, min(20, len(X)))
     total, s2m_tot, trav_tot = 0.0, 0.0, 0.0
     for _ in range(a.steps):
         per_mvm, s2m_s, trav_s = R.mvm_seconds(W, sample)
-        total += per_mvm
+        total += per_mvm * n_total / len(X)
         s2m_tot += s2m_s
         trav_tot += trav_s
-    value = a.steps * a.nrhs / total
-    cb = {"value": value, "unit": "MVM/s", "cores": R.O.num_threads(), "kind": "oracle",
-          "sample": R.describe(s2m_tot / a.steps, trav_tot / a.steps, sample) + " (per step)"}
-    return {"impl": "reference", "metric": f"FKT MVMs/s at N=1M, d=3 ({KERNELS[a.kernel][0]}, float64 oracle)",
+    value = a.steps * a.nrhs * scale_mvms / total
+    note = R.describe(s2m_tot / a.steps, trav_tot / a.steps, sample) + " (per step)"
+    if a.workload == "batch256":
+        note += f"; problem 0 of the batch, extrapolated by points to all {n_total} points"
+    cb = {"value": value, "unit": "MVM/s", "cores": R.O.num_threads(), "kind": "oracle", "sample": note}
+    return {"impl": "reference",
+            "metric": f"FKT MVMs/s ({a.workload}: {kern[0] if a.workload != 'batch256' else 'mixed kernels'}, float64 oracle)",
             "value": value, "unit": "MVM/s", "n_gpus": a.gpus, "steps": a.steps, "warmup": a.warmup,
             "ms_per_step": 1e3 * total / a.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f64", "data": "synthetic", "config": {"workload": workload_name(a)}, "cpu_baseline": cb,
