@@ -25,14 +25,14 @@ namespace fkt {
 
 struct NearTcShape {
     static constexpr int NR = 32;                     // right-hand sides (the MMA's N)
-    static constexpr int CH = 16;                     // sources per chunk (2 MMA K-steps of 8)
-    static constexpr int ST = 6;                      // record stages in flight
+    static constexpr int CH = 32;                     // sources per chunk (4 MMA K-steps of 8)
+    static constexpr int ST = 4;                      // record stages in flight
     static constexpr int F4 = (4 + NR + 3) / 4;       // float4s per source record (point + weights)
     static constexpr int CONSUMERS = 4;               // warps that own the 128 TMEM lanes / targets
     static constexpr int THREADS = 32 * (CONSUMERS + 1);  // + one producer / MMA-issuer warp
-    static constexpr int TMEM_COLS = 128;             // accumulator 32 + 2 slots x (A hi 16 + A lo 16)
-    static constexpr int COL_A = 32, SLOT_COLS = 2 * CH;
-    static constexpr int FLUSH = 8;                   // chunks (6 MMAs each) per float32 flush
+    static constexpr int TMEM_COLS = 128;             // accumulator 32 + A hi 32 + A lo 32
+    static constexpr int COL_AHI = 32, COL_ALO = 64;
+    static constexpr int FLUSH = 4;                   // chunks (12 MMAs each) per float32 flush
 };
 
 namespace tc {
@@ -210,36 +210,39 @@ struct NearChunks {
 
 // Per record stage: what the producer resolved for the chunk it holds.
 struct NearChunkInfo {
-    int n;                     // sources in the chunk; 0 marks the end of the block's list
+    int n;                     // sources in the chunk
     uint32_t on[kMaskWords];   // targets (TMEM lanes) that use the chunk's leaf
 };
 
 // One CTA per 128-target block, warp-specialised:
-//   warps 0-3 (consumers, thread = target = TMEM lane): per chunk c, wait for its records and
-//     for the MMAs of chunk c-2 (A slot and B planes c%2 are free); every FLUSH chunks add the
-//     accumulator rows into float32 registers and zero them; rearrange their share of the
-//     weights into the B planes; a warp with a target in the chunk's mask evaluates its rows
-//     (float32 kernel values, split hi/lo) into its A slot; then arrive on aready[c%2].
-//   warp 4 lane 0 (producer / MMA issuer): resolves chunk metadata from the lists and
-//     bulk-copies source records ST chunks ahead; per chunk waits aready, issues 3 MMAs per 8
-//     sources (rows outside the mask disabled), commits them to mma_done[c%2], and refills the
-//     chunk's record stage.
-// The consumers touch no global memory in the loop and no CTA-wide barrier runs in it.  Every
-// wait is bounded; a wait that runs out sets s_fail and the error word, every role leaves its
-// loop, and the producer drains what it issued before the CTA frees its tensor memory.
+//   warps 0-3 (consumers, thread = target = TMEM lane): per chunk c of up to 32 sources, wait for
+//     its records; wait (named barrier) until the MMAs of chunk c-1 are complete, which frees the
+//     A columns and the B planes; every FLUSH chunks add the accumulator rows into float32
+//     registers and zero them; rearrange their share of the weights into the B planes; a warp
+//     with a target in the chunk's mask evaluates its rows (float32 kernel values, split hi/lo)
+//     into tensor memory; then arrive on the ready barrier.
+//   warp 4 (producer / MMA issuer, lane 0 works): resolves chunk metadata from the lists and
+//     bulk-copies source records ST chunks ahead; per chunk syncs on the ready barrier, issues 3
+//     MMAs per 8 sources (rows outside the mask disabled), refills the chunk's record stage,
+//     waits for the MMAs and arrives on the MMA barrier.
+// Hand-offs between the roles use named barriers, so waiting warps are descheduled instead of
+// polling.  Both roles run the same number of rounds (the block's chunk count, counted by all
+// threads up front) whatever happens: a bounded mbarrier wait that runs out sets s_fail, which
+// only skips work, and the producer drains what it issued before the CTA frees tensor memory.
 template <int D, int KIND>
 __global__ void __launch_bounds__(NearTcShape::THREADS, 4) near_tc_kernel(MvmArgs a, KernelParams kp_all) {
     using S = NearTcShape;
     constexpr int CH = S::CH, ST = S::ST, F4 = S::F4, NR = S::NR, NC = S::CONSUMERS;
     constexpr uint32_t IDESC = tc::instr_desc(2u, 128u, (uint32_t)NR);
+    constexpr uint32_t kBarReady = 1, kBarMma = 2, kBarThreads = S::THREADS;
     __shared__ __align__(128) float4 stage[ST][CH * F4];
-    __shared__ __align__(128) float bpl[2][2][CH * NR];      // [slot][hi, lo]: K-major core matrices
+    __shared__ __align__(128) float bpl[2][CH * NR];        // B hi / lo: K-major core matrices
     __shared__ __align__(16) float s_src[NC][4][CH];        // per consumer warp: -x, -y, -z, -u (SoA)
     __shared__ NearChunkInfo info[ST];
-    __shared__ __align__(8) uint64_t full[ST], aready[2], mma_done[2];
+    __shared__ __align__(8) uint64_t full[ST], mma_done;
     __shared__ uint32_t tmem_base;
     __shared__ uint32_t s_valid[kMaskWords];
-    __shared__ int s_fail;
+    __shared__ int s_fail, s_nch;
     const int tl = threadIdx.x, warp = tl >> 5, lane = tl & 31;
     const int64_t blk = cta_block(a);
     const KernelParams kp = block_params(a, blk, kp_all);
@@ -247,15 +250,14 @@ __global__ void __launch_bounds__(NearTcShape::THREADS, 4) near_tc_kernel(MvmArg
     const int t = rg.x + tl;
     const bool valid = warp < NC && t < rg.y;
     const uint32_t vword = __ballot_sync(0xffffffffu, valid);
+    const int64_t e0 = a.near_off[blk], e1 = a.near_off[blk + 1];
     if (tl == 0) {
 #pragma unroll
         for (int s = 0; s < ST; ++s) ptx::mbar_init(&full[s], 1);
-        ptx::mbar_init(&aready[0], NC);
-        ptx::mbar_init(&aready[1], NC);
-        ptx::mbar_init(&mma_done[0], 1);
-        ptx::mbar_init(&mma_done[1], 1);
+        ptx::mbar_init(&mma_done, 1);
         ptx::fence_mbar_init();
         s_fail = 0;
+        s_nch = 0;
     }
     if (warp < NC && lane == 0) s_valid[warp] = vword;
     if (warp == 0) {
@@ -265,71 +267,78 @@ __global__ void __launch_bounds__(NearTcShape::THREADS, 4) near_tc_kernel(MvmArg
     tc::fence_before_sync();
     __syncthreads();
     tc::fence_after_sync();
+    {   // the block's chunk count (both roles loop exactly this many rounds)
+        int cnt = 0;
+        for (int64_t e = e0 + tl; e < e1; e += S::THREADS) {
+            const int leaf = a.near_ent[e].x;
+            cnt += (a.nd_end[leaf] - a.nd_begin[leaf] + CH - 1) / CH;
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+        if (lane == 0 && cnt) atomicAdd(&s_nch, cnt);
+    }
+    __syncthreads();
+    const int nch = s_nch;
     const uint32_t tmem = tmem_base;
 
     if (warp == NC) {
         // ---------------------------------------------------------------- producer / issuer
-        if (lane == 0) {
-            NearChunks pit;
-            pit.start(a, a.near_off[blk], a.near_off[blk + 1]);
-            int issued = 0;   // chunks (and the end marker) handed to stages
-            int nchunks = -1; // known once the end marker is written
-            auto produce = [&]() {
-                const int slot = issued % ST;
-                NearChunkInfo& in = info[slot];
-                if (pit.done()) {
-                    in.n = 0;
-                    nchunks = issued;
-                    ptx::mbar_arrive(&full[slot]);
-                } else {
-                    const int n = pit.count();
-                    const int mask = a.near_ent[pit.e].y;
-                    in.n = n;
+        NearChunks pit;
+        int issued = 0;
+        auto produce = [&]() {  // lane 0
+            if (pit.done()) return;
+            const int slot = issued % ST;
+            NearChunkInfo& in = info[slot];
+            const int n = pit.count();
+            const int mask = a.near_ent[pit.e].y;
+            in.n = n;
 #pragma unroll
-                    for (int w = 0; w < kMaskWords; ++w)
-                        in.on[w] = (mask < 0 ? 0xFFFFFFFFu : __ldg(&a.masks[(int64_t)mask * kMaskWords + w])) & s_valid[w];
-                    const uint32_t bytes = (uint32_t)n * F4 * 16u;
-                    ptx::mbar_arrive_expect_tx(&full[slot], bytes);
-                    ptx::bulk_g2s(&stage[slot][0], a.rec + (int64_t)pit.cb * F4, bytes, &full[slot]);
-                    pit.next(a);
-                }
-                ++issued;
-            };
-            for (int s = 0; s < ST && nchunks < 0; ++s) produce();
-            int c = 0;
-            bool ok = true;
-            for (; nchunks < 0 || c < nchunks; ++c) {
-                const int slot = c % ST, ab = c & 1;
-                ok = ptx::mbar_wait_bounded(&aready[ab], (uint32_t)((c >> 1) & 1), kWaitCycles) && !s_fail;
-                if (!ok) break;
+            for (int w = 0; w < kMaskWords; ++w)
+                in.on[w] = (mask < 0 ? 0xFFFFFFFFu : __ldg(&a.masks[(int64_t)mask * kMaskWords + w])) & s_valid[w];
+            const uint32_t bytes = (uint32_t)n * F4 * 16u;
+            ptx::mbar_arrive_expect_tx(&full[slot], bytes);
+            ptx::bulk_g2s(&stage[slot][0], a.rec + (int64_t)pit.cb * F4, bytes, &full[slot]);
+            pit.next(a);
+            ++issued;
+        };
+        if (lane == 0) {
+            pit.start(a, e0, e1);
+            for (int s = 0; s < ST; ++s) produce();
+        }
+        int waited_mma = 0;
+        for (int c = 0; c < nch; ++c) {
+            const int slot = c % ST;
+            ptx::named_sync(kBarReady, kBarThreads);
+            if (lane == 0 && !s_fail) {
                 tc::fence_after_sync();
                 const NearChunkInfo in = info[slot];
                 const uint32_t off[kMaskWords] = {~in.on[0], ~in.on[1], ~in.on[2], ~in.on[3]};
                 const int nks = (in.n + 7) / 8;
                 for (int ks = 0; ks < nks; ++ks) {
-                    const uint64_t bh = tc::smem_desc(&bpl[ab][0][ks * 256], 512, 128);
-                    const uint64_t bl = tc::smem_desc(&bpl[ab][1][ks * 256], 512, 128);
-                    const uint32_t ahi = tmem + S::COL_A + ab * S::SLOT_COLS + ks * 8, alo = ahi + CH;
+                    const uint64_t bh = tc::smem_desc(&bpl[0][ks * 256], 512, 128);
+                    const uint64_t bl = tc::smem_desc(&bpl[1][ks * 256], 512, 128);
+                    const uint32_t ahi = tmem + S::COL_AHI + ks * 8, alo = tmem + S::COL_ALO + ks * 8;
                     tc::mma_tf32_ts_masked(tmem, ahi, bh, IDESC, off);
                     tc::mma_tf32_ts_masked(tmem, ahi, bl, IDESC, off);
                     tc::mma_tf32_ts_masked(tmem, alo, bh, IDESC, off);
                 }
-                tc::commit(&mma_done[ab]);
-                // every consumer has read stage `slot`: refill it ST chunks ahead
-                if (nchunks < 0) {
-                    ptx::fence_proxy_async_smem();
-                    produce();
-                }
+                tc::commit(&mma_done);
+                // every consumer has read stage `slot`: refill it ST chunks ahead while the MMAs run
+                ptx::fence_proxy_async_smem();
+                produce();
+                if (ptx::mbar_wait_bounded(&mma_done, (uint32_t)(c & 1), kWaitCycles)) waited_mma = c + 1;
+                else s_fail = 1;
+                tc::fence_before_sync();
             }
-            if (!ok) {
-                s_fail = 1;
-                atomicExch(a.err, 1);
-                // let the copies and MMAs in flight finish before the CTA leaves (bounded)
-                for (int j = c; j < issued; ++j)
-                    ptx::mbar_wait_bounded(&full[j % ST], (uint32_t)((j / ST) & 1), kWaitCycles);
-                if (c >= 1) ptx::mbar_wait_bounded(&mma_done[(c - 1) & 1], (uint32_t)(((c - 1) >> 1) & 1), kWaitCycles);
-                if (c >= 2) ptx::mbar_wait_bounded(&mma_done[c & 1], (uint32_t)(((c - 2) >> 1) & 1), kWaitCycles);
-            }
+            __syncwarp();
+            ptx::named_arrive(kBarMma, kBarThreads);
+        }
+        if (lane == 0 && s_fail) {
+            atomicExch(a.err, 1);
+            // the last copy of each stage may still be in flight; then the last MMAs
+            for (int j = issued > ST ? issued - ST : 0; j < issued; ++j)
+                ptx::mbar_wait_bounded(&full[j % ST], (uint32_t)((j / ST) & 1), kWaitCycles);
+            if (waited_mma < nch) ptx::mbar_wait_bounded(&mma_done, (uint32_t)(waited_mma & 1), kWaitCycles);
         }
     } else {
         // ---------------------------------------------------------------- consumers
@@ -347,95 +356,86 @@ __global__ void __launch_bounds__(NearTcShape::THREADS, 4) near_tc_kernel(MvmArg
         float acc[NR];
 #pragma unroll
         for (int r = 0; r < NR; ++r) acc[r] = 0.f;
-        bool ok = true;
         bool dirty = false;  // this warp's accumulator rows hold products not yet added to acc
-        int c = 0;
-        for (;; ++c) {
-            const int slot = c % ST, ab = c & 1;
-            ok = ptx::mbar_wait_bounded(&full[slot], (uint32_t)((c / ST) & 1), kWaitCycles);
-            if (!__all_sync(0xffffffffu, ok) || s_fail) { ok = false; break; }
-            const int n = info[slot].n;
-            if (n == 0) break;
-            const uint32_t mword = info[slot].on[warp];
-            // MMAs of chunk c-2 done: A slot and B planes ab are free
-            if (c >= 2) {
-                ok = ptx::mbar_wait_bounded(&mma_done[ab], (uint32_t)(((c - 2) >> 1) & 1), kWaitCycles);
-                if (!__all_sync(0xffffffffu, ok)) break;
-            }
-            bool stored = false;
-            if (c > 0 && c % S::FLUSH == 0) {
-                // every FLUSH chunks: wait for chunk c-1 too, then accumulator rows -> registers
-                ok = ptx::mbar_wait_bounded(&mma_done[(c - 1) & 1], (uint32_t)(((c - 1) >> 1) & 1), kWaitCycles);
-                if (!__all_sync(0xffffffffu, ok)) break;
-                if (dirty) {
-                    tc::fence_after_sync();
-                    add_partial(tmem + lane_base, acc);
-                    tc::st32_zero(tmem + lane_base);
-                    dirty = false;
-                    stored = true;
-                }
-            }
+        for (int c = 0; c < nch; ++c) {
+            const int slot = c % ST;
+            const bool got = ptx::mbar_wait_bounded(&full[slot], (uint32_t)((c / ST) & 1), kWaitCycles);
+            if (!__all_sync(0xffffffffu, got)) s_fail = 1;
+            if (c >= 1) ptx::named_sync(kBarMma, kBarThreads);  // the MMAs of chunk c-1 are done
             tc::fence_after_sync();
+            const bool work = !s_fail;
+            const int n = info[slot].n;
+            const uint32_t mword = work ? info[slot].on[warp] : 0u;
+            bool stored = false;
+            if (work && c % S::FLUSH == 0 && dirty) {
+                add_partial(tmem + lane_base, acc);
+                tc::st32_zero(tmem + lane_base);
+                dirty = false;
+                stored = true;
+            }
             const float4* sb = &stage[slot][0];
-            {   // B operand: consumer warp w rearranges sources 4w..4w+3; lane = right-hand side.
-                // Element (n, k) sits at float (k/4)*128 + n*4 + k%4.
-                uint32_t h[4], l[4];
+            if (work) {
+                // B operand: consumer warp w rearranges sources 4w..4w+3 and 16+4w..16+4w+3;
+                // lane = right-hand side.  Element (n, k) sits at float (k/4)*128 + n*4 + k%4.
 #pragma unroll
-                for (int i = 0; i < 4; ++i) {
-                    const int k = 4 * warp + i;
-                    const float v = k < n ? reinterpret_cast<const float*>(sb + k * F4)[4 + lane] : 0.f;
-                    split_tf32(v, h[i], l[i]);
+                for (int kg = warp; kg < CH / 4; kg += NC) {
+                    uint32_t h[4], l[4];
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+                        const int k = 4 * kg + i;
+                        const float v = k < n ? reinterpret_cast<const float*>(sb + k * F4)[4 + lane] : 0.f;
+                        split_tf32(v, h[i], l[i]);
+                    }
+                    *reinterpret_cast<uint4*>(&bpl[0][kg * 128 + lane * 4]) = make_uint4(h[0], h[1], h[2], h[3]);
+                    *reinterpret_cast<uint4*>(&bpl[1][kg * 128 + lane * 4]) = make_uint4(l[0], l[1], l[2], l[3]);
                 }
-                *reinterpret_cast<uint4*>(&bpl[ab][0][warp * 128 + lane * 4]) = make_uint4(h[0], h[1], h[2], h[3]);
-                *reinterpret_cast<uint4*>(&bpl[ab][1][warp * 128 + lane * 4]) = make_uint4(l[0], l[1], l[2], l[3]);
             }
             if (mword != 0u) {
                 {   // this warp's SoA copy of the chunk's negated coordinates (zeros past the
                     // chunk's end: those columns meet zero weights in B)
                     const float4 r = lane < n ? sb[lane * F4] : make_float4(0.f, 0.f, 0.f, 0.f);
-                    if (lane < CH) {
-                        s_src[warp][0][lane] = -r.x;
-                        s_src[warp][1][lane] = -r.y;
-                        s_src[warp][2][lane] = -r.z;
-                        if (D == 4) s_src[warp][3][lane] = -r.w;
-                    }
+                    s_src[warp][0][lane] = -r.x;
+                    s_src[warp][1][lane] = -r.y;
+                    s_src[warp][2][lane] = -r.z;
+                    if (D == 4) s_src[warp][3][lane] = -r.w;
                 }
                 __syncwarp();
-                uint32_t khi[CH], klo[CH];
 #pragma unroll
-                for (int j4 = 0; j4 < CH; j4 += 4) {
-                    if (j4 < 8 || n > 8) {  // the second MMA K-step only when the chunk has one
-                        const float4 X = *reinterpret_cast<const float4*>(&s_src[warp][0][j4]);
-                        const float4 Y = *reinterpret_cast<const float4*>(&s_src[warp][1][j4]);
-                        const float4 Z = *reinterpret_cast<const float4*>(&s_src[warp][2][j4]);
-                        float2 q[2];
+                for (int h0 = 0; h0 < CH; h0 += 16) {
+                    if (h0 < n) {  // the MMA reads only ceil(n/8) K-steps
+                        uint32_t khi[16], klo[16];
 #pragma unroll
-                        for (int hh = 0; hh < 2; ++hh) {
-                            const float2 dx = __fadd2_rn(tx2[0], hh ? make_float2(X.z, X.w) : make_float2(X.x, X.y));
-                            const float2 dy = __fadd2_rn(tx2[1], hh ? make_float2(Y.z, Y.w) : make_float2(Y.x, Y.y));
-                            const float2 dz = __fadd2_rn(tx2[2], hh ? make_float2(Z.z, Z.w) : make_float2(Z.x, Z.y));
-                            q[hh] = __ffma2_rn(dx, dx, __ffma2_rn(dy, dy, __fmul2_rn(dz, dz)));
+                        for (int j4 = 0; j4 < 16; j4 += 4) {
+                            const int j = h0 + j4;
+                            const float4 X = *reinterpret_cast<const float4*>(&s_src[warp][0][j]);
+                            const float4 Y = *reinterpret_cast<const float4*>(&s_src[warp][1][j]);
+                            const float4 Z = *reinterpret_cast<const float4*>(&s_src[warp][2][j]);
+                            float2 q[2];
+#pragma unroll
+                            for (int hh = 0; hh < 2; ++hh) {
+                                const float2 dx = __fadd2_rn(tx2[0], hh ? make_float2(X.z, X.w) : make_float2(X.x, X.y));
+                                const float2 dy = __fadd2_rn(tx2[1], hh ? make_float2(Y.z, Y.w) : make_float2(Y.x, Y.y));
+                                const float2 dz = __fadd2_rn(tx2[2], hh ? make_float2(Z.z, Z.w) : make_float2(Z.x, Z.y));
+                                q[hh] = __ffma2_rn(dx, dx, __ffma2_rn(dy, dy, __fmul2_rn(dz, dz)));
+                            }
+                            if (D == 4) {
+                                const float4 W = *reinterpret_cast<const float4*>(&s_src[warp][3][j]);
+                                const float2 dw0 = __fadd2_rn(tx2[3], make_float2(W.x, W.y));
+                                const float2 dw1 = __fadd2_rn(tx2[3], make_float2(W.z, W.w));
+                                q[0] = __ffma2_rn(dw0, dw0, q[0]);
+                                q[1] = __ffma2_rn(dw1, dw1, q[1]);
+                            }
+#pragma unroll
+                            for (int hh = 0; hh < 2; ++hh) {
+                                const float2 kv = kval2<KIND>(q[hh], kp);
+                                split2(kv, khi[j4 + 2 * hh], khi[j4 + 2 * hh + 1], klo[j4 + 2 * hh],
+                                       klo[j4 + 2 * hh + 1]);
+                            }
                         }
-                        if (D == 4) {
-                            const float4 W = *reinterpret_cast<const float4*>(&s_src[warp][3][j4]);
-                            const float2 dw0 = __fadd2_rn(tx2[3], make_float2(W.x, W.y));
-                            const float2 dw1 = __fadd2_rn(tx2[3], make_float2(W.z, W.w));
-                            q[0] = __ffma2_rn(dw0, dw0, q[0]);
-                            q[1] = __ffma2_rn(dw1, dw1, q[1]);
-                        }
-#pragma unroll
-                        for (int hh = 0; hh < 2; ++hh) {
-                            const float2 kv = kval2<KIND>(q[hh], kp);
-                            split2(kv, khi[j4 + 2 * hh], khi[j4 + 2 * hh + 1], klo[j4 + 2 * hh], klo[j4 + 2 * hh + 1]);
-                        }
-                    } else {
-#pragma unroll
-                        for (int i = 0; i < 4; ++i) khi[j4 + i] = klo[j4 + i] = 0u;
+                        tc::st16(tmem + lane_base + S::COL_AHI + h0, khi);
+                        tc::st16(tmem + lane_base + S::COL_ALO + h0, klo);
                     }
                 }
-                const uint32_t acol = tmem + lane_base + S::COL_A + ab * S::SLOT_COLS;
-                tc::st16(acol, khi);
-                tc::st16(acol + CH, klo);
                 dirty = true;
                 stored = true;
             }
@@ -444,24 +444,18 @@ __global__ void __launch_bounds__(NearTcShape::THREADS, 4) near_tc_kernel(MvmArg
             ptx::fence_proxy_async_smem();
             tc::fence_before_sync();
             __syncwarp();
-            if (lane == 0) ptx::mbar_arrive(&aready[ab]);
+            ptx::named_arrive(kBarReady, kBarThreads);
         }
-        // chunks 0..c-1 were handed to the issuer; wait for the last two, then add what the
-        // accumulator rows still hold
-        if (ok && c >= 1) ok = ptx::mbar_wait_bounded(&mma_done[(c - 1) & 1], (uint32_t)(((c - 1) >> 1) & 1), kWaitCycles);
-        if (ok && c >= 2) ok = ptx::mbar_wait_bounded(&mma_done[c & 1], (uint32_t)(((c - 2) >> 1) & 1), kWaitCycles);
-        ok = __all_sync(0xffffffffu, ok);
-        if (!ok) {
-            s_fail = 1;
-            if (lane == 0) atomicExch(a.err, 1);
-        }
+        if (nch >= 1) ptx::named_sync(kBarMma, kBarThreads);  // the MMAs of the last chunk are done
         tc::fence_after_sync();
+        const bool ok = !s_fail;
         if (ok && dirty) add_partial(tmem + lane_base, acc);
         __syncwarp();
         if (ok && valid)
 #pragma unroll
             for (int r = 0; r < NR; ++r)
                 if (r < a.nr) acc_store(a, r, t, acc[r] * kp.scale);
+        if (!ok && tl == 0) atomicExch(a.err, 1);
     }
     tc::fence_before_sync();
     __syncthreads();

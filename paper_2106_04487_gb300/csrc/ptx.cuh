@@ -56,6 +56,16 @@ __device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t by
                  : "memory");
 }
 
+// Named CTA barriers (hardware barrier resources 1..15; 0 is __syncthreads): a warp waiting in
+// bar.sync is descheduled and issues nothing.  `threads` counts every thread that arrives or
+// syncs on the barrier in one round (a multiple of 32; whole warps take part).
+__device__ __forceinline__ void named_sync(uint32_t id, uint32_t threads) {
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(threads) : "memory");
+}
+__device__ __forceinline__ void named_arrive(uint32_t id, uint32_t threads) {
+    asm volatile("bar.arrive %0, %1;" ::"r"(id), "r"(threads) : "memory");
+}
+
 // Plain arrive (release at CTA scope) on an mbarrier.
 __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
@@ -84,9 +94,9 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
     return ok != 0;
 }
 
-// try_wait that suspends the thread (it issues nothing) until the phase completes or about
-// hint_ns nanoseconds pass, whichever comes first.
-__device__ __forceinline__ bool mbar_try_wait_sleep(uint64_t* bar, uint32_t parity, uint32_t hint_ns) {
+// try_wait with a suspend-time hint: the hardware may park the thread until the phase completes
+// or the hint (nanoseconds) runs out.
+__device__ __forceinline__ bool mbar_try_wait_hint(uint64_t* bar, uint32_t parity, uint32_t hint_ns) {
     uint32_t ok;
     asm volatile(
         "{\n"
@@ -101,16 +111,25 @@ __device__ __forceinline__ bool mbar_try_wait_sleep(uint64_t* bar, uint32_t pari
 }
 
 // Wait for phase `parity` of `bar` for at most ~max_cycles SM clocks.  Returns false when the
-// wait ran out (the caller records an error and stops instead of hanging the GPU).  The retries
-// sleep in the barrier instead of spinning, so a waiting warp takes no issue slots from the
-// warps that compute.
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, long long max_cycles) {
+// wait ran out (the caller records an error and stops instead of hanging the GPU).
+// max_sleep_ns > 0: between retries the thread sleeps (nanosleep, doubling up to the cap), for
+// waits that are not on the critical path.  max_sleep_ns == 0: retries use try_wait's own
+// suspend hint, the lowest-latency wake-up, for waits that gate the next step of a pipeline.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, long long max_cycles,
+                                                  uint32_t max_sleep_ns = 0) {
     if (mbar_try_wait(bar, parity)) return true;
     const long long t0 = clock64();
-    while (!mbar_try_wait_sleep(bar, parity, 20000u)) {
+    uint32_t ns = 32;
+    for (;;) {
+        if (max_sleep_ns == 0) {
+            if (mbar_try_wait_hint(bar, parity, 20000u)) return true;
+        } else {
+            __nanosleep(ns);
+            if (ns < max_sleep_ns) ns <<= 1;
+            if (mbar_try_wait(bar, parity)) return true;
+        }
         if (clock64() - t0 > max_cycles) return false;
     }
-    return true;
 }
 
 }  // namespace ptx
