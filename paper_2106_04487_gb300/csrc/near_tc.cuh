@@ -230,7 +230,7 @@ struct NearChunkInfo {
 // threads up front) whatever happens: a bounded mbarrier wait that runs out sets s_fail, which
 // only skips work, and the producer drains what it issued before the CTA frees tensor memory.
 template <int D, int KIND>
-__global__ void __launch_bounds__(NearTcShape::THREADS, 4) near_tc_kernel(MvmArgs a, KernelParams kp_all) {
+__global__ void __launch_bounds__(NearTcShape::THREADS, 3) near_tc_kernel(MvmArgs a, KernelParams kp_all) {
     using S = NearTcShape;
     constexpr int CH = S::CH, ST = S::ST, F4 = S::F4, NR = S::NR, NC = S::CONSUMERS;
     constexpr uint32_t IDESC = tc::instr_desc(2u, 128u, (uint32_t)NR);
@@ -283,28 +283,66 @@ __global__ void __launch_bounds__(NearTcShape::THREADS, 4) near_tc_kernel(MvmArg
 
     if (warp == NC) {
         // ---------------------------------------------------------------- producer / issuer
-        NearChunks pit;
-        int issued = 0;
-        auto produce = [&]() {  // lane 0
-            if (pit.done()) return;
-            const int slot = issued % ST;
-            NearChunkInfo& in = info[slot];
-            const int n = pit.count();
-            const int mask = a.near_ent[pit.e].y;
-            in.n = n;
+        // The whole warp walks the chunk sequence in step: every lane holds the leaf range and
+        // row mask of one entry of a 32-entry window (loaded together, one memory latency per 32
+        // entries), lane 0 issues the copies.
+        int64_t wbase = e0;
+        int wbeg = 0, wend = 0;
+        uint32_t wm[kMaskWords] = {0u, 0u, 0u, 0u};
+        auto load_window = [&]() {
+            const int64_t e = wbase + lane;
+            wbeg = wend = 0;
+            if (e < e1) {
+                const int2 ent = a.near_ent[e];
+                wbeg = a.nd_begin[ent.x];
+                wend = a.nd_end[ent.x];
 #pragma unroll
-            for (int w = 0; w < kMaskWords; ++w)
-                in.on[w] = (mask < 0 ? 0xFFFFFFFFu : __ldg(&a.masks[(int64_t)mask * kMaskWords + w])) & s_valid[w];
-            const uint32_t bytes = (uint32_t)n * F4 * 16u;
-            ptx::mbar_arrive_expect_tx(&full[slot], bytes);
-            ptx::bulk_g2s(&stage[slot][0], a.rec + (int64_t)pit.cb * F4, bytes, &full[slot]);
-            pit.next(a);
-            ++issued;
+                for (int w = 0; w < kMaskWords; ++w)
+                    wm[w] = (ent.y < 0 ? 0xFFFFFFFFu : __ldg(&a.masks[(int64_t)ent.y * kMaskWords + w])) & s_valid[w];
+            }
         };
-        if (lane == 0) {
-            pit.start(a, e0, e1);
-            for (int s = 0; s < ST; ++s) produce();
+        int ei = 0, cb = 0, cend = 0, issued = 0;
+        bool pdone = wbase >= e1;
+        auto settle = [&]() {  // warp-uniform: advance to the next entry with sources left
+            while (!pdone && cb >= cend) {
+                if (++ei == 32) {
+                    wbase += 32;
+                    ei = 0;
+                    if (wbase >= e1) { pdone = true; break; }
+                    load_window();
+                }
+                if (wbase + ei >= e1) { pdone = true; break; }
+                cb = __shfl_sync(0xffffffffu, wbeg, ei);
+                cend = __shfl_sync(0xffffffffu, wend, ei);
+            }
+        };
+        auto produce = [&]() {  // warp-collective
+            if (pdone) return;
+            const int slot = issued % ST;
+            const int n = min(CH, cend - cb);
+            uint32_t on[kMaskWords];
+#pragma unroll
+            for (int w = 0; w < kMaskWords; ++w) on[w] = __shfl_sync(0xffffffffu, wm[w], ei);
+            if (lane == 0) {
+                NearChunkInfo& in = info[slot];
+                in.n = n;
+#pragma unroll
+                for (int w = 0; w < kMaskWords; ++w) in.on[w] = on[w];
+                const uint32_t bytes = (uint32_t)n * F4 * 16u;
+                ptx::mbar_arrive_expect_tx(&full[slot], bytes);
+                ptx::bulk_g2s(&stage[slot][0], a.rec + (int64_t)cb * F4, bytes, &full[slot]);
+            }
+            ++issued;
+            cb += CH;
+            settle();
+        };
+        if (!pdone) {
+            load_window();
+            cb = __shfl_sync(0xffffffffu, wbeg, 0);
+            cend = __shfl_sync(0xffffffffu, wend, 0);
+            settle();
         }
+        for (int s = 0; s < ST; ++s) produce();
         int waited_mma = 0;
         for (int c = 0; c < nch; ++c) {
             const int slot = c % ST;
@@ -323,15 +361,18 @@ __global__ void __launch_bounds__(NearTcShape::THREADS, 4) near_tc_kernel(MvmArg
                     tc::mma_tf32_ts_masked(tmem, alo, bh, IDESC, off);
                 }
                 tc::commit(&mma_done);
-                // every consumer has read stage `slot`: refill it ST chunks ahead while the MMAs run
-                ptx::fence_proxy_async_smem();
-                produce();
                 if (ptx::mbar_wait_bounded(&mma_done, (uint32_t)(c & 1), kWaitCycles)) waited_mma = c + 1;
                 else s_fail = 1;
                 tc::fence_before_sync();
             }
             __syncwarp();
             ptx::named_arrive(kBarMma, kBarThreads);
+            // after releasing the consumers: every consumer has read stage `slot`, refill it ST
+            // chunks ahead (the list lookups for the chunk after it no longer delay the release)
+            if (__all_sync(0xffffffffu, !s_fail)) {  // warp-uniform: produce() shuffles
+                if (lane == 0) ptx::fence_proxy_async_smem();
+                produce();
+            }
         }
         if (lane == 0 && s_fail) {
             atomicExch(a.err, 1);
@@ -361,11 +402,55 @@ __global__ void __launch_bounds__(NearTcShape::THREADS, 4) near_tc_kernel(MvmArg
             const int slot = c % ST;
             const bool got = ptx::mbar_wait_bounded(&full[slot], (uint32_t)((c / ST) & 1), kWaitCycles);
             if (!__all_sync(0xffffffffu, got)) s_fail = 1;
+            const int n = info[slot].n;
+            const uint32_t mword = s_fail ? 0u : info[slot].on[warp];
+            const float4* sb = &stage[slot][0];
+            // this row's kernel values against the chunk, before waiting for the MMAs of chunk
+            // c-1: the wait then overlaps useful work (registers; rows of targets outside the
+            // mask are computed anyway when their warp is busy, and left out by the MMA)
+            uint32_t khi[CH], klo[CH];
+            if (mword != 0u) {
+                {   // this warp's SoA copy of the chunk's negated coordinates (zeros past the
+                    // chunk's end: those columns meet zero weights in B)
+                    const float4 r = lane < n ? sb[lane * F4] : make_float4(0.f, 0.f, 0.f, 0.f);
+                    s_src[warp][0][lane] = -r.x;
+                    s_src[warp][1][lane] = -r.y;
+                    s_src[warp][2][lane] = -r.z;
+                    if (D == 4) s_src[warp][3][lane] = -r.w;
+                }
+                __syncwarp();
+#pragma unroll
+                for (int j4 = 0; j4 < CH; j4 += 4) {
+                    if (j4 < 16 || n > 16) {  // the MMA reads only ceil(n/8) K-steps
+                        const float4 X = *reinterpret_cast<const float4*>(&s_src[warp][0][j4]);
+                        const float4 Y = *reinterpret_cast<const float4*>(&s_src[warp][1][j4]);
+                        const float4 Z = *reinterpret_cast<const float4*>(&s_src[warp][2][j4]);
+                        float2 q[2];
+#pragma unroll
+                        for (int hh = 0; hh < 2; ++hh) {
+                            const float2 dx = __fadd2_rn(tx2[0], hh ? make_float2(X.z, X.w) : make_float2(X.x, X.y));
+                            const float2 dy = __fadd2_rn(tx2[1], hh ? make_float2(Y.z, Y.w) : make_float2(Y.x, Y.y));
+                            const float2 dz = __fadd2_rn(tx2[2], hh ? make_float2(Z.z, Z.w) : make_float2(Z.x, Z.y));
+                            q[hh] = __ffma2_rn(dx, dx, __ffma2_rn(dy, dy, __fmul2_rn(dz, dz)));
+                        }
+                        if (D == 4) {
+                            const float4 W = *reinterpret_cast<const float4*>(&s_src[warp][3][j4]);
+                            const float2 dw0 = __fadd2_rn(tx2[3], make_float2(W.x, W.y));
+                            const float2 dw1 = __fadd2_rn(tx2[3], make_float2(W.z, W.w));
+                            q[0] = __ffma2_rn(dw0, dw0, q[0]);
+                            q[1] = __ffma2_rn(dw1, dw1, q[1]);
+                        }
+#pragma unroll
+                        for (int hh = 0; hh < 2; ++hh) {
+                            const float2 kv = kval2<KIND>(q[hh], kp);
+                            split2(kv, khi[j4 + 2 * hh], khi[j4 + 2 * hh + 1], klo[j4 + 2 * hh], klo[j4 + 2 * hh + 1]);
+                        }
+                    }
+                }
+            }
             if (c >= 1) ptx::named_sync(kBarMma, kBarThreads);  // the MMAs of chunk c-1 are done
             tc::fence_after_sync();
             const bool work = !s_fail;
-            const int n = info[slot].n;
-            const uint32_t mword = work ? info[slot].on[warp] : 0u;
             bool stored = false;
             if (work && c % S::FLUSH == 0 && dirty) {
                 add_partial(tmem + lane_base, acc);
@@ -373,7 +458,6 @@ __global__ void __launch_bounds__(NearTcShape::THREADS, 4) near_tc_kernel(MvmArg
                 dirty = false;
                 stored = true;
             }
-            const float4* sb = &stage[slot][0];
             if (work) {
                 // B operand: consumer warp w rearranges sources 4w..4w+3 and 16+4w..16+4w+3;
                 // lane = right-hand side.  Element (n, k) sits at float (k/4)*128 + n*4 + k%4.
@@ -390,51 +474,12 @@ __global__ void __launch_bounds__(NearTcShape::THREADS, 4) near_tc_kernel(MvmArg
                     *reinterpret_cast<uint4*>(&bpl[1][kg * 128 + lane * 4]) = make_uint4(l[0], l[1], l[2], l[3]);
                 }
             }
-            if (mword != 0u) {
-                {   // this warp's SoA copy of the chunk's negated coordinates (zeros past the
-                    // chunk's end: those columns meet zero weights in B)
-                    const float4 r = lane < n ? sb[lane * F4] : make_float4(0.f, 0.f, 0.f, 0.f);
-                    s_src[warp][0][lane] = -r.x;
-                    s_src[warp][1][lane] = -r.y;
-                    s_src[warp][2][lane] = -r.z;
-                    if (D == 4) s_src[warp][3][lane] = -r.w;
-                }
-                __syncwarp();
-#pragma unroll
-                for (int h0 = 0; h0 < CH; h0 += 16) {
-                    if (h0 < n) {  // the MMA reads only ceil(n/8) K-steps
-                        uint32_t khi[16], klo[16];
-#pragma unroll
-                        for (int j4 = 0; j4 < 16; j4 += 4) {
-                            const int j = h0 + j4;
-                            const float4 X = *reinterpret_cast<const float4*>(&s_src[warp][0][j]);
-                            const float4 Y = *reinterpret_cast<const float4*>(&s_src[warp][1][j]);
-                            const float4 Z = *reinterpret_cast<const float4*>(&s_src[warp][2][j]);
-                            float2 q[2];
-#pragma unroll
-                            for (int hh = 0; hh < 2; ++hh) {
-                                const float2 dx = __fadd2_rn(tx2[0], hh ? make_float2(X.z, X.w) : make_float2(X.x, X.y));
-                                const float2 dy = __fadd2_rn(tx2[1], hh ? make_float2(Y.z, Y.w) : make_float2(Y.x, Y.y));
-                                const float2 dz = __fadd2_rn(tx2[2], hh ? make_float2(Z.z, Z.w) : make_float2(Z.x, Z.y));
-                                q[hh] = __ffma2_rn(dx, dx, __ffma2_rn(dy, dy, __fmul2_rn(dz, dz)));
-                            }
-                            if (D == 4) {
-                                const float4 W = *reinterpret_cast<const float4*>(&s_src[warp][3][j]);
-                                const float2 dw0 = __fadd2_rn(tx2[3], make_float2(W.x, W.y));
-                                const float2 dw1 = __fadd2_rn(tx2[3], make_float2(W.z, W.w));
-                                q[0] = __ffma2_rn(dw0, dw0, q[0]);
-                                q[1] = __ffma2_rn(dw1, dw1, q[1]);
-                            }
-#pragma unroll
-                            for (int hh = 0; hh < 2; ++hh) {
-                                const float2 kv = kval2<KIND>(q[hh], kp);
-                                split2(kv, khi[j4 + 2 * hh], khi[j4 + 2 * hh + 1], klo[j4 + 2 * hh],
-                                       klo[j4 + 2 * hh + 1]);
-                            }
-                        }
-                        tc::st16(tmem + lane_base + S::COL_AHI + h0, khi);
-                        tc::st16(tmem + lane_base + S::COL_ALO + h0, klo);
-                    }
+            if (work && mword != 0u) {  // A operand: the row into tensor memory
+                tc::st16(tmem + lane_base + S::COL_AHI, khi);
+                tc::st16(tmem + lane_base + S::COL_ALO, klo);
+                if (n > 16) {
+                    tc::st16(tmem + lane_base + S::COL_AHI + 16, khi + 16);
+                    tc::st16(tmem + lane_base + S::COL_ALO + 16, klo + 16);
                 }
                 dirty = true;
                 stored = true;
