@@ -373,28 +373,59 @@ __global__ void __launch_bounds__(160, P <= 7 ? 3 : 2) far_tc2_kernel(MvmArgs a,
     const uint32_t tmem = tmem_base;
 
     if (warp == 4) {
-        if (lane == 0) {
-            int issued = 0;
-            auto produce = [&]() {
-                const int slot = issued % ST;
-                const int2 ent = a.far_ent[e0 + issued];
-                FarTc2Info& in = info[slot];
-                in.c = a.nd_cf[ent.x];
-                in.s = a.nd_scale[ent.x];
+        // The whole warp runs the loop in step: every lane holds the node centre, scale and row
+        // mask of one entry of a 32-entry window (loaded together, one memory latency per 32
+        // entries); lane 0 issues the copies and the MMAs.
+        int wb = 0, wnode = 0;
+        float4 wc = make_float4(0.f, 0.f, 0.f, 0.f);
+        float ws = 0.f;
+        uint32_t wm[kMaskWords] = {0u, 0u, 0u, 0u};
+        auto load_window = [&]() {
+            const int e = wb + lane;
+            if (e < ne) {
+                const int2 ent = a.far_ent[e0 + e];
+                wnode = ent.x;
+                wc = a.nd_cf[ent.x];
+                ws = a.nd_scale[ent.x];
 #pragma unroll
                 for (int w = 0; w < kMaskWords; ++w)
-                    in.on[w] = (ent.y < 0 ? 0xFFFFFFFFu : __ldg(&a.masks[(int64_t)ent.y * kMaskWords + w])) & s_valid[w];
+                    wm[w] = (ent.y < 0 ? 0xFFFFFFFFu : __ldg(&a.masks[(int64_t)ent.y * kMaskWords + w])) & s_valid[w];
+            }
+        };
+        int issued = 0;
+        auto produce = [&]() {  // warp-collective
+            if (issued >= wb + 32) {
+                wb += 32;
+                load_window();
+            }
+            const int src = issued - wb, slot = issued % ST;
+            const int node = __shfl_sync(0xffffffffu, wnode, src);
+            const float cx = __shfl_sync(0xffffffffu, wc.x, src), cy = __shfl_sync(0xffffffffu, wc.y, src);
+            const float cz = __shfl_sync(0xffffffffu, wc.z, src), cw = __shfl_sync(0xffffffffu, wc.w, src);
+            const float sc = __shfl_sync(0xffffffffu, ws, src);
+            uint32_t on[kMaskWords];
+#pragma unroll
+            for (int w = 0; w < kMaskWords; ++w) on[w] = __shfl_sync(0xffffffffu, wm[w], src);
+            if (lane == 0) {
+                FarTc2Info& in = info[slot];
+                in.c = make_float4(cx, cy, cz, cw);
+                in.s = sc;
+#pragma unroll
+                for (int w = 0; w < kMaskWords; ++w) in.on[w] = on[w];
                 ptx::mbar_arrive_expect_tx(&full[slot], (uint32_t)BB);
-                ptx::bulk_g2s(Bbuf + slot * BB, image + (int64_t)ent.x * BB, (uint32_t)BB, &full[slot]);
-                ++issued;
-            };
-            while (issued < ST && issued < ne) produce();
-            bool ok = true;
-            int i = 0;
-            for (; i < ne; ++i) {
-                const int slot = i % ST;
-                ok = ptx::mbar_wait_bounded(&aready, (uint32_t)(i & 1), kWaitCycles) && !s_fail;
-                if (!ok) break;
+                ptx::bulk_g2s(Bbuf + slot * BB, image + (int64_t)node * BB, (uint32_t)BB, &full[slot]);
+            }
+            ++issued;
+        };
+        if (ne > 0) load_window();
+        while (issued < ST && issued < ne) produce();
+        bool ok = true;
+        int i = 0;
+        for (; i < ne; ++i) {
+            const int slot = i % ST;
+            ok = ptx::mbar_wait_bounded(&aready, (uint32_t)(i & 1), kWaitCycles) && !s_fail;
+            if (!__all_sync(0xffffffffu, ok)) { ok = false; break; }
+            if (lane == 0) {
                 tc::fence_after_sync();
                 uint32_t off[kMaskWords];
 #pragma unroll
@@ -412,21 +443,22 @@ __global__ void __launch_bounds__(160, P <= 7 ? 3 : 2) far_tc2_kernel(MvmArgs a,
                     }
                 }
                 tc::commit(&mma_done);
-                // the consumers saw the MMAs of entry i-1 complete before they arrived on aready
-                // for entry i: its stage is free for entry i-1+ST
-                if (i >= 1 && issued < ne) {
-                    ptx::fence_proxy_async_smem();
-                    produce();
-                }
             }
-            if (!ok) {
-                s_fail = 1;
-                atomicExch(a.err, 1);
-                // the last copy of each stage may still be in flight; then the last MMAs
-                for (int j = issued > ST ? issued - ST : 0; j < issued; ++j)
-                    ptx::mbar_wait_bounded(&full[j % ST], (uint32_t)((j / ST) & 1), kWaitCycles);
-                if (i >= 1) ptx::mbar_wait_bounded(&mma_done, (uint32_t)((i - 1) & 1), kWaitCycles);
+            __syncwarp();
+            // the consumers saw the MMAs of entry i-1 complete before they arrived on aready for
+            // entry i: its stage is free for entry i-1+ST
+            if (i >= 1 && issued < ne) {
+                if (lane == 0) ptx::fence_proxy_async_smem();
+                produce();
             }
+        }
+        if (!ok && lane == 0) {
+            s_fail = 1;
+            atomicExch(a.err, 1);
+            // the last copy of each stage may still be in flight; then the last MMAs
+            for (int j = issued > ST ? issued - ST : 0; j < issued; ++j)
+                ptx::mbar_wait_bounded(&full[j % ST], (uint32_t)((j / ST) & 1), kWaitCycles);
+            if (i >= 1) ptx::mbar_wait_bounded(&mma_done, (uint32_t)((i - 1) & 1), kWaitCycles);
         }
     } else {
         const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
@@ -448,11 +480,21 @@ __global__ void __launch_bounds__(160, P <= 7 ? 3 : 2) far_tc2_kernel(MvmArgs a,
         for (; i < ne; ++i) {
             const int slot = i % ST;
             ok = ptx::mbar_wait_bounded(&full[slot], (uint32_t)((i / ST) & 1), kWaitCycles);
-            if (i >= 1 && ok) ok = ptx::mbar_wait_bounded(&mma_done, (uint32_t)((i - 1) & 1), kWaitCycles);
             if (!__all_sync(0xffffffffu, ok) || s_fail) { ok = false; break; }
-            tc::fence_after_sync();
+            // The MMAs of entry i-1 must be complete before this warp writes its A rows, flushes
+            // or arrives for entry i; a busy warp waits only just before its first store, so the
+            // radial part of its rows overlaps them.
+            bool waited = i == 0;
+            auto wait_prev = [&]() {
+                if (!waited) {
+                    ok = ptx::mbar_wait_bounded(&mma_done, (uint32_t)((i - 1) & 1), kWaitCycles) && ok;
+                    waited = true;
+                    tc::fence_after_sync();
+                }
+            };
             bool stored = false;
             if (i > 0 && i % kFarFlush == 0 && dirty) {
+                wait_prev();
                 flush();
                 tc::st32_zero(tmem + lane_base);
                 dirty = false;
@@ -474,6 +516,7 @@ __global__ void __launch_bounds__(160, P <= 7 ? 3 : 2) far_tc2_kernel(MvmArgs a,
                             lo[i2] = bf2_bits(__floats2bfloat162_rn(buf[2 * i2] - f.x, buf[2 * i2 + 1] - f.y));
                         }
                     }
+                    if (g == 0) wait_prev();
                     tc::st8(tmem + lane_base + Sh::COL_AHI + g * 8, hi);
                     if (PREC == TC_BF16X3) tc::st8(tmem + lane_base + Sh::COL_ALO + g * 8, lo);
                 };
@@ -490,6 +533,8 @@ __global__ void __launch_bounds__(160, P <= 7 ? 3 : 2) far_tc2_kernel(MvmArgs a,
                 dirty = true;
                 stored = true;
             }
+            wait_prev();
+            if (!__all_sync(0xffffffffu, ok)) break;
             if (stored) tc::wait_st();
             tc::fence_before_sync();
             __syncwarp();
