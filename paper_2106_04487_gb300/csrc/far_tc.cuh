@@ -513,7 +513,8 @@ __global__ void __launch_bounds__(160, P <= 7 ? 3 : 2) far_tc2_kernel(MvmArgs a,
                         hi[i2] = bf2_bits(h);
                         if (PREC == TC_BF16X3) {
                             const float2 f = __bfloat1622float2(h);
-                            lo[i2] = bf2_bits(__floats2bfloat162_rn(buf[2 * i2] - f.x, buf[2 * i2 + 1] - f.y));
+                            const float2 r = __ffma2_rn(f, make_float2(-1.f, -1.f), make_float2(buf[2 * i2], buf[2 * i2 + 1]));
+                            lo[i2] = bf2_bits(__floats2bfloat162_rn(r.x, r.y));
                         }
                     }
                     if (g == 0) wait_prev();

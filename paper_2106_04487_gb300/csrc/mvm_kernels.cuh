@@ -81,11 +81,17 @@ s2m_kernel(MvmArgs a, const __grid_constant__ FarTables T) {
     const int node = it.x;
     const float4 c = a.nd_cf[node];
     const float inv_s = 1.0f / a.nd_scale[node];
-    float acc[TPL][NR];
+    // accumulators as pairs of right-hand sides (packed FMA) when NR is even
+    constexpr int NP = NR % 2 == 0 ? NR / 2 : NR;
+    using Acc = typename std::conditional<NR % 2 == 0, float2, float>::type;
+    Acc acc[TPL][NP];
 #pragma unroll
     for (int i = 0; i < TPL; ++i)
 #pragma unroll
-        for (int r = 0; r < NR; ++r) acc[i][r] = 0.f;
+        for (int r = 0; r < NP; ++r) {
+            if constexpr (NR % 2 == 0) acc[i][r] = make_float2(0.f, 0.f);
+            else acc[i][r] = 0.f;
+        }
     for (int base = it.y + warp * 32; base < it.z; base += WARPS * 32) {
         const int s = base + lane;
         const bool ok = s < it.z;
@@ -109,16 +115,22 @@ s2m_kernel(MvmArgs a, const __grid_constant__ FarTables T) {
         __syncwarp();
 #pragma unroll 4
         for (int row = 0; row < 32; ++row) {
-            float wr[NR];
+            Acc wr[NP];
 #pragma unroll
-            for (int r = 0; r < NR; ++r) wr[r] = wt[row * NR + r];
+            for (int r = 0; r < NP; ++r) {
+                if constexpr (NR % 2 == 0) wr[r] = *reinterpret_cast<const float2*>(&wt[row * NR + 2 * r]);
+                else wr[r] = wt[row * NR + r];
+            }
 #pragma unroll
             for (int i = 0; i < TPL; ++i) {
                 const int t = lane + 32 * i;
                 if (t < NT) {
-                    float b = tile[row * ROW + t];
+                    const float b = tile[row * ROW + t];
 #pragma unroll
-                    for (int r = 0; r < NR; ++r) acc[i][r] = fmaf(b, wr[r], acc[i][r]);
+                    for (int r = 0; r < NP; ++r) {
+                        if constexpr (NR % 2 == 0) acc[i][r] = __ffma2_rn(make_float2(b, b), wr[r], acc[i][r]);
+                        else acc[i][r] = fmaf(b, wr[r], acc[i][r]);
+                    }
                 }
             }
         }
@@ -131,7 +143,14 @@ s2m_kernel(MvmArgs a, const __grid_constant__ FarTables T) {
         const int t = lane + 32 * i;
         if (t < NT)
 #pragma unroll
-            for (int r = 0; r < NR; ++r) red[(warp * NT + t) * NR + r] = acc[i][r];
+            for (int r = 0; r < NP; ++r) {
+                if constexpr (NR % 2 == 0) {
+                    red[(warp * NT + t) * NR + 2 * r] = acc[i][r].x;
+                    red[(warp * NT + t) * NR + 2 * r + 1] = acc[i][r].y;
+                } else {
+                    red[(warp * NT + t) * NR + r] = acc[i][r];
+                }
+            }
     }
     __syncthreads();
     float* out = a.part + (int64_t)blockIdx.x * NT * NR;
