@@ -299,16 +299,19 @@ __global__ void __launch_bounds__(kTB) far_tc_kernel(MvmArgs a, KernelParams kp_
 // ----------------------------------------------------------------------------------------
 // d = 3, BF16 / BF16 hi+lo: the basis rows go straight into tensor memory (A operand) instead
 // of shared memory, warp-specialised like the near field.
-//   warps 0-3 (thread = target = TMEM lane): per far entry i, wait for its info, then for the
-//     MMAs of entry i-1 (A columns free; every kFarFlush entries the accumulator rows are
-//     added into float32 registers and zeroed); a warp with a target in the entry's mask
-//     generates its rows 32 terms at a time and stores them as packed BF16 pairs (hi, lo
-//     planes) with tcgen05.st; arrive on aready.
-//   warp 4 lane 0: per entry, the node's centre, scale and the entry's row mask go to a stage
-//     with a bulk copy of the node's packed multipoles (ST entries ahead); waits aready,
+//   warps 0-3 (thread = target = TMEM lane): per far entry i, wait for its info; a warp with a
+//     target in the entry's mask generates its rows (radial part first, then the harmonics in
+//     increasing term order) and stores them 16 terms at a time as packed BF16 pairs (hi, lo
+//     planes) with tcgen05.st -- waiting for the MMAs of entry i-1 only just before its first
+//     store; every kFarFlush entries the accumulator rows are added into float32 sums in shared
+//     memory and zeroed; every warp has seen the MMAs of entry i-1 complete before it arrives on
+//     aready for entry i.
+//   warp 4 (lane 0 issues): per entry, the node's centre, scale and the entry's row mask go to a
+//     stage with a bulk copy of the node's packed multipoles (ST - 1 entries ahead; the metadata
+//     of 32 entries at a time is loaded by the whole warp, one lane per entry); waits aready,
 //     issues the MMAs (rows outside the mask disabled) and commits them to mma_done.
-// The accumulator is flushed into float32 registers because the tensor core's float32
-// accumulation drifts over thousands of MMAs.  Every wait is bounded.
+// The accumulator is flushed because the tensor core's float32 accumulation drifts over
+// thousands of MMAs.  Every wait is bounded.
 template <int P, int PREC>
 struct Tc2Shape {
     using S = TcShape<3, P, PREC>;

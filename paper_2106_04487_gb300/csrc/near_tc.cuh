@@ -14,9 +14,8 @@
 // hi*hi + hi*lo + lo*hi.  The dropped lo*lo and the truncation of lo to TF32 leave at most about
 // 2^-20 of each product, with random sign.  The tensor core's own float32 accumulation is not
 // round-to-nearest: summed over the thousands of MMAs of a target block it drifts by about 2^-24
-// per MMA in one direction (measured: 2e-5 relative after ~600 MMAs).  So each chunk's MMAs start
-// a fresh accumulator, and each thread adds the chunk's partial row into float32 registers
-// (round-to-nearest) once the chunk's MMAs are done.
+// per MMA in one direction (measured: 2e-5 relative after ~600 MMAs).  So every few chunks each
+// thread adds its accumulator row into float32 registers (round-to-nearest) and zeroes it.
 #pragma once
 
 #include "mvm_kernels.cuh"
@@ -175,38 +174,6 @@ __device__ __forceinline__ void add_partial(uint32_t taddr, float acc[32]) {
 #pragma unroll
     for (int r = 0; r < 32; ++r) acc[r] += d[r];
 }
-
-// Walks the (near leaf, chunk of <= CH sources) sequence of one target block.
-struct NearChunks {
-    int64_t e, e1;
-    int cb, s1;
-    __device__ __forceinline__ void settle(const MvmArgs& a) {
-        while (e < e1 && cb >= s1) {
-            if (++e < e1) {
-                const int leaf = a.near_ent[e].x;
-                cb = a.nd_begin[leaf];
-                s1 = a.nd_end[leaf];
-            }
-        }
-    }
-    __device__ __forceinline__ void start(const MvmArgs& a, int64_t e0, int64_t e_end) {
-        e = e0;
-        e1 = e_end;
-        cb = s1 = 0;
-        if (e < e1) {
-            const int leaf = a.near_ent[e].x;
-            cb = a.nd_begin[leaf];
-            s1 = a.nd_end[leaf];
-        }
-        settle(a);
-    }
-    __device__ __forceinline__ bool done() const { return e >= e1; }
-    __device__ __forceinline__ int count() const { return min(NearTcShape::CH, s1 - cb); }
-    __device__ __forceinline__ void next(const MvmArgs& a) {
-        cb += NearTcShape::CH;
-        settle(a);
-    }
-};
 
 // Per record stage: what the producer resolved for the chunk it holds.
 struct NearChunkInfo {
