@@ -333,7 +333,7 @@ struct FarTc2Info {
 };
 
 template <int P, int PREC>
-__global__ void __launch_bounds__(160, P <= 7 ? 3 : 2) far_tc2_kernel(MvmArgs a, KernelParams kp_all, const __grid_constant__ FarTables T,
+__global__ void __launch_bounds__(160, P <= 6 ? 4 : P <= 7 ? 3 : 2) far_tc2_kernel(MvmArgs a, KernelParams kp_all, const __grid_constant__ FarTables T,
                                                          const unsigned char* __restrict__ image, int nr_total) {
     using Sh = Tc2Shape<P, PREC>;
     using S = typename Sh::S;
