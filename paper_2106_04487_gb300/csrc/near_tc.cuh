@@ -197,7 +197,7 @@ struct NearChunkInfo {
 // threads up front) whatever happens: a bounded mbarrier wait that runs out sets s_fail, which
 // only skips work, and the producer drains what it issued before the CTA frees tensor memory.
 template <int D, int KIND>
-__global__ void __launch_bounds__(NearTcShape::THREADS, 3) near_tc_kernel(MvmArgs a, KernelParams kp_all) {
+__global__ void __launch_bounds__(NearTcShape::THREADS, 4) near_tc_kernel(MvmArgs a, KernelParams kp_all) {
     using S = NearTcShape;
     constexpr int CH = S::CH, ST = S::ST, F4 = S::F4, NR = S::NR, NC = S::CONSUMERS;
     constexpr uint32_t IDESC = tc::instr_desc(2u, 128u, (uint32_t)NR);
@@ -210,6 +210,7 @@ __global__ void __launch_bounds__(NearTcShape::THREADS, 3) near_tc_kernel(MvmArg
     __shared__ uint32_t tmem_base;
     __shared__ uint32_t s_valid[kMaskWords];
     __shared__ int s_fail, s_nch;
+    __shared__ float s_acc[NR][NC * 32];                     // float32 sums of the accumulator rows
     const int tl = threadIdx.x, warp = tl >> 5, lane = tl & 31;
     const int64_t blk = cta_block(a);
     const KernelParams kp = block_params(a, blk, kp_all);
@@ -361,9 +362,18 @@ __global__ void __launch_bounds__(NearTcShape::THREADS, 3) near_tc_kernel(MvmArg
         }
         tc::st32_zero(tmem + lane_base);  // accumulator rows start at zero; every MMA accumulates
         tc::wait_st();
-        float acc[NR];
 #pragma unroll
-        for (int r = 0; r < NR; ++r) acc[r] = 0.f;
+        for (int r = 0; r < NR; ++r) s_acc[r][tl] = 0.f;
+        // accumulator row -> the float32 sums in shared memory, 16 columns at a time
+        auto flush = [&]() {
+#pragma unroll
+            for (int h = 0; h < NR; h += 16) {
+                float d[16];
+                tc::ld16(tmem + lane_base + h, d);
+#pragma unroll
+                for (int r = 0; r < 16; ++r) s_acc[h + r][tl] += d[r];
+            }
+        };
         bool dirty = false;  // this warp's accumulator rows hold products not yet added to acc
         for (int c = 0; c < nch; ++c) {
             const int slot = c % ST;
@@ -420,7 +430,7 @@ __global__ void __launch_bounds__(NearTcShape::THREADS, 3) near_tc_kernel(MvmArg
             const bool work = !s_fail;
             bool stored = false;
             if (work && c % S::FLUSH == 0 && dirty) {
-                add_partial(tmem + lane_base, acc);
+                flush();
                 tc::st32_zero(tmem + lane_base);
                 dirty = false;
                 stored = true;
@@ -461,12 +471,12 @@ __global__ void __launch_bounds__(NearTcShape::THREADS, 3) near_tc_kernel(MvmArg
         if (nch >= 1) ptx::named_sync(kBarMma, kBarThreads);  // the MMAs of the last chunk are done
         tc::fence_after_sync();
         const bool ok = !s_fail;
-        if (ok && dirty) add_partial(tmem + lane_base, acc);
+        if (ok && dirty) flush();
         __syncwarp();
         if (ok && valid)
 #pragma unroll
             for (int r = 0; r < NR; ++r)
-                if (r < a.nr) acc_store(a, r, t, acc[r] * kp.scale);
+                if (r < a.nr) acc_store(a, r, t, s_acc[r][tl] * kp.scale);
         if (!ok && tl == 0) atomicExch(a.err, 1);
     }
     tc::fence_before_sync();
