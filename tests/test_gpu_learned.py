@@ -94,7 +94,8 @@ def test_training_reduces_the_objective(trained):
 def test_solve_with_learned_correction(fkt, trained):
     """The corrected preconditioner inside CG converges to the requested residual (falling back to
     block-Jacobi if it does not); the iteration counts of the three preconditioners are reported --
-    for this long-range kernel no block-diagonal preconditioner beats none."""
+    for this long-range kernel no block-diagonal preconditioner beats none: CG's slow directions
+    are smooth modes spanning many blocks, which a block-local correction cannot represent."""
     import torch
 
     X, plan, info = trained
