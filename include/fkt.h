@@ -99,6 +99,8 @@ typedef struct {
     int64_t s2m_nodes;       /* nodes whose coefficients some target uses */
     double plan_ms;          /* wall time of fkt_plan */
     double last_near_ms, last_far_ms, last_s2m_ms, last_total_ms; /* last fkt_mvm, if timing is on */
+    int32_t coarse_columns;  /* columns of fkt_solve's coarse space after its last set-up (0: none) */
+    int32_t coarse_dropped;  /* eigen-directions of its coarse operator E left out of E^+ */
 } fkt_stats;
 
 /* Build a plan (Sec. 3.1 tree, far/near sets of Sec. 3.1-3.2, expansion tables of Theorem 3.1).
@@ -210,6 +212,17 @@ int fkt_learn_eval(fkt_plan_t plan, const float* params, double* loss, float* gr
  * rows and columns beyond the block's size are zero).  Either pointer may be NULL. */
 int fkt_learn_teacher(fkt_plan_t plan, int64_t* blocks, float* D);
 
+/* Random Fourier frequencies of a kernel (host only, no device work): omega [R][d] and phase [R]
+ * (row-major, caller-allocated host buffers) such that E[cos(omega . delta)] = K(|delta|) / K(0)
+ * (Bochner's theorem), phase ~ U[0, 2 pi), drawn with a 64-bit Mersenne Twister seeded by seed.
+ * Spectral densities: Gaussian N(0, I/l^2); exponential and Matern-nu (nu = 1/2, 3/2, 5/2)
+ * multivariate Student t with 2 nu degrees of freedom and scale 1/l; rational quadratic and
+ * Cauchy Gaussian scale mixtures (precision tau/l^2 with tau ~ Gamma(a, rate a), Cauchy: a = 1
+ * and l^2/2); Laplace 1/r has no normalisable density, so it gets the Gaussian's at l.  These
+ * are the features of fkt_solve's coarse space (option "coarse_rank").  The paper has no
+ * counterpart.  1 <= d <= 8, 1 <= R <= 2^24; FKT_ERR_INVALID_ARG otherwise. */
+int fkt_spectral_sample(fkt_kernel kernel, int d, int R, uint64_t seed, double* omega, double* phase);
+
 /* Solve (Ktilde + sigma2 I) x = b.  b, x device [nrhs][N] float32 (x is output only),
  * 1 <= nrhs <= 64, sigma2 > 0, 0 < tol < 1, max_iter >= 1.  Synchronizes.
  * Returns FKT_OK when every right-hand side reached |r| <= tol |b|, FKT_ERR_NOT_CONVERGED
@@ -275,6 +288,20 @@ int fkt_autotune_leaf(const float* points, int64_t N, int d, fkt_kernel kernel, 
  *   "preconditioner" "block_jacobi" (default) | "learned" | "none"   preconditioner of fkt_solve;
  *               "learned" needs fkt_precond_learn first and falls back to block_jacobi when
  *               CG with the correction does not converge (fkt_solve_info.used_fallback)
+ *   "coarse_rank"  "0" (default) | R in 1..256  adds a two-level coarse correction to fkt_solve's
+ *               preconditioner: the coarse space spans R random Fourier features of the kernel
+ *               (frequencies from fkt_spectral_sample), orthonormalised; with A = Ktilde + sigma2 I,
+ *               W = A Q and E = Q^T W the preconditioner becomes
+ *               Q E^-1 Q^T + (I - Q E^-1 W^T) M (I - W E^-1 Q^T), M = the "preconditioner" option
+ *               (balancing two-level form; symmetric positive semi-definite).  It targets the
+ *               smooth global modes that make CG slow for long-range kernels and small sigma2,
+ *               which no block-diagonal M can represent.  Set-up per (sigma2, R, seed): R / 64
+ *               fkt_mvm products plus float64 R x R factorisations on the host; per iteration
+ *               two skinny N x R products each way.  Needs N >= 4 R and a single-problem plan
+ *               (FKT_ERR_INVALID_ARG / FKT_ERR_UNSUPPORTED otherwise); fkt_solve returns
+ *               FKT_ERR_INVALID_ARG if Ktilde + sigma2 I is not positive definite on the coarse
+ *               space.  The paper has no counterpart (its GP solves run plain CG, Sec. C).
+ *   "coarse_seed"  unsigned integer (default 1): seed of the coarse space's frequencies
  *   "near_targets_per_thread"  "2" (default) | "4"  register blocking of the near-field kernel
  *               (4 applies to one right-hand side; results are identical up to rounding order)
  * Errors: FKT_ERR_INVALID_ARG for an unknown key or value. */

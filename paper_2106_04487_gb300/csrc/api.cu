@@ -1,5 +1,6 @@
 // C ABI entry points (include/fkt.h).
 #include <math.h>
+#include <stdlib.h>
 #include <string.h>
 
 #include <chrono>
@@ -204,6 +205,18 @@ int fkt_set_option(fkt_plan_t plan, const char* key, const char* value) {
         else if (!strcmp(value, "block_jacobi")) plan->pc_mode = 1;
         else if (!strcmp(value, "learned")) plan->pc_mode = 2;
         else return FKT_ERR_INVALID_ARG;
+        return FKT_OK;
+    }
+    if (!strcmp(key, "coarse_rank") || !strcmp(key, "coarse_seed")) {
+        char* end = nullptr;
+        const unsigned long long v = strtoull(value, &end, 10);
+        if (!*value || *end || value[0] == '-') return FKT_ERR_INVALID_ARG;
+        if (key[7] == 'r') {
+            if (v > 256) return FKT_ERR_INVALID_ARG;
+            plan->coarse_rank = (int)v;
+        } else {
+            plan->coarse_seed = (uint64_t)v;
+        }
         return FKT_OK;
     }
     if (!strcmp(key, "near_targets_per_thread")) {

@@ -125,6 +125,10 @@ struct fkt_plan_s {
     float* cg_q = nullptr;         // [nrhs][N] (Ktilde + sigma2 I) p
     float* cg_z = nullptr;         // [nrhs][N] preconditioned residual
     double* cg_s = nullptr;        // scalars: [8][kMaxRhs]
+    // two-level coarse correction of the preconditioner (coarse.cu)
+    int coarse_rank = 0;           // R random Fourier features (0: off)
+    uint64_t coarse_seed = 1;
+    void* coarse = nullptr;        // coarse-space state
     cudaStream_t stream2 = nullptr;
     cudaEvent_t ev[10] = {};
     // batch of independent problems merged into one plan (empty for a single problem)
@@ -193,6 +197,12 @@ int precond_apply(fkt_plan_s* P, const float* r, const double* r64, float* z, in
 int solve(fkt_plan_s* P, double sigma2, const float* b, float* x, int nrhs, double tol, int max_iter,
           fkt_solve_info* info);
 void free_solve(fkt_plan_s* P);
+
+// coarse.cu
+int spectral_sample(const fkt_kernel& k, int d, int R, uint64_t seed, double* omega, double* phase);
+int coarse_setup(fkt_plan_s* P, double sigma2);
+int coarse_apply(fkt_plan_s* P, const double* r64, float* z, int nrhs);
+void free_coarse(fkt_plan_s* P);
 
 // learn.cu
 int precond_learn(fkt_plan_s* P, double sigma2, const fkt_learn_opts* opts, fkt_learn_info* info);

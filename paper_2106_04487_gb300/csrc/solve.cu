@@ -245,6 +245,7 @@ __global__ void cg_true_residual_kernel(int64_t N, float sigma2, const float* __
 }  // namespace
 
 void free_solve(fkt_plan_s* P) {
+    free_coarse(P);
     cudaFree(P->pc_inv);
     cudaFree(P->cg_x);
     cudaFree(P->cg_r);
@@ -328,10 +329,16 @@ int solve(fkt_plan_s* P, double sigma2, const float* b, float* x, int nrhs, doub
     return rc;
 }
 
+// z = P^{-1} r: the first-level preconditioner alone, or inside the two-level coarse correction.
+static int apply_pc(fkt_plan_s* P, const double* r64, float* z, int nrhs) {
+    return P->coarse_rank > 0 ? coarse_apply(P, r64, z, nrhs) : precond_apply(P, nullptr, r64, z, nrhs);
+}
+
 static int solve_once(fkt_plan_s* P, double sigma2, const float* b, float* x, int nrhs, double tol, int max_iter,
                       fkt_solve_info* info) {
     int rc = P->pc_mode ? precond_setup(P, sigma2) : FKT_OK;
     if (rc) return rc;
+    if (P->coarse_rank > 0 && (rc = coarse_setup(P, sigma2))) return rc;
     const int64_t N = P->N;
     cudaStream_t st = P->stream;
     if (P->cg_cap < nrhs) {
@@ -355,7 +362,7 @@ static int solve_once(fkt_plan_s* P, double sigma2, const float* b, float* x, in
     FKT_CUDA_TRY(cudaMemcpyAsync(sc + kAct * kMaxRhs, act.data(), sizeof(double) * kMaxRhs, cudaMemcpyHostToDevice, st));
     cg_init_kernel<<<grid, 256, 0, st>>>(N, nrhs, b, P->cg_x, P->cg_r, sc);
     // z = M^{-1} r, rz = r.z, p = z
-    if ((rc = precond_apply(P, nullptr, P->cg_r, P->cg_z, nrhs))) return rc;
+    if ((rc = apply_pc(P, P->cg_r, P->cg_z, nrhs))) return rc;
     double* rz_cur = sc + kRzA * kMaxRhs;
     double* rz_nxt = sc + kRzB * kMaxRhs;
     cg_dot_kernel<<<grid, 256, 0, st>>>(N, P->cg_r, nullptr, P->cg_z, rz_cur);
@@ -378,7 +385,7 @@ static int solve_once(fkt_plan_s* P, double sigma2, const float* b, float* x, in
         FKT_CUDA_TRY(cudaMemsetAsync(rz_nxt, 0, sizeof(double) * kMaxRhs, st));
         cg_shift_dot_kernel<<<grid, 256, 0, st>>>(N, s2, P->cg_p, P->cg_q, sc);
         cg_update_kernel<<<grid, 256, 0, st>>>(N, P->cg_p, P->cg_q, P->cg_x, P->cg_r, sc, rz_cur);
-        if ((rc = precond_apply(P, nullptr, P->cg_r, P->cg_z, nrhs))) return rc;
+        if ((rc = apply_pc(P, P->cg_r, P->cg_z, nrhs))) return rc;
         cg_dot_kernel<<<grid, 256, 0, st>>>(N, P->cg_r, nullptr, P->cg_z, rz_nxt);
         cg_direction_kernel<<<grid, 256, 0, st>>>(N, P->cg_z, P->cg_p, rz_nxt, rz_cur, sc, 0);
         FKT_CUDA_TRY(cudaGetLastError());

@@ -26,7 +26,7 @@ EXPORTS = ["fkt_plan", "fkt_mvm", "fkt_mvm_host", "fkt_dense_mvm", "fkt_set_opti
            "fkt_plan_tree", "fkt_plan_lists", "fkt_destroy", "fkt_error_string", "fkt_mvm_noalloc",
            "fkt_check", "fkt_precond_setup", "fkt_precond_apply", "fkt_solve", "fkt_batch_plan", "fkt_batch_mvm",
            "fkt_batch_set_option", "fkt_batch_info", "fkt_batch_check", "fkt_batch_destroy", "fkt_autotune_leaf",
-           "fkt_precond_learn", "fkt_learn_params", "fkt_learn_eval", "fkt_learn_teacher"]
+           "fkt_precond_learn", "fkt_learn_params", "fkt_learn_eval", "fkt_learn_teacher", "fkt_spectral_sample"]
 
 
 class FktError(RuntimeError):
@@ -66,7 +66,8 @@ class fkt_stats(ctypes.Structure):
                 ("near_entries", ctypes.c_int64), ("masks", ctypes.c_int64), ("far_pairs", ctypes.c_int64),
                 ("near_pairs", ctypes.c_int64), ("s2m_pairs", ctypes.c_int64), ("s2m_nodes", ctypes.c_int64),
                 ("plan_ms", ctypes.c_double), ("last_near_ms", ctypes.c_double), ("last_far_ms", ctypes.c_double),
-                ("last_s2m_ms", ctypes.c_double), ("last_total_ms", ctypes.c_double)]
+                ("last_s2m_ms", ctypes.c_double), ("last_total_ms", ctypes.c_double),
+                ("coarse_columns", ctypes.c_int32), ("coarse_dropped", ctypes.c_int32)]
 
 
 _LIB = None
@@ -110,6 +111,7 @@ def lib() -> ctypes.CDLL:
     L.fkt_precond_apply.argtypes = [vp, vp, vp, ctypes.c_int]
     L.fkt_solve.argtypes = [vp, ctypes.c_double, vp, vp, ctypes.c_int, ctypes.c_double, ctypes.c_int,
                             ctypes.POINTER(fkt_solve_info)]
+    L.fkt_spectral_sample.argtypes = [fkt_kernel, ctypes.c_int, ctypes.c_int, ctypes.c_uint64, vp, vp]
     L.fkt_destroy.argtypes = [vp]
     L.fkt_destroy.restype = None
     L.fkt_error_string.argtypes = [ctypes.c_int]
@@ -198,6 +200,15 @@ def fkt_solve(plan, sigma2: float, b, x, nrhs: int, tol: float, max_iter: int, r
     out = {k: getattr(info, k) for k, _ in fkt_solve_info._fields_ if k != "pad"}
     out["status"] = st
     return out
+
+
+def fkt_spectral_sample(kernel: fkt_kernel, d: int, R: int, seed: int = 1):
+    """Random Fourier frequencies (host only): returns (omega [R][d], phase [R]) float64."""
+    omega = np.zeros((R, d), np.float64)
+    phase = np.zeros(R, np.float64)
+    _check(lib().fkt_spectral_sample(kernel, int(d), int(R), int(seed), _ptr(omega), _ptr(phase)),
+           "fkt_spectral_sample")
+    return omega, phase
 
 
 def fkt_check(plan):

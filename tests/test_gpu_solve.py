@@ -118,3 +118,71 @@ def test_solve_reports_non_convergence_and_bad_args(fkt):
         plan.solve(0.0, b)
     with pytest.raises(fkt.FktError):
         plan.solve(1e-2, b, tol=2.0)
+
+
+def test_coarse_space_cuts_iterations(fkt, orc):
+    """Two-level coarse correction (128 random Fourier features of the kernel) on the long-range
+    Matern-5/2 l = 0.3 system where block-Jacobi does not help: far fewer CG iterations, and the
+    solution still satisfies the oracle's float64 FKT system to the float32 floor."""
+    import torch
+
+    X = inputs.gaussian_mixture(20000, 4, 20, 0.05, seed=34)
+    b = inputs.normal_weights(20000, 2, seed=40)
+    bt = torch.from_numpy(b).cuda()
+    sigma2 = 1e-2
+    plan = fkt.Plan(torch.from_numpy(X).cuda(), "matern52", lengthscale=0.3, p=6, leaf_size=256, theta=0.3)
+    its = {}
+    for pc, rank in (("none", 0), ("none", 128), ("block_jacobi", 128)):
+        plan.set_option("preconditioner", pc)
+        plan.set_option("coarse_rank", str(rank))
+        x, info = plan.solve(sigma2, bt, tol=1e-5, max_iter=4000, raise_on_not_converged=False)
+        its[(pc, rank)] = (info["iterations"], info["converged"], info["true_rel_residual"],
+                           plan.stats()["coarse_columns"])
+        if (pc, rank) == ("none", 128):
+            x128 = x.cpu().numpy().astype(np.float64)
+    print(its)
+    assert all(v[1] == 1 for v in its.values()), its
+    assert its[("none", 128)][0] <= 0.4 * its[("none", 0)][0], its
+    assert 64 <= its[("none", 128)][3] <= 128, its
+    F = orc.FKT(X, orc.kparams("matern52", 0.3), p=6, leaf_size=256, theta=0.3)
+    Ax = F.mvm(x128) + sigma2 * x128
+    res = np.linalg.norm(b - Ax, axis=1) / np.linalg.norm(b, axis=1)
+    assert res.max() < 3e-3, (res, its)
+
+
+def test_coarse_space_dense_limit(fkt, orc):
+    """theta -> 0 (Ktilde = K): with the coarse correction on top of block-Jacobi the solution
+    satisfies the float64 dense system, for two seeds of the coarse space."""
+    import torch
+
+    X = inputs.gaussian_mixture(2000, 4, 20, 0.05, seed=32)
+    b = inputs.normal_weights(2000, 3, seed=41)
+    sigma2 = 1e-2
+    plan = fkt.Plan(torch.from_numpy(X).cuda(), "matern52", lengthscale=0.3, p=4, leaf_size=128, theta=1e-6)
+    plan.set_option("coarse_rank", "64")
+    for seed in ("1", "2"):
+        plan.set_option("coarse_seed", seed)
+        x, info = plan.solve(sigma2, torch.from_numpy(b).cuda(), tol=1e-6, max_iter=2000)
+        x = x.cpu().numpy().astype(np.float64)
+        Ax = orc.dense(X, orc.kparams("matern52", 0.3), x) + sigma2 * x
+        res = np.linalg.norm(b - Ax, axis=1) / np.linalg.norm(b, axis=1)
+        assert info["converged"] == 1
+        assert res.max() < 3e-4, (seed, res, info)
+
+
+def test_coarse_space_arguments(fkt):
+    import torch
+
+    X = inputs.uniform_cube(500, 3, seed=42)
+    b = torch.from_numpy(inputs.normal_weights(500, 1, seed=43)).cuda()
+    plan = fkt.Plan(torch.from_numpy(X).cuda(), "gaussian", lengthscale=0.2, p=4, leaf_size=64, theta=1e-6)
+    for bad in ("257", "-1", "x", ""):
+        with pytest.raises(fkt.FktError):
+            plan.set_option("coarse_rank", bad)
+    plan.set_option("coarse_rank", "200")        # needs N >= 4 R
+    with pytest.raises(fkt.FktError) as e:
+        plan.solve(1e-2, b)
+    assert e.value.status == fkt.FKT_ERR_INVALID_ARG
+    plan.set_option("coarse_rank", "100")
+    x, info = plan.solve(1e-2, b, tol=1e-6, max_iter=500)
+    assert info["converged"] == 1
