@@ -249,6 +249,24 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def max_over_ranks(x: float, world: int, device="cuda") -> float:
+    """The largest x over all ranks (the slowest replica's time); x itself on one rank."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_value(steps: int, units_per_step: int, world: int, total_ms: float) -> float:
+    """Whole-job throughput of independent replicas: the units all ranks processed over the
+    slowest rank's time."""
+    return steps * units_per_step * world / (total_ms / 1e3)
+
+
 def time_form(obj, Wd, Yd, steps, warmup, flush, stream, stats=True):
     """Per-step CUDA-event times of obj.mvm on the launching stream, with the library's own
     per-stage events (near, far + wait, s2m) read after each step when stats is set."""
@@ -387,15 +405,9 @@ def run_ours(a):
         head = time_form(obj, Wd, Yd, a.steps, 0, flush, stream, stats=not batch)
     barrier()
     obj.check()  # raises if a bounded device-side wait ran out during the timed steps
-    total_ms = float(sum(head["step_ms"]))
-    if world > 1:
-        import torch.distributed as dist
-
-        t = torch.tensor([total_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(float(sum(head["step_ms"])), world)
     mvms_per_step = a.nrhs * (256 if batch else 1)
-    value = a.steps * mvms_per_step * world / (total_ms / 1e3)
+    value = replica_value(a.steps, mvms_per_step, world, total_ms)
     y_head = Yd.cpu().numpy().astype(np.float64)
 
     # the plain float32 form on the same plan
