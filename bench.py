@@ -553,7 +553,7 @@ def run_ours(a):
                                "speedup_of_headline": value / world / cv}
     if second is not None:
         out["second_kernel"] = second
-    if rank == 0 and not a.no_cpu_baseline:
+    if rank == 0 and world == 1 and not a.no_cpu_baseline:  # the CPU baseline is a single-GPU figure
         out["cpu_baseline"] = cpu_baseline(a, X, W, probs if batch else None, obj if batch else None)
     if world > 1:
         import torch.distributed as dist
