@@ -1,5 +1,5 @@
-"""Pin of the oracle's exact expansion tables against Table 3 of the paper (appendix, compression of
-the radial expansion).
+"""Pins of the oracle's exact expansion tables against the two tables of the paper's appendix on the
+compression of the radial expansion: the ranks of Table 3 and the worked exp(-r) example.
 
 For a kernel with K' = q K, q a Laurent polynomial, every derivative is K^(m) = E(r) L_m(r) with
 L_m a Laurent polynomial (L_{m+1} = L_m' + q L_m), so the degree-k radial part of the expansion,
@@ -131,3 +131,54 @@ def test_table3_catches_planted_table_mistakes():
     assert radial_rank("exp(-r)", 0, P, 3, no_binomial)[0] != 2
     assert radial_rank("1/r", 0, P, 3, no_m0)[0] != 1
     assert radial_rank("exp(-r)", 0, P, 5, flipped)[0] != 3
+
+
+def _exp_decomp():
+    F, G = defaultdict(dict), defaultdict(dict)
+    for line in open(os.path.join(HERE, "golden", "exp_decomp.txt")):
+        if not line.strip() or line.startswith("#"):
+            continue
+        f = line.split()
+        poly = {int(t.split(":")[0]): Fraction(t.split(":")[1]) for t in f[3:]}
+        (F if f[0] == "F" else G)[int(f[1])][int(f[2])] = poly
+    return F, G
+
+
+def radial_part_exp(k, p, tbar=T.Tbar):
+    """{(power of r', power of r): coefficient} of the degree-k radial part of exp(-|r - r'|) in
+    d = 3, divided by exp(-r): sum_j r'^j sum_m (-1)^m r^(m-j) Tbar_{k,j,m}."""
+    out = defaultdict(Fraction)
+    for j in range(k, p + 1, 2):
+        for m in range(j + 1):
+            t = tbar(k, j, m, 3)
+            if t:
+                out[(j, m - j)] += (-1) ** m * t
+    return {key: v for key, v in out.items() if v}
+
+
+@pytest.mark.parametrize("k", [0, 1, 2])
+def test_exp_decomp_worked_example(k):
+    """The printed F_{k,i} G_{k,i} of exp(-r), times r'^k / r^(k+1), equal the tables' radial part
+    term by term, for every power of r' the table prints (up to r'^(k+6))."""
+    F, G = _exp_decomp()
+    printed = defaultdict(Fraction)
+    for i in F[k]:
+        for e, c in F[k][i].items():
+            for j, g in G[k][i].items():
+                printed[(j + k, e - k - 1)] += c * g
+    printed = {key: v for key, v in printed.items() if v}
+    jmax = max(j for j, _ in printed)
+    ours = {key: v for key, v in radial_part_exp(k, jmax).items() if key[0] <= jmax}
+    assert ours == printed
+
+
+def test_exp_decomp_catches_the_printed_tbar_formula():
+    """Without the binomial of reading R1 the k = 1 radial part no longer matches the worked example."""
+    def no_binomial(k, j, m, d):
+        if j < k or (j - k) % 2 or m < 0 or m > j:
+            return Fraction(0)
+        return sum((T.A(k, 2 * n - j, d) * Fraction(-2) ** (2 * n - j) * T.B(n, m) / factorial(n)
+                    for n in range(max((j + k) // 2, m), j + 1)), Fraction(0))
+
+    assert radial_part_exp(1, 7, no_binomial) != radial_part_exp(1, 7)
+    assert radial_part_exp(1, 7, no_binomial)[(3, -1)] != Fraction(-1, 5)
