@@ -10,14 +10,17 @@ against the float64 dense product on a 10,000-target subsample.
 Other workloads (--workload): gauss20k (20k uniform points, Gaussian l = 0.1, p = 4, 1 RHS),
 laplace16m (16M points half uniform / half in 100 tight clusters, Laplace 1/(4 pi r), p = 8, 4 RHS,
 BF16 far field) and batch256 (256 independent problems of 2k-200k points in the unit ball, mixed
-Gaussian / Laplace / rational-quadratic kernels, 8 RHS, one CUDA-graph launch).
+Gaussian / Laplace / rational-quadratic kernels, 8 RHS, one CUDA-graph launch) and gpsolve (the GP
+solve (Ktilde + sigma2 I) x = b of fkt_solve: d = 4, 100k mixture points, Matern-5/2 l = 0.3,
+sigma2 = 1e-2, 8 RHS; one step = one solve with the two-level coarse space, the solves without a
+preconditioner and with block-Jacobi run once beside it).
 
 One step = one product over all right-hand sides (all stages of Algorithm 1: permute, s2m, near
 field, m2t, combine) on resident device buffers; one MVM = one right-hand side of one problem.  L2
 is flushed between timed steps (a 256 MiB write outside the timed events).  Prints ONE JSON line.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                    [--workload matern1m|gauss20k|laplace16m|batch256]
+                    [--workload matern1m|gauss20k|laplace16m|batch256|gpsolve]
                     [--kernel matern32|cauchy] [--p P] [--theta T] [--leaf M] [--nrhs R]
                     [--far-precision bf16x3|tf32|bf16|fp32] [--near-precision tf32x3|fp32]
                     [--compare fp32|none]
@@ -64,8 +67,12 @@ WORKLOADS = {
     "batch256": dict(desc="256 problems, N log-uniform [2000, 200000], unit ball, kernels gaussian l=0.1 / "
                           "laplace 1/r / ratquad alpha=1 l=0.2", n=0, points=None, kernel=None, p=4, theta=0.5,
                      leaf=512, nrhs=8, near="fp32", far="bf16x3", weights="normal", err_targets=150),
+    "gpsolve": dict(desc="d=4 N=100000 gaussian-mixture(20 comps, std 0.05)", n=100_000,
+                    points=lambda n: inputs.gaussian_mixture(n, 4, 20, 0.05), kernel=("matern52", 0.3, 1.0, 1.0),
+                    p=6, theta=0.3, leaf=256, nrhs=8, near="fp32", far="fp32", weights="normal", err_targets=0),
 }
 BATCH_KERNELS = [("gaussian", 0.1, 1.0, 1.0), ("laplace", 1.0, 1.0, 1.0), ("ratquad", 0.2, 1.0, 1.0)]
+GP_SIGMA2 = 1e-2
 
 # DRAM bytes (read + write) per launch of a kernel from one ncu capture, keyed by kernel and
 # workload (kernel, p, theta, leaf, nrhs, N); see profiles/.  Any other workload reports null.
@@ -162,6 +169,10 @@ def parse():
     ap.add_argument("--n", type=int, default=None)
     ap.add_argument("--err-targets", type=int, default=None)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--coarse-rank", type=int, default=256, help="gpsolve: coarse space of the timed solves")
+    ap.add_argument("--tol", type=float, default=1e-5, help="gpsolve: CG tolerance")
+    ap.add_argument("--compare-iters", type=int, default=3000,
+                    help="gpsolve: iteration cap of the comparison solves (no preconditioner, block-Jacobi)")
     a = ap.parse_args()
     w = WORKLOADS[a.workload]
     for key, wkey in [("p", "p"), ("theta", "theta"), ("leaf", "leaf"), ("nrhs", "nrhs"), ("far_precision", "far"),
@@ -562,6 +573,95 @@ def run_ours(a):
     return out if rank == 0 else None
 
 
+def solve_record(plan, b, pc: str, rank: int, tol: float, max_iter: int) -> dict:
+    """One fkt_solve with the given first-level preconditioner and coarse rank (fkt_solve
+    synchronises, so the host clock brackets the device work)."""
+    plan.set_option("preconditioner", pc)
+    plan.set_option("coarse_rank", str(rank))
+    t0 = time.perf_counter()
+    _, info = plan.solve(GP_SIGMA2, b, tol=tol, max_iter=max_iter, raise_on_not_converged=False)
+    dt = time.perf_counter() - t0
+    st = plan.stats()
+    return {"preconditioner": pc, "coarse_rank": rank, "coarse_columns": st["coarse_columns"],
+            "iterations": info["iterations"], "converged": bool(info["converged"]),
+            "rel_residual": info["rel_residual"], "true_rel_residual": info["true_rel_residual"], "seconds": dt}
+
+
+def run_gpsolve(a, fkt=None, torch=None):
+    """GP solves per second through fkt_solve with the coarse space (timed steps), beside one solve
+    without a preconditioner and one with block-Jacobi (iteration cap --compare-iters)."""
+    if torch is None:
+        import torch
+    if fkt is None:
+        from paper_2106_04487_gb300 import fkt
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl")
+    X = WORKLOADS["gpsolve"]["points"](a.n)
+    kname, ell, alpha, scale = a.kern
+    plan = fkt.Plan(torch.from_numpy(X).cuda(), kname, lengthscale=ell, alpha=alpha, scale=scale, p=a.p,
+                    leaf_size=a.leaf, theta=a.theta)
+    plan.set_option("far_precision", a.far_precision)
+    plan.set_option("near_precision", a.near_precision)
+    B = inputs.normal_weights(a.n, a.nrhs)
+    b = torch.from_numpy(B).cuda()
+    # one-time set-up of the coarse space (features, Gram, W = A Q, E): a solve of one iteration
+    setup = solve_record(plan, b, "none", a.coarse_rank, a.tol, 1)
+    for _ in range(a.warmup):
+        solve_record(plan, b, "none", a.coarse_rank, a.tol, 5)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.barrier()
+    torch.cuda.synchronize()
+    steps = []
+    with ClockSampler(local) as clk:
+        for _ in range(a.steps):
+            steps.append(solve_record(plan, b, "none", a.coarse_rank, a.tol, a.compare_iters))
+    total_ms = max_over_ranks(1e3 * sum(r["seconds"] for r in steps), world)
+    value = replica_value(a.steps, a.nrhs, world, total_ms)
+    # end to end: b from pinned host memory in, x back to host, inside the timed region
+    Bh = torch.from_numpy(B).pin_memory()
+    Xh = torch.empty_like(Bh).pin_memory()
+    t0 = time.perf_counter()
+    bd = Bh.to("cuda", non_blocking=True)
+    plan.set_option("preconditioner", "none")
+    x, _ = plan.solve(GP_SIGMA2, bd, tol=a.tol, max_iter=a.compare_iters, raise_on_not_converged=False)
+    Xh.copy_(x)
+    e2e_s = time.perf_counter() - t0
+    compare = [solve_record(plan, b, pc, 0, a.tol, a.compare_iters) for pc in ("none", "block_jacobi")]
+    plan.close()
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.destroy_process_group()
+    if rank != 0:
+        return None
+    last = steps[-1]
+    return {
+        "metric": f"GP solves (RHS/s) to rel. residual {a.tol:g}, fkt_solve with a {a.coarse_rank}-feature coarse space",
+        "value": value, "unit": "RHS/s", "n_gpus": world, "steps": a.steps, "warmup": a.warmup,
+        "ms_per_step": total_ms / a.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32 products, f64 CG iterates and dots", "data": "synthetic",
+        "config": {"workload": workload_name(a) + f" sigma2={GP_SIGMA2} tol={a.tol}", "points": int(a.n),
+                   "timed_solve": last, "coarse_setup_s": setup["seconds"],
+                   "l2": "not flushed: each step is thousands of products over a working set far above L2",
+                   "compare": compare},
+        "roofline": None,
+        "roofline_note": "the products inside the solve are the kernels the MVM workloads report rooflines for",
+        "e2e": {"value": a.nrhs / e2e_s, "unit": "RHS/s", "h2d_bytes_per_step": int(B.nbytes),
+                "d2h_bytes_per_step": int(B.nbytes)},
+        "gpu_launches": None,
+        "gpu_launches_note": "per CG iteration one fkt_mvm (launches_per_step) plus the CG and coarse-space kernels",
+        "clocks": clk.summary(),
+    }
+
+
 class OracleRunner:
     """The float64 oracle, as it stands, on the host cores.  One sample = s2m over all nodes
     (needed by any target) + the per-target traversal for a sample of targets, extrapolated to
@@ -665,6 +765,8 @@ def main():
     a = parse()
     if a.impl == "reference":
         out = run_reference(a)
+    elif a.workload == "gpsolve":
+        out = run_gpsolve(a)
     else:
         out = run_ours(a)
     if out is not None:

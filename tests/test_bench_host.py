@@ -35,3 +35,71 @@ def test_launches_per_step():
     assert bench.launches_per_step(1, "fp32") == 6
     # two passes (33 right-hand sides)
     assert bench.launches_per_step(33, "bf16x3") == 13 + (3 + 2 + 2)
+
+
+def test_gpsolve_orchestration_with_a_fake_plan(monkeypatch):
+    """bench.py --workload gpsolve on stand-ins for torch and the binding: the timed solves use the
+    coarse space, the comparison solves do not, and the JSON line adds up."""
+    import numpy as np
+
+    class T:
+        def __init__(self, a):
+            self.a = a
+
+        def cuda(self):
+            return self
+
+        def pin_memory(self):
+            return self
+
+        def to(self, *args, **kw):
+            return self
+
+        def copy_(self, o):
+            self.a[...] = o.a
+            return self
+
+    class FakeTorch:
+        class cuda:
+            set_device = staticmethod(lambda i: None)
+            synchronize = staticmethod(lambda: None)
+
+        from_numpy = staticmethod(T)
+        empty_like = staticmethod(lambda t: T(np.empty_like(t.a)))
+
+    calls = []
+
+    class Plan:
+        def __init__(self, X, kname, **kw):
+            assert kname == "matern52" and X.a.shape == (1000, 4)
+            self.opt = {}
+
+        def set_option(self, k, v):
+            self.opt[k] = v
+
+        def solve(self, sigma2, b, tol, max_iter, raise_on_not_converged):
+            calls.append((self.opt["preconditioner"], self.opt.get("coarse_rank"), max_iter))
+            its = 100 if self.opt.get("coarse_rank") != "0" else max_iter
+            return T(np.zeros_like(b.a)), {"iterations": min(its, max_iter), "converged": its <= max_iter,
+                                           "rel_residual": 1e-6, "true_rel_residual": 1e-3}
+
+        def stats(self):
+            return {"coarse_columns": 173 if self.opt.get("coarse_rank") != "0" else 0}
+
+        def close(self):
+            pass
+
+    class FakeFkt:
+        pass
+
+    FakeFkt.Plan = Plan
+    monkeypatch.setattr("sys.argv", ["bench.py", "--workload", "gpsolve", "--n", "1000", "--steps", "2",
+                                     "--warmup", "3", "--compare-iters", "50"])
+    out = bench.run_gpsolve(bench.parse(), fkt=FakeFkt, torch=FakeTorch)
+    timed = [c for c in calls if c[1] == "256" and c[2] == 50]
+    assert len(timed) >= 2 + 1                       # the timed steps and the end-to-end solve
+    assert ("none", "0", 50) in calls and ("block_jacobi", "0", 50) in calls
+    assert out["unit"] == "RHS/s" and out["steps"] == 2 and out["value"] > 0
+    assert out["config"]["timed_solve"]["coarse_columns"] == 173
+    assert [c["preconditioner"] for c in out["config"]["compare"]] == ["none", "block_jacobi"]
+    assert out["e2e"]["h2d_bytes_per_step"] == 8 * 1000 * 4
