@@ -103,3 +103,16 @@ def test_gpsolve_orchestration_with_a_fake_plan(monkeypatch):
     assert out["config"]["timed_solve"]["coarse_columns"] == 173
     assert [c["preconditioner"] for c in out["config"]["compare"]] == ["none", "block_jacobi"]
     assert out["e2e"]["h2d_bytes_per_step"] == 8 * 1000 * 4
+
+
+def test_reference_arm_line(monkeypatch):
+    """bench.py --impl reference (the float64 oracle on the host cores) on a small case: the keys
+    of the line the reference arm must print."""
+    monkeypatch.setattr("sys.argv", ["bench.py", "--impl", "reference", "--workload", "gauss20k", "--n", "3000",
+                                     "--steps", "1", "--warmup", "1"])
+    out = bench.run_reference(bench.parse())
+    assert out["impl"] == "reference" and out["unit"] == "MVM/s" and out["value"] > 0
+    assert out["cpu_baseline"]["kind"] == "oracle" and out["cpu_baseline"]["cores"] >= 1
+    assert out["cpu_baseline"]["value"] == out["value"]
+    assert out["e2e"] == {"value": out["value"], "unit": "MVM/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
+    assert out["config"]["workload"].startswith("gaussian l=0.1 d=3 N=3000")
