@@ -230,6 +230,17 @@ int fkt_spectral_sample(fkt_kernel kernel, int d, int R, uint64_t seed, double* 
 int fkt_solve(fkt_plan_t plan, double sigma2, const float* b, float* x, int nrhs, double tol, int max_iter,
               fkt_solve_info* info);
 
+/* fkt_solve with the solution returned in float64: x device [nrhs][N] float64 (output only).
+ * The CG iterates are float64 already; fkt_solve rounds them to float32, which by itself limits
+ * the true residual |b - (Ktilde + sigma2 I) x| / |b| to about |K| |x| 2^-24 / |b| (1e-4 to 1e-3
+ * for GP systems with sigma2 = 1e-2).  Here x keeps its float64 iterate, and
+ * info->true_rel_residual is recomputed with two products, Ktilde x = Ktilde hi + Ktilde lo
+ * (x = hi + lo, both float32), so that the rounding of x does not enter; what remains is the
+ * float32 arithmetic of the product itself.  Arguments, errors and synchronisation as for
+ * fkt_solve. */
+int fkt_solve_f64(fkt_plan_t plan, double sigma2, const float* b, double* x, int nrhs, double tol, int max_iter,
+                  fkt_solve_info* info);
+
 /* ---- Batches of independent problems (one product over all of them) ----
  * Each problem has its own points and kernel; all share d, p and theta.  The batch plan builds
  * every problem's tree, lists and expansion, then merges them into one arena so each stage of the
@@ -304,6 +315,14 @@ int fkt_autotune_leaf(const float* points, int64_t N, int d, fkt_kernel kernel, 
  *   "coarse_seed"  unsigned integer (default 1): seed of the coarse space's frequencies
  *   "near_targets_per_thread"  "2" (default) | "4"  register blocking of the near-field kernel
  *               (4 applies to one right-hand side; results are identical up to rounding order)
+ *   "wait_limit_cycles"  "default" | an integer 0..2000000000  limit, in SM clocks, of the
+ *               pipeline waits of the tensor-core near and far kernels (a source-record or
+ *               multipole copy landing, the hand-off of a chunk or entry to the MMA issuer).
+ *               The default (about one second) is reached only by a fault; a wait that runs out
+ *               stops that CTA's work, and fkt_check reports FKT_ERR_TIMEOUT.  A small value makes
+ *               the waits give up early on valid work: a test hook for the failure path (0 = a
+ *               single poll).  The waits that drain copies and MMAs in flight before a CTA exits
+ *               keep the default.
  * Errors: FKT_ERR_INVALID_ARG for an unknown key or value. */
 int fkt_set_option(fkt_plan_t plan, const char* key, const char* value);
 
@@ -339,10 +358,12 @@ int fkt_plan_lists(fkt_plan_t plan, int64_t* block_range, int64_t* far_off, int3
  * caching pool, where a raw cudaMalloc can fail or fragment memory the pool already holds.
  * This entry point computes exactly what fkt_mvm computes, with the same kernels, but takes
  * its work buffers from a fixed array in device memory that the library declares statically;
- * it calls no cudaMalloc, cudaFree or other allocating routine.  The paper has no counterpart:
- * this is a deployment variant of the same Algorithm 1 product.
+ * it calls no cudaMalloc, cudaFree or other allocating routine.  The paper has no counterpart;
+ * the result is the same product that fkt_mvm computes.
  *
  *   plan, w, y, nrhs  as for fkt_mvm (device buffers, [nrhs][N], 1 <= nrhs <= 64).
+ *   The device that was current at fkt_plan must be current at the call (FKT_ERR_INVALID_ARG
+ *   otherwise).
  *
  * Limits and behaviour:
  *   - The array holds FKT_NOALLOC_SCRATCH_BYTES (48 MiB) and is part of the library image:

@@ -20,9 +20,9 @@
  * Ytilde_k(u) = L_k^{-1} [C_k^alpha(u . v_i)]_i with G_k = [C_k^alpha(v_i . v_j)] = L_k L_k^T
  * for D_k = |H_k| given unit vectors v_i; it satisfies
  * sum_h Ytilde_kh(u) Ytilde_kh(v) = C_k^alpha(u . v), so Tbar is used without
- * the normalisation Z_k (reading R4).
+ * the normalisation Z_k (which the paper never gives).
  *
- * Tree contract (reading R6): bounding cube lo = min x, L = max extent;
+ * Tree contract (midpoint splits cycling the axes, Sec. 3.1 rules (a), (b)): bounding cube lo = min x, L = max extent;
  * q_a = min(floor((x_a - lo_a) * (2^B / L)), 2^B - 1) with B = floor(63/d);
  * Morton code interleaving bits from the top, axis 0 first; stable sort by
  * (code, index); a node at level l with more than leaf_size points splits at
@@ -60,7 +60,8 @@ static okernel mk_kernel(const double* kp) {
 static int kernel_singular(const okernel* k) { return k->kind == ORC_LAPLACE; }
 
 /* Kernel values (Table 1 of the paper, plus the Gaussian, Matern-5/2 and
- * Laplace kernels of the workloads; reading R15 for the parameterisations). */
+ * Laplace kernels of the workloads; Cauchy 1/(1 + r^2/l^2), rational quadratic
+ * (1 + r^2/(2 a l^2))^(-a)). */
 static double kernel_value(const okernel* k, double r) {
     double s = k->scale, l = k->ell;
     switch (k->kind) {
@@ -384,7 +385,7 @@ void orc_gegenbauer(double alpha, int n, double x, double* out) { gegenbauer(alp
 
 /* ------------------------------ dense MVM ------------------------------- */
 /* z[q][t] = sum_s K(|x_t - x_s|) w[q][s] over all sources (eq. nbody); a singular
- * kernel skips r = 0 pairs (reading R12). Targets are indices into X. */
+ * kernel skips r = 0 pairs (eq. nbody includes j = i; 1/r is singular there). Targets are indices into X. */
 int orc_dense(const float* X, int64_t N, int d, const double* kp, const double* W, int nrhs,
               const int64_t* targets, int64_t nt, double* out) {
     okernel ker = mk_kernel(kp);

@@ -14,10 +14,11 @@ derivation of the paper (Sec. A.2, "Derivation of the FKT expansion"):
   with the factor binom(n, 2n-j) that the binomial expansion in eq. prelemma
   carries.  The printed final formula omits it; with it the expansion
   reproduces the paper's Table 4 and collapses to the Legendre multipole for
-  1/r (Sec. 3.3, eq. electro).  This is reading R1 of the design notes.
-* The n-sum starts at m = 0 with B_{0,0} = 1 (reading R2), so the kernel value
-  itself (n = 0 term of eq. taylor) is kept.
-* The printed A_{k,i} denominator "(i-k)/2" is read as ((i-k)/2)! (reading R3).
+  1/r (Sec. 3.3, eq. electro); without it the error grows with p.
+* The n-sum starts at m = 0 with B_{0,0} = 1 (the theorem's printed sums start
+  at m = 1), so the kernel value itself (n = 0 term of eq. taylor) is kept.
+* The printed A_{k,i} denominator "(i-k)/2" is read as ((i-k)/2)!, which makes
+  eq. coschange hold for d = 3 and 4.
 """
 from __future__ import annotations
 
@@ -83,7 +84,7 @@ def Tbar(k: int, j: int, m: int, d: int) -> Fraction:
     K(|r'-r|) = sum_k C_k^alpha(cos g) sum_{j>=k} r'^j sum_{m=0}^j K^(m)(r) r^(m-j) Tbar_{k,j,m}
 
     Tbar_{k,j,m} = sum_{n=max((j+k)/2, m)}^{j} A_{k,2n-j} (-2)^(2n-j) binom(n, 2n-j) B_{n,m} / n!
-    (end of Sec. A.2, with the binomial of eq. prelemma kept -- reading R1).
+    (end of Sec. A.2, with the binomial of eq. prelemma kept, which the printed final formula omits).
     """
     if j < k or (j - k) % 2 or m < 0 or m > j:
         return Fraction(0)

@@ -83,6 +83,7 @@ int fkt_plan(const float* points, int64_t N, int d, fkt_kernel kernel, int p, in
     P->kernel = kernel;
     P->kp = fkt::make_kernel_params(kernel);
     P->stream = (cudaStream_t)cuda_stream;
+    if (cudaGetDevice(&P->device) != cudaSuccess) { free_plan(P); return FKT_ERR_CUDA; }
     int rc = fkt::build_far_tables(d, p, &P->tabs);
     if (rc) { free_plan(P); return rc; }
     {
@@ -168,7 +169,16 @@ int fkt_solve(fkt_plan_t plan, double sigma2, const float* b, float* x, int nrhs
     if (!plan || !b || !x || b == x || nrhs < 1 || nrhs > fkt::kMaxRhs || !(sigma2 > 0.0) || !isfinite(sigma2) ||
         !(tol > 0.0 && tol < 1.0) || max_iter < 1)
         return FKT_ERR_INVALID_ARG;
-    return fkt::solve(plan, sigma2, b, x, nrhs, tol, max_iter, info);
+    return fkt::solve(plan, sigma2, b, x, nullptr, nrhs, tol, max_iter, info);
+}
+
+int fkt_solve_f64(fkt_plan_t plan, double sigma2, const float* b, double* x, int nrhs, double tol, int max_iter,
+                  fkt_solve_info* info) {
+    if (info) memset(info, 0, sizeof(*info));
+    if (!plan || !b || !x || (const void*)b == (const void*)x || nrhs < 1 || nrhs > fkt::kMaxRhs ||
+        !(sigma2 > 0.0) || !isfinite(sigma2) || !(tol > 0.0 && tol < 1.0) || max_iter < 1)
+        return FKT_ERR_INVALID_ARG;
+    return fkt::solve(plan, sigma2, b, nullptr, x, nrhs, tol, max_iter, info);
 }
 
 int fkt_precond_learn(fkt_plan_t plan, double sigma2, const fkt_learn_opts* opts, fkt_learn_info* info) {
@@ -217,6 +227,17 @@ int fkt_set_option(fkt_plan_t plan, const char* key, const char* value) {
         } else {
             plan->coarse_seed = (uint64_t)v;
         }
+        return FKT_OK;
+    }
+    if (!strcmp(key, "wait_limit_cycles")) {
+        if (!strcmp(value, "default")) {
+            plan->wait_cycles = fkt::kWaitCycles;
+            return FKT_OK;
+        }
+        char* end = nullptr;
+        const long long v = strtoll(value, &end, 10);
+        if (!end || *end || end == value || v < 0 || v > fkt::kWaitCycles) return FKT_ERR_INVALID_ARG;
+        plan->wait_cycles = v;
         return FKT_OK;
     }
     if (!strcmp(key, "near_targets_per_thread")) {

@@ -309,6 +309,7 @@ int fkt_batch_plan(int nprob, const fkt_problem* probs, int d, int p, int leaf_s
         M->kernel = probs[0].kernel;
         M->kp = plans[0]->kp;
         M->stream = (cudaStream_t)cuda_stream;
+        M->device = plans[0]->device;
         if (fkt::create_far_stream(&M->stream2) != FKT_OK) rc = FKT_ERR_CUDA;
         for (auto& e : M->ev)
             if (!rc && cudaEventCreate(&e) != cudaSuccess) rc = FKT_ERR_CUDA;

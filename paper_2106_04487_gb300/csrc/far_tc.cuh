@@ -426,7 +426,7 @@ __global__ void __launch_bounds__(160, P <= 6 ? 4 : P <= 7 ? 3 : 2) far_tc2_kern
         int i = 0;
         for (; i < ne; ++i) {
             const int slot = i % ST;
-            ok = ptx::mbar_wait_bounded(&aready, (uint32_t)(i & 1), kWaitCycles) && !s_fail;
+            ok = ptx::mbar_wait_bounded(&aready, (uint32_t)(i & 1), a.wait_cycles) && !s_fail;
             if (!__all_sync(0xffffffffu, ok)) { ok = false; break; }
             if (lane == 0) {
                 tc::fence_after_sync();
@@ -482,7 +482,7 @@ __global__ void __launch_bounds__(160, P <= 6 ? 4 : P <= 7 ? 3 : 2) far_tc2_kern
         int i = 0;
         for (; i < ne; ++i) {
             const int slot = i % ST;
-            ok = ptx::mbar_wait_bounded(&full[slot], (uint32_t)((i / ST) & 1), kWaitCycles);
+            ok = ptx::mbar_wait_bounded(&full[slot], (uint32_t)((i / ST) & 1), a.wait_cycles);
             if (!__all_sync(0xffffffffu, ok) || s_fail) { ok = false; break; }
             // The MMAs of entry i-1 must be complete before this warp writes its A rows, flushes
             // or arrives for entry i; a busy warp waits only just before its first store, so the

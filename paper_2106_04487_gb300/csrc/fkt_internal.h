@@ -17,6 +17,7 @@ constexpr int kTB = 128;          // targets per target block (one CTA)
 constexpr int kMaskWords = kTB / 32;
 constexpr int kMaxRhs = 64;
 constexpr int kMaxTerms = 495;    // binom(8+4, 4); binom(10+3, 3) = 286
+constexpr long long kWaitCycles = 2000000000;  // ~1 s at 2 GHz: a device-side wait this long is a fault
 
 // Far-field coefficient tables handed to the kernels by value (they land in the
 // constant bank).  Index conventions:
@@ -57,6 +58,8 @@ struct fkt_plan_s {
     fkt::KernelParams kp{};
     fkt::FarTables tabs{};
     cudaStream_t stream = nullptr;
+    int device = 0;                // CUDA device that was current at fkt_plan (the plan's memory lives there)
+    long long wait_cycles = fkt::kWaitCycles;  // limit of the tensor-core kernels' pipeline waits (option)
     bool timing = false;
     int far_precision = fkt::FAR_FP32;
     int near_tpt = 2;              // near-field targets per thread (2 or 4)
@@ -194,7 +197,7 @@ int free_batch_arrays(fkt_plan_s* P);
 int precond_setup(fkt_plan_s* P, double sigma2);
 int precond_build(fkt_plan_s* P, double sigma2, const float* addV, int R, const float* addT, float* out);
 int precond_apply(fkt_plan_s* P, const float* r, const double* r64, float* z, int nrhs);
-int solve(fkt_plan_s* P, double sigma2, const float* b, float* x, int nrhs, double tol, int max_iter,
+int solve(fkt_plan_s* P, double sigma2, const float* b, float* x, double* x64, int nrhs, double tol, int max_iter,
           fkt_solve_info* info);
 void free_solve(fkt_plan_s* P);
 

@@ -237,6 +237,10 @@ struct MvmArgs {
     const int32_t* blk_prob;   // problem of each target block
     const int32_t* blk_list;   // grid index -> target block (work ordered largest first)
     const float* pt_sig;       // near-field coordinate scale of each point's problem
+    // limit, in SM clocks, of the pipeline waits of the tensor-core kernels (record / multipole
+    // copies landing, the consumers' hand-off to the MMA issuer); the waits that drain work in
+    // flight before a CTA exits always use kWaitCycles
+    long long wait_cycles;
 };
 
 // Target block handled by this CTA and its kernel parameters (per problem in a batch).

@@ -123,6 +123,7 @@ MvmArgs base_args(fkt_plan_s* P) {
     a.blk_prob = P->blk_prob;
     a.blk_list = nullptr;
     a.pt_sig = P->pt_sig;
+    a.wait_cycles = P->wait_cycles;
     return a;
 }
 

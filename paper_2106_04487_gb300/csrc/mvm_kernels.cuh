@@ -207,7 +207,6 @@ __device__ __forceinline__ float kval(float q, const KernelParams& kp) {
     }
 }
 
-constexpr long long kWaitCycles = 2000000000;  // ~1 s at 2 GHz: a wait this long is a fault
 
 // T targets per thread (128 / T threads per 128-target block); ST-stage ring of CH-point chunks.
 // Thread tl owns targets tl + (128 / T) j, so the targets of slot j of one warp form one

@@ -311,7 +311,7 @@ __global__ void __launch_bounds__(NearTcShape::THREADS, 4) near_tc_kernel(MvmArg
             settle();
         }
         for (int s = 0; s < ST; ++s) produce();
-        int waited_mma = 0;
+        int waited_mma = 0, committed = 0;
         for (int c = 0; c < nch; ++c) {
             const int slot = c % ST;
             ptx::named_sync(kBarReady, kBarThreads);
@@ -329,7 +329,8 @@ __global__ void __launch_bounds__(NearTcShape::THREADS, 4) near_tc_kernel(MvmArg
                     tc::mma_tf32_ts_masked(tmem, alo, bh, IDESC, off);
                 }
                 tc::commit(&mma_done);
-                if (ptx::mbar_wait_bounded(&mma_done, (uint32_t)(c & 1), kWaitCycles)) waited_mma = c + 1;
+                ++committed;
+                if (ptx::mbar_wait_bounded(&mma_done, (uint32_t)((committed - 1) & 1), kWaitCycles)) waited_mma = committed;
                 else s_fail = 1;
                 tc::fence_before_sync();
             }
@@ -347,7 +348,7 @@ __global__ void __launch_bounds__(NearTcShape::THREADS, 4) near_tc_kernel(MvmArg
             // the last copy of each stage may still be in flight; then the last MMAs
             for (int j = issued > ST ? issued - ST : 0; j < issued; ++j)
                 ptx::mbar_wait_bounded(&full[j % ST], (uint32_t)((j / ST) & 1), kWaitCycles);
-            if (waited_mma < nch) ptx::mbar_wait_bounded(&mma_done, (uint32_t)(waited_mma & 1), kWaitCycles);
+            if (waited_mma < committed) ptx::mbar_wait_bounded(&mma_done, (uint32_t)(waited_mma & 1), kWaitCycles);
         }
     } else {
         // ---------------------------------------------------------------- consumers
@@ -377,7 +378,7 @@ __global__ void __launch_bounds__(NearTcShape::THREADS, 4) near_tc_kernel(MvmArg
         bool dirty = false;  // this warp's accumulator rows hold products not yet added to acc
         for (int c = 0; c < nch; ++c) {
             const int slot = c % ST;
-            const bool got = ptx::mbar_wait_bounded(&full[slot], (uint32_t)((c / ST) & 1), kWaitCycles);
+            const bool got = ptx::mbar_wait_bounded(&full[slot], (uint32_t)((c / ST) & 1), a.wait_cycles);
             if (!__all_sync(0xffffffffu, got)) s_fail = 1;
             const int n = info[slot].n;
             const uint32_t mword = s_fail ? 0u : info[slot].on[warp];

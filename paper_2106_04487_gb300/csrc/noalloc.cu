@@ -19,10 +19,14 @@ constexpr int kMaxDevices = 64;
 std::mutex g_setup_mutex;
 float* g_scratch_ptr[kMaxDevices] = {};
 
-// Device address of the scratch on the current device, looked up once per device.
-int scratch_for_current_device(float** out) {
+// Device address of the scratch on the plan's device, looked up once per device.  That device
+// must be the current one: the symbol lookup and the kernels both act on the current device, so
+// a call made while another device is current is rejected instead of handing the plan's kernels
+// another device's address.
+int scratch_for_plan_device(const fkt_plan_s* P, float** out) {
     int dev = 0;
     FKT_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev != P->device) return FKT_ERR_INVALID_ARG;
     if (dev < 0 || dev >= kMaxDevices) return FKT_ERR_UNSUPPORTED;
     std::lock_guard<std::mutex> lock(g_setup_mutex);
     if (!g_scratch_ptr[dev]) {
@@ -50,7 +54,7 @@ extern "C" int fkt_mvm_noalloc(fkt_plan_t plan, const float* w, float* y, int nr
     for (size_t v : f) total += v;
     if (total > kScratchFloats) return FKT_ERR_SCRATCH_LIMIT;
     float* base = nullptr;
-    int rc = scratch_for_current_device(&base);
+    int rc = scratch_for_plan_device(plan, &base);
     if (rc) return rc;
     float* q = base;
     MvmBuffers B{};

@@ -118,6 +118,7 @@ __device__ __forceinline__ bool mbar_try_wait_hint(uint64_t* bar, uint32_t parit
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, long long max_cycles,
                                                   uint32_t max_sleep_ns = 0) {
     if (mbar_try_wait(bar, parity)) return true;
+    if (max_cycles <= 0) return false;  // a limit of 0: one poll only
     const long long t0 = clock64();
     uint32_t ns = 32;
     for (;;) {

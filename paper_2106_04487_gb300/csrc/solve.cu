@@ -228,15 +228,25 @@ __global__ void cg_to_float_kernel(int64_t n, const double* __restrict__ a, floa
         b[i] = (float)a[i];
 }
 
-// true residual: rr = |b - (q + sigma2 x)|^2 with q = Ktilde x
+// x = hi + lo: hi = x rounded to float32, lo = the float32 rounding of the remainder
+__global__ void cg_split_kernel(int64_t n, const double* __restrict__ x, float* __restrict__ hi, float* __restrict__ lo) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const float h = (float)x[i];
+        hi[i] = h;
+        lo[i] = (float)(x[i] - (double)h);
+    }
+}
+
+// true residual: rr = |b - (q + q2 + sigma2 x)|^2 with q (+ q2) = Ktilde x (q2 may be null)
 __global__ void cg_true_residual_kernel(int64_t N, float sigma2, const float* __restrict__ b,
                                         const double* __restrict__ x, const float* __restrict__ q,
-                                        double* __restrict__ dst) {
+                                        const float* __restrict__ q2, double* __restrict__ dst) {
     const int rh = blockIdx.y;
     double s = 0.0;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
         const int64_t k = rh * N + i;
-        const double v = (double)b[k] - ((double)q[k] + (double)sigma2 * x[k]);
+        const double kx = (double)q[k] + (q2 ? (double)q2[k] : 0.0);
+        const double v = (double)b[k] - (kx + (double)sigma2 * x[k]);
         s += v * v;
     }
     block_add(s, &dst[rh]);
@@ -312,18 +322,18 @@ int precond_apply(fkt_plan_s* P, const float* r, const double* r64, float* z, in
     return FKT_OK;
 }
 
-static int solve_once(fkt_plan_s* P, double sigma2, const float* b, float* x, int nrhs, double tol, int max_iter,
-                      fkt_solve_info* info);
+static int solve_once(fkt_plan_s* P, double sigma2, const float* b, float* x, double* x64, int nrhs, double tol,
+                      int max_iter, fkt_solve_info* info);
 
 // With the learned correction, a run that does not converge is repeated with plain block-Jacobi.
-int solve(fkt_plan_s* P, double sigma2, const float* b, float* x, int nrhs, double tol, int max_iter,
+int solve(fkt_plan_s* P, double sigma2, const float* b, float* x, double* x64, int nrhs, double tol, int max_iter,
           fkt_solve_info* info) {
-    if (P->pc_mode != 2) return solve_once(P, sigma2, b, x, nrhs, tol, max_iter, info);
+    if (P->pc_mode != 2) return solve_once(P, sigma2, b, x, x64, nrhs, tol, max_iter, info);
     if (!P->pc_learned || P->pc_learned_sigma2 != sigma2) return FKT_ERR_INVALID_ARG;
-    int rc = solve_once(P, sigma2, b, x, nrhs, tol, max_iter, info);
+    int rc = solve_once(P, sigma2, b, x, x64, nrhs, tol, max_iter, info);
     if (rc != FKT_ERR_NOT_CONVERGED) return rc;
     P->pc_mode = 1;
-    rc = solve_once(P, sigma2, b, x, nrhs, tol, max_iter, info);
+    rc = solve_once(P, sigma2, b, x, x64, nrhs, tol, max_iter, info);
     P->pc_mode = 2;
     if (info) info->used_fallback = 1;
     return rc;
@@ -334,8 +344,9 @@ static int apply_pc(fkt_plan_s* P, const double* r64, float* z, int nrhs) {
     return P->coarse_rank > 0 ? coarse_apply(P, r64, z, nrhs) : precond_apply(P, nullptr, r64, z, nrhs);
 }
 
-static int solve_once(fkt_plan_s* P, double sigma2, const float* b, float* x, int nrhs, double tol, int max_iter,
-                      fkt_solve_info* info) {
+// x (float32) or x64 (float64): exactly one is non-null.
+static int solve_once(fkt_plan_s* P, double sigma2, const float* b, float* x, double* x64, int nrhs, double tol,
+                      int max_iter, fkt_solve_info* info) {
     int rc = P->pc_mode ? precond_setup(P, sigma2) : FKT_OK;
     if (rc) return rc;
     if (P->coarse_rank > 0 && (rc = coarse_setup(P, sigma2))) return rc;
@@ -406,11 +417,20 @@ static int solve_once(fkt_plan_s* P, double sigma2, const float* b, float* x, in
             if (all_conv) break;
         }
     }
-    // x to float32, true residual with one more product
-    cg_to_float_kernel<<<grid.x * nrhs, 256, 0, st>>>((int64_t)nrhs * N, P->cg_x, x);
-    if ((rc = launch_mvm(P, x, P->cg_q, nrhs))) return rc;
+    // the solution, and its true residual with one more product (float32 x), or two (float64 x:
+    // Ktilde x = Ktilde hi + Ktilde lo, so the rounding of x to float32 does not enter)
     FKT_CUDA_TRY(cudaMemsetAsync(sc + kRr * kMaxRhs, 0, sizeof(double) * kMaxRhs, st));
-    cg_true_residual_kernel<<<grid, 256, 0, st>>>(N, s2, b, P->cg_x, P->cg_q, sc + kRr * kMaxRhs);
+    if (x64) {
+        FKT_CUDA_TRY(cudaMemcpyAsync(x64, P->cg_x, sizeof(double) * (size_t)nrhs * N, cudaMemcpyDeviceToDevice, st));
+        cg_split_kernel<<<grid.x * nrhs, 256, 0, st>>>((int64_t)nrhs * N, P->cg_x, P->cg_z, P->cg_p);
+        if ((rc = launch_mvm(P, P->cg_z, P->cg_q, nrhs))) return rc;
+        if ((rc = launch_mvm(P, P->cg_p, P->cg_z, nrhs))) return rc;
+        cg_true_residual_kernel<<<grid, 256, 0, st>>>(N, s2, b, P->cg_x, P->cg_q, P->cg_z, sc + kRr * kMaxRhs);
+    } else {
+        cg_to_float_kernel<<<grid.x * nrhs, 256, 0, st>>>((int64_t)nrhs * N, P->cg_x, x);
+        if ((rc = launch_mvm(P, x, P->cg_q, nrhs))) return rc;
+        cg_true_residual_kernel<<<grid, 256, 0, st>>>(N, s2, b, P->cg_x, P->cg_q, nullptr, sc + kRr * kMaxRhs);
+    }
     FKT_CUDA_TRY(cudaGetLastError());
     FKT_CUDA_TRY(cudaMemcpyAsync(host.data(), sc, sizeof(double) * 8 * kMaxRhs, cudaMemcpyDeviceToHost, st));
     FKT_CUDA_TRY(cudaStreamSynchronize(st));

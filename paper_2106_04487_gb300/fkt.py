@@ -24,7 +24,7 @@ KERNELS = {"gaussian": 0, "exponential": 1, "matern32": 2, "matern52": 3, "cauch
 # Every entry point declared in include/fkt.h.
 EXPORTS = ["fkt_plan", "fkt_mvm", "fkt_mvm_host", "fkt_dense_mvm", "fkt_set_option", "fkt_plan_stats",
            "fkt_plan_tree", "fkt_plan_lists", "fkt_destroy", "fkt_error_string", "fkt_mvm_noalloc",
-           "fkt_check", "fkt_precond_setup", "fkt_precond_apply", "fkt_solve", "fkt_batch_plan", "fkt_batch_mvm",
+           "fkt_check", "fkt_precond_setup", "fkt_precond_apply", "fkt_solve", "fkt_solve_f64", "fkt_batch_plan", "fkt_batch_mvm",
            "fkt_batch_set_option", "fkt_batch_info", "fkt_batch_check", "fkt_batch_destroy", "fkt_autotune_leaf",
            "fkt_precond_learn", "fkt_learn_params", "fkt_learn_eval", "fkt_learn_teacher", "fkt_spectral_sample"]
 
@@ -111,6 +111,7 @@ def lib() -> ctypes.CDLL:
     L.fkt_precond_apply.argtypes = [vp, vp, vp, ctypes.c_int]
     L.fkt_solve.argtypes = [vp, ctypes.c_double, vp, vp, ctypes.c_int, ctypes.c_double, ctypes.c_int,
                             ctypes.POINTER(fkt_solve_info)]
+    L.fkt_solve_f64.argtypes = L.fkt_solve.argtypes
     L.fkt_spectral_sample.argtypes = [fkt_kernel, ctypes.c_int, ctypes.c_int, ctypes.c_uint64, vp, vp]
     L.fkt_destroy.argtypes = [vp]
     L.fkt_destroy.restype = None
@@ -192,11 +193,14 @@ def fkt_precond_apply(plan, r, z, nrhs: int):
     _check(lib().fkt_precond_apply(plan, _ptr(r), _ptr(z), nrhs), "fkt_precond_apply")
 
 
-def fkt_solve(plan, sigma2: float, b, x, nrhs: int, tol: float, max_iter: int, raise_on_not_converged=True) -> dict:
+def fkt_solve(plan, sigma2: float, b, x, nrhs: int, tol: float, max_iter: int, raise_on_not_converged=True,
+              f64: bool = False) -> dict:
+    """fkt_solve (x float32) or fkt_solve_f64 (x float64)."""
     info = fkt_solve_info()
-    st = lib().fkt_solve(plan, float(sigma2), _ptr(b), _ptr(x), nrhs, float(tol), int(max_iter), ctypes.byref(info))
+    fn = lib().fkt_solve_f64 if f64 else lib().fkt_solve
+    st = fn(plan, float(sigma2), _ptr(b), _ptr(x), nrhs, float(tol), int(max_iter), ctypes.byref(info))
     if st != FKT_OK and not (st == FKT_ERR_NOT_CONVERGED and not raise_on_not_converged):
-        raise FktError(st, "fkt_solve")
+        raise FktError(st, "fkt_solve_f64" if f64 else "fkt_solve")
     out = {k: getattr(info, k) for k, _ in fkt_solve_info._fields_ if k != "pad"}
     out["status"] = st
     return out
@@ -289,14 +293,16 @@ class Plan:
     def check(self):
         fkt_check(self.h)
 
-    def solve(self, sigma2: float, b, tol: float = 1e-6, max_iter: int = 1000, raise_on_not_converged=True):
-        """x with (Ktilde + sigma2 I) x = b by preconditioned CG; returns (x, info dict)."""
+    def solve(self, sigma2: float, b, tol: float = 1e-6, max_iter: int = 1000, raise_on_not_converged=True,
+              f64: bool = False):
+        """x with (Ktilde + sigma2 I) x = b by preconditioned CG; returns (x, info dict).
+        f64: x in float64 (fkt_solve_f64), otherwise float32."""
         import torch
 
         b2 = b if b.dim() == 2 else b[None]
         b2 = b2.to(device="cuda", dtype=torch.float32).contiguous()
-        x = torch.empty_like(b2)
-        info = fkt_solve(self.h, sigma2, b2, x, b2.shape[0], tol, max_iter, raise_on_not_converged)
+        x = torch.empty(b2.shape, dtype=torch.float64 if f64 else torch.float32, device=b2.device)
+        info = fkt_solve(self.h, sigma2, b2, x, b2.shape[0], tol, max_iter, raise_on_not_converged, f64)
         return (x if b.dim() == 2 else x[0]), info
 
     def learn_precond(self, sigma2: float, rank=8, hidden=32, steps=300, lr=3e-3, train_blocks=512, seed=1,

@@ -20,7 +20,7 @@ def L():
 def _declared():
     txt = open(os.path.join(ROOT, "include", "fkt.h")).read()
     txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
-    return sorted(set(re.findall(r"\b(fkt_[a-z_]+)\s*\(", txt)))
+    return sorted(set(re.findall(r"\b(fkt_[a-z0-9_]+)\s*\(", txt)))
 
 
 def test_header_declares_the_boundary():

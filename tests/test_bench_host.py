@@ -116,3 +116,38 @@ def test_reference_arm_line(monkeypatch):
     assert out["cpu_baseline"]["value"] == out["value"]
     assert out["e2e"] == {"value": out["value"], "unit": "MVM/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
     assert out["config"]["workload"].startswith("gaussian l=0.1 d=3 N=3000")
+    # what was timed: steps x ms_per_step is the elapsed time of the timed steps
+    assert abs(out["steps"] * out["ms_per_step"] / 1e3 - out["config"]["timed_s"]) < 1e-6
+    # N = 3000 <= the per-step target sample: every step is a whole product, so the measured
+    # rate and the full-product extrapolation agree up to timing noise
+    assert 0.5 < out["config"]["extrapolated_value"] / out["value"] < 2.0
+    assert out["metric"] == bench.metric_name("gauss20k")
+
+
+def test_metric_names_match_the_benchmark():
+    """Both arms print the same metric string; the headline one is the benchmark's own."""
+    import json
+    import os
+
+    with open(os.path.join(os.path.dirname(bench.__file__), "BASELINE.json")) as fh:
+        assert bench.metric_name("matern1m") == json.load(fh)["metric"]
+    assert len({bench.metric_name(w) for w in bench.WORKLOADS}) == len(bench.WORKLOADS)
+
+
+def test_oracle_step_accounting():
+    """oracle_steps on stand-in runners with known times: value counts only the outputs produced."""
+    import time
+
+    class R:
+        n, nrhs = 1000, 4
+
+        def step(self, W, T, seed=5):
+            time.sleep(0.01)
+            return 0.004, 0.006
+
+    rec = bench.oracle_steps([(R(), None, 100)], steps=3, warmup=0, units_full=4, n_total=1000)
+    assert rec["targets_per_step"] == 100
+    # 3 steps x 4 MVMs x 100/1000 of the outputs = 1.2 MVM-equivalents in about 0.03 s
+    assert 1.2 / (3 * 0.02) < rec["value"] < 1.2 / (3 * 0.0099)
+    # full product: s2m 0.004 s + traversal 0.006 s x 10
+    assert abs(rec["extrapolated_value"] - 4 / 0.064) < 1e-9

@@ -11,6 +11,7 @@ library runs them in, checked on sampled targets the float64 oracle evaluates on
 import numpy as np
 import pytest
 
+from bars import assert_bars, rel_2norm, rel_elementwise
 from paper_2106_04487_gb300 import inputs
 
 pytestmark = pytest.mark.gpu
@@ -56,9 +57,11 @@ def test_batch_256_problems_full_size(fkt, orc, prec, tol):
         F = orc.FKT(X, orc.kparams(kname, ell, alpha=alpha, scale=scale), p=4, leaf_size=512, theta=0.5)
         idx = inputs.subsample(hi - lo, 150, seed=7 + i)
         z = F.mvm(W[:, lo:hi], idx)
-        err = _rel_rows(Y[:, lo + idx], z)
-        print(f"problem {i} ({kname}, N={hi - lo}) {prec}: rel err vs oracle on {len(idx)} targets {err:.2e}")
+        err, einf = rel_2norm(Y[:, lo + idx], z), rel_elementwise(Y[:, lo + idx], z)
+        print(f"problem {i} ({kname}, N={hi - lo}) {prec}: rel err vs oracle on {len(idx)} targets {err:.2e}, "
+              f"element-wise {einf:.2e}")
         assert err < tol, (i, kname, hi - lo, err)
+        assert einf < tol, (i, kname, hi - lo, einf)
 
 
 @pytest.fixture(scope="module")
@@ -94,6 +97,6 @@ def test_laplace_16m_sampled(fkt, laplace16m, prec, tol):
     plan.set_option("far_precision", prec)
     y = plan.mvm(torch.from_numpy(W).cuda()).cpu().numpy().astype(np.float64)
     plan.check()
-    err = _rel_rows(y[:, idx], z)
-    print(f"laplace 16M {prec}: rel err vs oracle FKT {err:.2e}, vs float64 direct sum {_rel_rows(y[:, idx], zd):.2e}")
-    assert err < tol, err
+    err, einf = assert_bars(y[:, idx], z, tol, f"laplace 16M {prec}")
+    print(f"laplace 16M {prec}: rel err vs oracle FKT {err:.2e} (element-wise {einf:.2e}), "
+          f"vs float64 direct sum {_rel_rows(y[:, idx], zd):.2e}")

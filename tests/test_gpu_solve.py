@@ -2,7 +2,7 @@
 
 The solution is judged by residuals in float64 against operators the oracle defines: the
 dense kernel matrix (eq. nbody) where theta -> 0 makes the FKT exact, and the oracle FKT
-otherwise (reading R13: Ktilde is only approximately symmetric, so the true residual is the
+otherwise (Ktilde is only approximately symmetric, so the true residual is the
 judge).  The block-Jacobi blocks are checked against float64 dense solves of the same blocks.
 
 Bar: the products run in float32 and x is returned in float32, so for these ill-conditioned
@@ -69,6 +69,33 @@ def test_solve_dense_limit(fkt, orc):
     assert info["converged"] == 1
     assert res.max() < 3e-4, (res, info)
     assert info["true_rel_residual"] < 3e-4, info
+
+
+def test_solve_f64_dense_limit(fkt, orc):
+    """fkt_solve_f64: the same dense-limit system with x returned in float64.  Without the rounding
+    of x to float32 the float64 residual falls below the float32 floor of fkt_solve (about 1e-4
+    here) and is limited by the float32 arithmetic of the products CG used; the library's own
+    two-product true residual agrees with the float64 dense one."""
+    import torch
+
+    X = inputs.gaussian_mixture(2000, 4, 20, 0.05, seed=32)
+    b = inputs.normal_weights(2000, 4, seed=33)
+    sigma2 = 1e-2
+    plan = fkt.Plan(torch.from_numpy(X).cuda(), "matern52", lengthscale=0.3, p=4, leaf_size=128, theta=1e-6)
+    x32, _ = plan.solve(sigma2, torch.from_numpy(b).cuda(), tol=1e-7, max_iter=3000, raise_on_not_converged=False)
+    x, info = plan.solve(sigma2, torch.from_numpy(b).cuda(), tol=1e-7, max_iter=3000, raise_on_not_converged=False,
+                         f64=True)
+    assert x.dtype == torch.float64
+    x = x.cpu().numpy()
+    kp = orc.kparams("matern52", 0.3)
+    res = np.linalg.norm(b - (orc.dense(X, kp, x) + sigma2 * x), axis=1) / np.linalg.norm(b, axis=1)
+    x32 = x32.cpu().numpy().astype(np.float64)
+    res32 = np.linalg.norm(b - (orc.dense(X, kp, x32) + sigma2 * x32), axis=1) / np.linalg.norm(b, axis=1)
+    print(f"float64 residual of x: f64 {res.max():.2e} (library {info['true_rel_residual']:.2e}), "
+          f"f32 {res32.max():.2e}; iterations {info['iterations']}")
+    assert res.max() < 3e-5, (res, info)
+    assert res.max() < 0.5 * res32.max()
+    assert abs(info["true_rel_residual"] - res.max()) < 0.5 * res.max() + 2e-6, info
 
 
 def test_solve_against_oracle_fkt_operator(fkt, orc):

@@ -14,7 +14,7 @@ def small(orc):
 
 
 def test_tree_invariants(small):
-    """Contract of Sec. 3.1 (reading R6): children partition the parent's range at a code bit,
+    """Contract of Sec. 3.1 (midpoint splits cycling the axes): children partition the parent's range at a code bit,
     leaves hold <= leaf_size points, codes sorted, centres are box midpoints, rho2 is the max."""
     X, kp, F = small
     t = F.tree()
@@ -132,7 +132,7 @@ def test_fkt_subsample_matches_full(orc, small):
 
 def test_duplicate_points_and_max_depth(orc):
     """Exact duplicates cannot be separated: the leaf at level d*B may exceed leaf_size;
-    the singular kernel skips r = 0 pairs (reading R12)."""
+    the singular kernel skips r = 0 pairs."""
     X = np.repeat(inputs.uniform_cube(30, 3, seed=9), 20, axis=0)
     w = inputs.normal_weights(len(X))
     for kname in ("laplace", "cauchy"):

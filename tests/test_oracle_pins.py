@@ -17,7 +17,7 @@ from oracle import tables
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 
-# Table 4 kernels in the oracle's parameterisation (reading R15):
+# Table 4 kernels in the oracle's parameterisation:
 #   e^{-r}: exponential, l = 1;  (1+r^2)^{-1}: cauchy, l = 1;  e^{-r^2}: gaussian, l = 1/sqrt(2)
 TABLE4_KERNELS = {"exp": ("exponential", 1.0), "cauchy": ("cauchy", 1.0), "gauss": ("gaussian", 1.0 / math.sqrt(2.0))}
 
@@ -48,8 +48,8 @@ def test_table4_max_abs_error(orc, row):
     """Max |K - K_p| over 1000 random pairs, |r'|=1, |r|=2 (Table 4).
 
     The paper's value is a maximum over its own random sample, so we accept a
-    factor 1.5 either way (reading R16); dropping the binomial of eq. prelemma
-    (reading R1) makes the error grow with p and fails this by orders of magnitude.
+    factor 1.5 either way (the printed maximum over random pairs depends on the draw); dropping the binomial of eq. prelemma
+    makes the error grow with p and fails this by orders of magnitude.
     """
     name, d, p, ref = row
     kname, ell = TABLE4_KERNELS[name]
@@ -118,7 +118,7 @@ def test_inverse_distance_collapses_to_legendre_multipole():
 
 
 def test_tbar_zero_order_and_parity():
-    """Tbar_{0,0,0} = 1 (the n = 0 term of eq. taylor, reading R2); Tbar vanishes unless j = k mod 2."""
+    """Tbar_{0,0,0} = 1 (the n = 0 term of eq. taylor); Tbar vanishes unless j = k mod 2."""
     for d in (3, 4):
         assert tables.Tbar(0, 0, 0, d) == 1
         for k in range(6):
@@ -268,7 +268,7 @@ def _taylor_poly_in_source(name, x, xp, p, ell, alpha, rad=0.5, nodes=256):
                                             ("laplace", 1.0, 1.0)])
 def test_truncation_is_total_degree_taylor_polynomial(orc, d, name, ell, alpha):
     """The order-p truncation (eq. finaltrunc, j <= p) equals the Taylor polynomial of total
-    degree p in the source offset (reading R8), computed here without any of the paper's
+    degree p in the source offset (each term is a homogeneous polynomial of degree j in it), computed here without any of the paper's
     tables, harmonics or jets.  Catches a dropped term, a wrong sign or index in Tbar,
     in the jets or in the harmonic basis."""
     p = 6

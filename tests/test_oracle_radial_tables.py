@@ -8,7 +8,7 @@ is E(r) times a polynomial in r' and r (Theorem 3.1 with the tables of oracle/ta
 smallest number of separable terms F(r) G(r') is the rank of its coefficient matrix (rows: powers
 of r', columns: powers of r), computed here exactly over the rationals.  Table 3 prints that rank
 for eight kernels in d = 3..9; "-" means no compression (full rank).  The binomial factor of
-reading R1, the m = 0 term of reading R2 and every sign of the tables enter these ranks: dropping
+eq. prelemma, the m = 0 term of the n-sum and every sign of the tables enter these ranks: dropping
 either or flipping the m = 1 sign changes them (checked below).
 """
 import os
@@ -115,13 +115,13 @@ def test_table3_rows_not_reproduced_are_full_rank():
 
 
 def test_table3_catches_planted_table_mistakes():
-    def no_binomial(k, j, m, d):          # the printed final formula, without reading R1
+    def no_binomial(k, j, m, d):          # the printed final formula, without the binomial
         if j < k or (j - k) % 2 or m < 0 or m > j:
             return Fraction(0)
         return sum((T.A(k, 2 * n - j, d) * Fraction(-2) ** (2 * n - j) * T.B(n, m) / factorial(n)
                     for n in range(max((j + k) // 2, m), j + 1)), Fraction(0))
 
-    def no_m0(k, j, m, d):                # the sums of Theorem 3.1 as printed, from m = 1 (reading R2)
+    def no_m0(k, j, m, d):                # the sums of Theorem 3.1 as printed, from m = 1
         return Fraction(0) if m == 0 else T.Tbar(k, j, m, d)
 
     def flipped(k, j, m, d):
@@ -173,7 +173,7 @@ def test_exp_decomp_worked_example(k):
 
 
 def test_exp_decomp_catches_the_printed_tbar_formula():
-    """Without the binomial of reading R1 the k = 1 radial part no longer matches the worked example."""
+    """Without the binomial of eq. prelemma the k = 1 radial part no longer matches the worked example."""
     def no_binomial(k, j, m, d):
         if j < k or (j - k) % 2 or m < 0 or m > j:
             return Fraction(0)

@@ -33,12 +33,15 @@ def _rel(a, b):
     return max(np.linalg.norm(a[i] - b[i]) / np.linalg.norm(b[i]) for i in range(len(b)))
 
 
-@pytest.mark.parametrize("nrhs", [1, 11])
-def test_noalloc_matches_fkt_mvm_on_two_calls(fkt, nrhs):
+@pytest.mark.parametrize("far_precision,nrhs", [("fp32", 1), ("fp32", 11), ("bf16x3", 11), ("bf16x3", 3)])
+def test_noalloc_matches_fkt_mvm_on_two_calls(fkt, far_precision, nrhs):
+    """Both far-field paths: float32 on the CUDA cores, and the tensor-core path whose packed
+    multipole image is also carved out of the scratch; nrhs 3 and 11 leave partial groups of 8."""
     import torch
 
     X = torch.from_numpy(inputs.gaussian_mixture(60000, 3, 10, 0.05, seed=21)).cuda()
     plan = fkt.Plan(X, "matern32", lengthscale=0.2, p=6, leaf_size=256, theta=0.5)
+    plan.set_option("far_precision", far_precision)
     for call, seed in enumerate((22, 23)):          # two calls in a row share the scratch
         w = torch.from_numpy(inputs.normal_weights(60000, nrhs, seed=seed)).cuda()
         want = plan.mvm(w).cpu().numpy()             # the existing entry point
@@ -48,6 +51,35 @@ def test_noalloc_matches_fkt_mvm_on_two_calls(fkt, nrhs):
         got = got.cpu().numpy()
         assert np.isfinite(got).all(), call
         assert _rel(got, want) < TOL, call
+    plan.close()
+
+
+@pytest.mark.parametrize("far_precision", ["fp32", "bf16x3"])
+def test_noalloc_call_allocates_no_device_memory(fkt, far_precision):
+    """The defining property: on a fresh plan (none of fkt_mvm's work buffers exist yet) a call
+    leaves the device's free memory unchanged.  A warm-up call on another plan first loads the
+    kernels and the scratch array itself (module loading, not the call's own allocation)."""
+    import torch
+
+    X = torch.from_numpy(inputs.gaussian_mixture(60000, 3, 10, 0.05, seed=31)).cuda()
+    w = torch.from_numpy(inputs.normal_weights(60000, 11, seed=32)).cuda()
+    y = torch.empty_like(w)
+    warm = fkt.Plan(X, "matern32", lengthscale=0.2, p=6, leaf_size=256, theta=0.5)
+    warm.set_option("far_precision", far_precision)
+    fkt.fkt_mvm_noalloc(warm.h, w, y, 11)
+    torch.cuda.synchronize()
+    want = y.cpu().numpy()
+    warm.close()
+    plan = fkt.Plan(X, "matern32", lengthscale=0.2, p=6, leaf_size=256, theta=0.5)
+    plan.set_option("far_precision", far_precision)
+    y.fill_(float("nan"))
+    torch.cuda.synchronize()
+    free_before, _ = torch.cuda.mem_get_info()
+    fkt.fkt_mvm_noalloc(plan.h, w, y, 11)
+    torch.cuda.synchronize()
+    free_after, _ = torch.cuda.mem_get_info()
+    assert free_after == free_before, (free_before, free_after)
+    assert _rel(y.cpu().numpy(), want) < TOL
     plan.close()
 
 
