@@ -100,11 +100,14 @@ def near_kernel_name(kname: str, nw: int, near_precision: str = "fp32") -> str:
     return f"{base}<3,{kname},{nw}>"
 
 
-def far_kernel_name(p: int, far_precision: str, nrhs: int) -> str:
+def far_kernel_name(p: int, far_precision: str, nrhs: int, far_kernel: str = "single") -> str:
     if far_precision == "fp32":
         return f"far_kernel<3,{p},1>" if nrhs == 1 else f"far_mr_kernel<3,{p}>"
     if far_precision == "tf32":
         return f"far_tc_kernel<3,{p},tf32>"
+    pairs_ok = p <= (6 if far_precision == "bf16x3" else 9)  # two A buffers fit 256 tensor-memory columns
+    if far_kernel == "pairs" and pairs_ok:
+        return f"far_tc3_kernel<{p},{far_precision}>"
     return f"far_tc2_kernel<{p},{far_precision}>"
 
 
@@ -162,6 +165,8 @@ def parse():
     ap.add_argument("--far-precision", default=None, choices=["bf16x3", "tf32", "bf16", "fp32"])
     ap.add_argument("--near-precision", default=None, choices=["tf32x3", "fp32"],
                     help="near-field contraction of 32-wide passes: tensor cores (TF32 hi/lo) or CUDA cores")
+    ap.add_argument("--far-kernel", default="single", choices=["pairs", "single"],
+                    help="tensor-core far field (d = 3, BF16 forms): two far entries per thread or one")
     ap.add_argument("--compare", default="fp32", choices=["fp32", "none"],
                     help="plain float32 form (near and far on the CUDA cores) timed beside the headline one")
     ap.add_argument("--second-kernel", default="cauchy", choices=list(KERNELS) + ["none"],
@@ -342,7 +347,7 @@ def rooflines(a, stats, head, nsm, peaks, src, kname, passes):
         ops = far_pair_ops(a.p)
         far_peak = nsm * sm_max * 1e6 * FP32_LANES / ops
         far_ach = stats["far_pairs"] / (head["far_ms"] / 1e3)
-        far_name = far_kernel_name(a.p, a.far_precision, a.nrhs)
+        far_name = far_kernel_name(a.p, a.far_precision, a.nrhs, a.far_kernel)
         roof = {"kernel": far_name, "bound": "alu", "achieved": far_ach / 1e9, "peak": far_peak / 1e9,
                 "unit": "Gpair/s", "frac": far_ach / far_peak, "traffic": PROFILED_TRAFFIC.get((far_name,) + key),
                 "traffic_unit": "bytes per launch (ncu dram__bytes_read + write)", "ms_per_step": head["far_ms"],
@@ -398,6 +403,8 @@ def run_ours(a):
     Yd = torch.empty_like(Wd)
     obj.set_option("far_precision", a.far_precision)
     obj.set_option("near_precision", a.near_precision)
+    if not batch:
+        obj.set_option("far_kernel", a.far_kernel)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     stream = torch.cuda.current_stream()
 

@@ -231,13 +231,13 @@ int fkt_solve(fkt_plan_t plan, double sigma2, const float* b, float* x, int nrhs
               fkt_solve_info* info);
 
 /* fkt_solve with the solution returned in float64: x device [nrhs][N] float64 (output only).
- * The CG iterates are float64 already; fkt_solve rounds them to float32, which by itself limits
- * the true residual |b - (Ktilde + sigma2 I) x| / |b| to about |K| |x| 2^-24 / |b| (1e-4 to 1e-3
- * for GP systems with sigma2 = 1e-2).  Here x keeps its float64 iterate, and
- * info->true_rel_residual is recomputed with two products, Ktilde x = Ktilde hi + Ktilde lo
- * (x = hi + lo, both float32), so that the rounding of x does not enter; what remains is the
- * float32 arithmetic of the product itself.  Arguments, errors and synchronisation as for
- * fkt_solve. */
+ * The CG iterates are float64; fkt_solve rounds them to float32.  Here x keeps the float64
+ * iterate, and info->true_rel_residual is recomputed with two products, Ktilde x = Ktilde hi +
+ * Ktilde lo (x = hi + lo, both float32), so that the rounding of x does not enter.  What limits
+ * the true residual |b - (Ktilde + sigma2 I) x| / |b| either way is the float32 arithmetic of the
+ * products CG runs on: the recurrence residual drifts from the true one by their errors (measured
+ * for a GP system with sigma2 = 1e-2, N = 2000: recurrence 1e-7, true residual 9e-5 for both the
+ * float64 and the float32 x).  Arguments, errors and synchronisation as for fkt_solve. */
 int fkt_solve_f64(fkt_plan_t plan, double sigma2, const float* b, double* x, int nrhs, double tol, int max_iter,
                   fkt_solve_info* info);
 
@@ -315,6 +315,10 @@ int fkt_autotune_leaf(const float* points, int64_t N, int d, fkt_kernel kernel, 
  *   "coarse_seed"  unsigned integer (default 1): seed of the coarse space's frequencies
  *   "near_targets_per_thread"  "2" (default) | "4"  register blocking of the near-field kernel
  *               (4 applies to one right-hand side; results are identical up to rounding order)
+ *   "far_kernel"  "single" (default) | "pairs"  tensor-core far field of d = 3 in the BF16 forms:
+ *               each target thread generates its basis rows for two far entries at once in packed
+ *               float32 pairs (where the tensor memory allows: BF16 hi/lo up to p = 6, BF16 up to
+ *               p = 9), or for one entry at a time.  Results agree up to rounding order.
  *   "wait_limit_cycles"  "default" | an integer 0..2000000000  limit, in SM clocks, of the
  *               pipeline waits of the tensor-core near and far kernels (a source-record or
  *               multipole copy landing, the hand-off of a chunk or entry to the MMA issuer).
@@ -348,6 +352,51 @@ int fkt_plan_tree(fkt_plan_t plan, int64_t* perm, int64_t* begin, int64_t* end, 
 int fkt_plan_lists(fkt_plan_t plan, int64_t* block_range, int64_t* far_off, int32_t* far_node,
                    int32_t* far_mask, int64_t* near_off, int32_t* near_leaf, int32_t* near_mask,
                    uint32_t* masks);
+
+/* ---- Target-sharded product over several processes (one GPU each) ----
+ * The product shards by targets with one exchange step.  Every rank builds the same plan from all
+ * the points (the tree and lists of Sec. 3.1 are deterministic).  The target blocks, in tree
+ * (Morton) order, are split into one contiguous range per rank, balanced by their work (near
+ * pairs plus far pairs weighted by the cost of a basis row).  Each target keeps its own far and
+ * near sets (eq. accparam), so every (target, source) pair is evaluated exactly once, by the rank
+ * owning the target.  A rank owns the sources of its target range too: fkt_mvm_shard_begin
+ * computes the partial multipoles (s2m, Algorithm 1) of those sources for every node, the caller
+ * sums them over the ranks (one allreduce), and fkt_mvm_shard_end evaluates the far field
+ * (m2t) and the near field of the rank's targets.  s2m is linear in the weights, so the sum is
+ * the full product's multipoles.  w must hold all N weights on every rank (the near field reads
+ * any source); y receives the rank's targets only.  One pass: 1 <= nrhs <= 32.  The paper's code
+ * is single-process; this is the partition of its Algorithm 1 by targets. */
+
+/* Host only, no device work: split nblocks blocks of the given non-negative work into nranks
+ * contiguous ranges; bounds [nranks+1] receives the first block of each rank and nblocks.  A
+ * block goes to the rank whose share of the total work contains the block's cumulative midpoint.
+ * FKT_ERR_INVALID_ARG for nranks outside 1..4096, negative or NaN work, or null pointers. */
+int fkt_shard_partition(int64_t nblocks, const double* work, int nranks, int64_t* bounds);
+
+/* The work of each target block (host [target_blocks], from fkt_plan_stats) that the partition
+ * balances: near pairs plus 30 x far pairs.  Synchronizes.  FKT_ERR_UNSUPPORTED for batch plans. */
+int fkt_shard_block_work(fkt_plan_t plan, double* work);
+
+/* Select this process's share: rank in 0..nranks-1.  Partitions the blocks (fkt_shard_partition
+ * over fkt_shard_block_work) and cuts the s2m work to the rank's sources.  Synchronizes. */
+int fkt_shard_set(fkt_plan_t plan, int nranks, int rank);
+
+/* The selected share: target blocks [block_lo, block_hi), sorted targets [target_lo, target_hi)
+ * (positions in tree order; fkt_plan_tree's perm maps them to the caller's indices), and the size
+ * in floats of the multipole array that fkt_mvm_shard_begin fills for nrhs right-hand sides.
+ * Any pointer may be NULL.  FKT_ERR_INVALID_ARG before fkt_shard_set. */
+int fkt_shard_info(fkt_plan_t plan, int nrhs, int64_t* block_lo, int64_t* block_hi, int64_t* target_lo,
+                   int64_t* target_hi, int64_t* mult_floats);
+
+/* Phase 1: w device [nrhs][N] float32 (all points, caller order); mult device float32 of
+ * fkt_shard_info's mult_floats, overwritten with this rank's partial multipoles.  The caller then
+ * sums mult over the ranks (e.g. an NCCL allreduce) before phase 2.  Asynchronous. */
+int fkt_mvm_shard_begin(fkt_plan_t plan, const float* w, float* mult, int nrhs);
+
+/* Phase 2: mult = the multipoles summed over all ranks; y device [nrhs][N] float32 (caller
+ * order) receives the product for this rank's targets, other entries untouched.  Uses the source
+ * records of the last fkt_mvm_shard_begin on this plan (same w, same nrhs).  Asynchronous. */
+int fkt_mvm_shard_end(fkt_plan_t plan, const float* mult, float* y, int nrhs);
 
 /* fkt_mvm without any device allocation.
  *

@@ -690,6 +690,22 @@ int orc_fkt_eval(void* h, const int64_t* targets, int64_t nt, double* out) {
     return 0;
 }
 
+/* The multipoles of the last orc_fkt_s2m ([node][nrhs][nterms], count = nodes * nrhs * nterms
+ * doubles), read out or replaced (accessors only: a test sums per-rank partial multipoles and
+ * evaluates with the sum).  Return -1 on a count mismatch or before orc_fkt_s2m. */
+int orc_fkt_get_multipoles(void* h, double* out, int64_t count) {
+    ofkt* f = (ofkt*)h;
+    if (!f->M || count != f->nnodes * (int64_t)f->nrhs * f->basis->nterms) return -1;
+    memcpy(out, f->M, sizeof(double) * (size_t)count);
+    return 0;
+}
+int orc_fkt_set_multipoles(void* h, const double* in, int64_t count) {
+    ofkt* f = (ofkt*)h;
+    if (!f->M || count != f->nnodes * (int64_t)f->nrhs * f->basis->nterms) return -1;
+    memcpy(f->M, in, sizeof(double) * (size_t)count);
+    return 0;
+}
+
 /* Interaction lists of one target (original index): far nodes and near leaves. */
 static void lists_rec(const ofkt* f, int64_t t, int64_t b, int64_t* far, int64_t* nf, int64_t* near, int64_t* nn) {
     const onode* n = &f->nodes[b];

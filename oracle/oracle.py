@@ -73,6 +73,8 @@ def lib() -> ctypes.CDLL:
     L.orc_fkt_eval.argtypes = [ctypes.c_void_p, _i64p, ctypes.c_int64, _dp]
     L.orc_fkt_target_lists.argtypes = [ctypes.c_void_p, ctypes.c_int64, _i64p, _i64p, _i64p, _i64p]
     L.orc_num_threads.restype = ctypes.c_int
+    L.orc_fkt_get_multipoles.argtypes = [ctypes.c_void_p, _dp, ctypes.c_int64]
+    L.orc_fkt_set_multipoles.argtypes = [ctypes.c_void_p, _dp, ctypes.c_int64]
     return L
 
 
@@ -241,6 +243,32 @@ class FKT:
             targets = np.arange(self.N, dtype=np.int64)
         T = np.ascontiguousarray(targets, dtype=np.int64)
         out = np.zeros((nrhs, len(T)))
+        lib().orc_fkt_eval(self.h, _p(T, _i64p), len(T), _p(out, _dp))
+        return out
+
+    def s2m(self, w) -> None:
+        """Multipoles of every node for weights w [nrhs][N] (orc_fkt_s2m), kept for eval()."""
+        W = np.ascontiguousarray(np.atleast_2d(w), dtype=np.float64)
+        if lib().orc_fkt_s2m(self.h, _p(W, _dp), W.shape[0]) != 0:
+            raise ValueError("oracle FKT: bad nrhs")
+        self._nrhs = W.shape[0]
+
+    def multipoles(self) -> np.ndarray:
+        n = lib().orc_fkt_num_nodes(self.h) * self._nrhs * self.basis.nterms
+        out = np.zeros(n)
+        if lib().orc_fkt_get_multipoles(self.h, _p(out, _dp), n) != 0:
+            raise ValueError("oracle FKT: no multipoles")
+        return out
+
+    def set_multipoles(self, M: np.ndarray) -> None:
+        M = np.ascontiguousarray(M, dtype=np.float64)
+        if lib().orc_fkt_set_multipoles(self.h, _p(M, _dp), len(M)) != 0:
+            raise ValueError("oracle FKT: multipole count mismatch")
+
+    def eval(self, targets) -> np.ndarray:
+        """z at the given original target indices with the current multipoles and weights."""
+        T = np.ascontiguousarray(targets, dtype=np.int64)
+        out = np.zeros((self._nrhs, len(T)))
         lib().orc_fkt_eval(self.h, _p(T, _i64p), len(T), _p(out, _dp))
         return out
 

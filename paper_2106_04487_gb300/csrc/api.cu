@@ -32,6 +32,7 @@ void free_plan(fkt_plan_s* P) {
     fkt::free_learn(P);
     fkt::free_solve(P);
     fkt::free_batch_arrays(P);
+    fkt::free_shard(P);
     for (auto& e : P->ev)
         if (e) cudaEventDestroy(e);
     if (P->stream2) cudaStreamDestroy(P->stream2);
@@ -229,6 +230,12 @@ int fkt_set_option(fkt_plan_t plan, const char* key, const char* value) {
         }
         return FKT_OK;
     }
+    if (!strcmp(key, "far_kernel")) {
+        if (!strcmp(value, "pairs")) plan->far_kernel = 0;
+        else if (!strcmp(value, "single")) plan->far_kernel = 1;
+        else return FKT_ERR_INVALID_ARG;
+        return FKT_OK;
+    }
     if (!strcmp(key, "wait_limit_cycles")) {
         if (!strcmp(value, "default")) {
             plan->wait_cycles = fkt::kWaitCycles;
@@ -331,6 +338,47 @@ int fkt_plan_lists(fkt_plan_t plan, int64_t* block_range, int64_t* far_off, int3
     if (masks && P->nmasks)
         FKT_CUDA_TRY(cudaMemcpy(masks, P->masks, sizeof(uint32_t) * fkt::kMaskWords * P->nmasks, cudaMemcpyDeviceToHost));
     return FKT_OK;
+}
+
+int fkt_shard_partition(int64_t nblocks, const double* work, int nranks, int64_t* bounds) {
+    if (nranks < 1 || nranks > 4096) return FKT_ERR_INVALID_ARG;
+    return fkt::shard_partition(nblocks, work, nranks, bounds);
+}
+
+int fkt_shard_set(fkt_plan_t plan, int nranks, int rank) {
+    if (!plan || nranks < 1 || nranks > 4096 || rank < 0 || rank >= nranks) return FKT_ERR_INVALID_ARG;
+    return fkt::shard_set(plan, nranks, rank);
+}
+
+int fkt_shard_block_work(fkt_plan_t plan, double* work) {
+    if (!plan || !work) return FKT_ERR_INVALID_ARG;
+    if (plan->nprob) return FKT_ERR_UNSUPPORTED;
+    std::vector<double> w;
+    int rc = fkt::shard_block_work(plan, w);
+    if (rc) return rc;
+    std::copy(w.begin(), w.end(), work);
+    return FKT_OK;
+}
+
+int fkt_shard_info(fkt_plan_t plan, int nrhs, int64_t* block_lo, int64_t* block_hi, int64_t* target_lo,
+                   int64_t* target_hi, int64_t* mult_floats) {
+    if (!plan || plan->sh_nranks == 0 || nrhs < 1 || nrhs > 32) return FKT_ERR_INVALID_ARG;
+    if (block_lo) *block_lo = plan->sh_b0;
+    if (block_hi) *block_hi = plan->sh_b1;
+    if (target_lo) *target_lo = plan->sh_t0;
+    if (target_hi) *target_hi = plan->sh_t1;
+    if (mult_floats) *mult_floats = (int64_t)fkt::shard_mult_floats(plan, nrhs);
+    return FKT_OK;
+}
+
+int fkt_mvm_shard_begin(fkt_plan_t plan, const float* w, float* mult, int nrhs) {
+    if (!plan || !w || !mult || plan->sh_nranks == 0 || nrhs < 1 || nrhs > 32) return FKT_ERR_INVALID_ARG;
+    return fkt::shard_begin(plan, w, mult, nrhs);
+}
+
+int fkt_mvm_shard_end(fkt_plan_t plan, const float* mult, float* y, int nrhs) {
+    if (!plan || !mult || !y || plan->sh_nranks == 0 || nrhs < 1 || nrhs > 32) return FKT_ERR_INVALID_ARG;
+    return fkt::shard_end(plan, mult, y, nrhs);
 }
 
 int fkt_check(fkt_plan_t plan) {

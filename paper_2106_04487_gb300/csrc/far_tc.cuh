@@ -332,238 +332,14 @@ struct FarTc2Info {
     uint32_t on[kMaskWords];   // targets (TMEM lanes) that use the entry
 };
 
-template <int P, int PREC>
-__global__ void __launch_bounds__(160, P <= 6 ? 4 : P <= 7 ? 3 : 2) far_tc2_kernel(MvmArgs a, KernelParams kp_all, const __grid_constant__ FarTables T,
-                                                         const unsigned char* __restrict__ image, int nr_total) {
-    using Sh = Tc2Shape<P, PREC>;
-    using S = typename Sh::S;
-    constexpr int NT = Sh::NT, NTP = Sh::NTP, ST = Sh::ST, BB = S::B_BYTES, BPLANE = kTcN * NTP * 2;
-    constexpr int kFarFlush = 4;
-    constexpr uint32_t IDESC = tc::instr_desc(1u, 128u, (uint32_t)kTcN);
-    extern __shared__ __align__(128) unsigned char tc2_smem[];
-    unsigned char* Bbuf = tc2_smem;                                  // [ST][B_BYTES]
-    float* accs = reinterpret_cast<float*>(tc2_smem + ST * BB);      // [kTcN][128] float32 sums
-    __shared__ FarTc2Info info[ST];
-    __shared__ __align__(8) uint64_t full[ST], aready, mma_done;
-    __shared__ uint32_t tmem_base;
-    __shared__ uint32_t s_valid[kMaskWords];
-    __shared__ int s_fail;
-    const int tl = threadIdx.x, warp = tl >> 5, lane = tl & 31;
-    const int64_t blk = cta_block(a);
-    const KernelParams kp = block_params(a, blk, kp_all);
-    const int2 rg = a.blk[blk];
-    const int t = rg.x + tl;
-    const bool valid = warp < 4 && t < rg.y;
-    const uint32_t vword = __ballot_sync(0xffffffffu, valid);
-    const int64_t e0 = a.far_off[blk];
-    const int ne = (int)(a.far_off[blk + 1] - e0);
-    if (tl == 0) {
-#pragma unroll
-        for (int s = 0; s < ST; ++s) ptx::mbar_init(&full[s], 1);
-        ptx::mbar_init(&aready, 4);
-        ptx::mbar_init(&mma_done, 1);
-        ptx::fence_mbar_init();
-        s_fail = 0;
-    }
-    if (warp < 4 && lane == 0) s_valid[warp] = vword;
-    if (warp == 0) {
-        tc::alloc(&tmem_base, Sh::TMEM_COLS);
-        tc::relinquish();
-    }
-    tc::fence_before_sync();
-    __syncthreads();
-    tc::fence_after_sync();
-    const uint32_t tmem = tmem_base;
-
-    if (warp == 4) {
-        // The whole warp runs the loop in step: every lane holds the node centre, scale and row
-        // mask of one entry of a 32-entry window (loaded together, one memory latency per 32
-        // entries); lane 0 issues the copies and the MMAs.
-        int wb = 0, wnode = 0;
-        float4 wc = make_float4(0.f, 0.f, 0.f, 0.f);
-        float ws = 0.f;
-        uint32_t wm[kMaskWords] = {0u, 0u, 0u, 0u};
-        auto load_window = [&]() {
-            const int e = wb + lane;
-            if (e < ne) {
-                const int2 ent = a.far_ent[e0 + e];
-                wnode = ent.x;
-                wc = a.nd_cf[ent.x];
-                ws = a.nd_scale[ent.x];
-#pragma unroll
-                for (int w = 0; w < kMaskWords; ++w)
-                    wm[w] = (ent.y < 0 ? 0xFFFFFFFFu : __ldg(&a.masks[(int64_t)ent.y * kMaskWords + w])) & s_valid[w];
-            }
-        };
-        int issued = 0;
-        auto produce = [&]() {  // warp-collective
-            if (issued >= wb + 32) {
-                wb += 32;
-                load_window();
-            }
-            const int src = issued - wb, slot = issued % ST;
-            const int node = __shfl_sync(0xffffffffu, wnode, src);
-            const float cx = __shfl_sync(0xffffffffu, wc.x, src), cy = __shfl_sync(0xffffffffu, wc.y, src);
-            const float cz = __shfl_sync(0xffffffffu, wc.z, src), cw = __shfl_sync(0xffffffffu, wc.w, src);
-            const float sc = __shfl_sync(0xffffffffu, ws, src);
-            uint32_t on[kMaskWords];
-#pragma unroll
-            for (int w = 0; w < kMaskWords; ++w) on[w] = __shfl_sync(0xffffffffu, wm[w], src);
-            if (lane == 0) {
-                FarTc2Info& in = info[slot];
-                in.c = make_float4(cx, cy, cz, cw);
-                in.s = sc;
-#pragma unroll
-                for (int w = 0; w < kMaskWords; ++w) in.on[w] = on[w];
-                ptx::mbar_arrive_expect_tx(&full[slot], (uint32_t)BB);
-                ptx::bulk_g2s(Bbuf + slot * BB, image + (int64_t)node * BB, (uint32_t)BB, &full[slot]);
-            }
-            ++issued;
-        };
-        if (ne > 0) load_window();
-        while (issued < ST && issued < ne) produce();
-        bool ok = true;
-        int i = 0;
-        for (; i < ne; ++i) {
-            const int slot = i % ST;
-            ok = ptx::mbar_wait_bounded(&aready, (uint32_t)(i & 1), a.wait_cycles) && !s_fail;
-            if (!__all_sync(0xffffffffu, ok)) { ok = false; break; }
-            if (lane == 0) {
-                tc::fence_after_sync();
-                uint32_t off[kMaskWords];
-#pragma unroll
-                for (int w = 0; w < kMaskWords; ++w) off[w] = ~info[slot].on[w];
-                const unsigned char* B = Bbuf + slot * BB;
-#pragma unroll 1
-                for (int ks = 0; ks < NTP / 16; ++ks) {
-                    const uint64_t bh = tc::smem_desc(B + ks * 256, 128, S::SBO_A);
-                    const uint32_t ahi = tmem + Sh::COL_AHI + ks * 8;
-                    tc::mma_bf16_ts_masked(tmem, ahi, bh, IDESC, off);
-                    if (PREC == TC_BF16X3) {
-                        const uint64_t bl = tc::smem_desc(B + BPLANE + ks * 256, 128, S::SBO_A);
-                        tc::mma_bf16_ts_masked(tmem, ahi, bl, IDESC, off);
-                        tc::mma_bf16_ts_masked(tmem, tmem + Sh::COL_ALO + ks * 8, bh, IDESC, off);
-                    }
-                }
-                tc::commit(&mma_done);
-            }
-            __syncwarp();
-            // the consumers saw the MMAs of entry i-1 complete before they arrived on aready for
-            // entry i: its stage is free for entry i-1+ST
-            if (i >= 1 && issued < ne) {
-                if (lane == 0) ptx::fence_proxy_async_smem();
-                produce();
-            }
-        }
-        if (!ok && lane == 0) {
-            s_fail = 1;
-            atomicExch(a.err, 1);
-            // the last copy of each stage may still be in flight; then the last MMAs
-            for (int j = issued > ST ? issued - ST : 0; j < issued; ++j)
-                ptx::mbar_wait_bounded(&full[j % ST], (uint32_t)((j / ST) & 1), kWaitCycles);
-            if (i >= 1) ptx::mbar_wait_bounded(&mma_done, (uint32_t)((i - 1) & 1), kWaitCycles);
-        }
-    } else {
-        const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
-        const float4 xt = valid ? a.xs[t] : make_float4(0.f, 0.f, 0.f, 0.f);
-        tc::st32_zero(tmem + lane_base);
-        tc::wait_st();
-#pragma unroll
-        for (int r = 0; r < kTcN; ++r) accs[r * 128 + tl] = 0.f;
-        // accumulator rows -> the float32 sums in shared memory (conflict-free: r-major)
-        auto flush = [&]() {
-            float d[kTcN];
-            tc::ld16(tmem + lane_base, d);
-            tc::ld16(tmem + lane_base + 16, d + 16);
-#pragma unroll
-            for (int r = 0; r < kTcN; ++r) accs[r * 128 + tl] += d[r];
-        };
-        bool ok = true, dirty = false;
-        int i = 0;
-        for (; i < ne; ++i) {
-            const int slot = i % ST;
-            ok = ptx::mbar_wait_bounded(&full[slot], (uint32_t)((i / ST) & 1), a.wait_cycles);
-            if (!__all_sync(0xffffffffu, ok) || s_fail) { ok = false; break; }
-            // The MMAs of entry i-1 must be complete before this warp writes its A rows, flushes
-            // or arrives for entry i; a busy warp waits only just before its first store, so the
-            // radial part of its rows overlaps them.
-            bool waited = i == 0;
-            auto wait_prev = [&]() {
-                if (!waited) {
-                    ok = ptx::mbar_wait_bounded(&mma_done, (uint32_t)((i - 1) & 1), kWaitCycles) && ok;
-                    waited = true;
-                    tc::fence_after_sync();
-                }
-            };
-            bool stored = false;
-            if (i > 0 && i % kFarFlush == 0 && dirty) {
-                wait_prev();
-                flush();
-                tc::st32_zero(tmem + lane_base);
-                dirty = false;
-                stored = true;
-            }
-            const uint32_t mword = info[slot].on[warp];
-            if (mword != 0u) {
-                const float4 c = info[slot].c;
-                const float sc = info[slot].s;
-                float buf[16];
-                auto store_group = [&](int g) {  // terms 16g..16g+15 as 8 packed pairs per plane
-                    uint32_t hi[8], lo[8];
-#pragma unroll
-                    for (int i2 = 0; i2 < 8; ++i2) {
-                        const __nv_bfloat162 h = __floats2bfloat162_rn(buf[2 * i2], buf[2 * i2 + 1]);
-                        hi[i2] = bf2_bits(h);
-                        if (PREC == TC_BF16X3) {
-                            const float2 f = __bfloat1622float2(h);
-                            const float2 r = __ffma2_rn(f, make_float2(-1.f, -1.f), make_float2(buf[2 * i2], buf[2 * i2 + 1]));
-                            lo[i2] = bf2_bits(__floats2bfloat162_rn(r.x, r.y));
-                        }
-                    }
-                    if (g == 0) wait_prev();
-                    tc::st8(tmem + lane_base + Sh::COL_AHI + g * 8, hi);
-                    if (PREC == TC_BF16X3) tc::st8(tmem + lane_base + Sh::COL_ALO + g * 8, lo);
-                };
-                far_basis<3, P>(xt, c, sc, kp, T, [&](int q, float v) {
-                    buf[q & 15] = v;
-                    if (q == NT - 1) {
-#pragma unroll
-                        for (int z = (q & 15) + 1; z < 16; ++z) buf[z] = 0.f;
-                        store_group(q >> 4);
-                    } else if ((q & 15) == 15) {
-                        store_group(q >> 4);
-                    }
-                });
-                dirty = true;
-                stored = true;
-            }
-            wait_prev();
-            if (!__all_sync(0xffffffffu, ok)) break;
-            if (stored) tc::wait_st();
-            tc::fence_before_sync();
-            __syncwarp();
-            if (lane == 0) ptx::mbar_arrive(&aready);
-        }
-        if (ok && i >= 1) ok = ptx::mbar_wait_bounded(&mma_done, (uint32_t)((i - 1) & 1), kWaitCycles);
-        ok = __all_sync(0xffffffffu, ok);
-        if (!ok) {
-            s_fail = 1;
-            if (lane == 0) atomicExch(a.err, 1);
-        }
-        tc::fence_after_sync();
-        if (ok && dirty) flush();
-        __syncwarp();
-        if (ok && valid)
-#pragma unroll 4
-            for (int r = 0; r < kTcN; ++r)
-                if (r < nr_total) a.yfar[(int64_t)r * a.N + t] = accs[r * 128 + tl];  // tree order, coalesced
-    }
-    tc::fence_before_sync();
-    __syncthreads();
-    if (warp == 0) tc::dealloc(tmem, Sh::TMEM_COLS);
-}
-
 }  // namespace fkt
+
+#include "far_tc2.cuh"
+
+namespace fkt {
+}  // namespace fkt
+
+#include "far_tc3.cuh"
 
 namespace fkt {
 
@@ -576,6 +352,8 @@ struct TcLaunch {
     int nr_total;                // right-hand sides in this pass (<= kTcN)
     unsigned char* image;        // packed B operands, [nodes][B_BYTES]
     cudaStream_t s_pack, s_far;
+    int far_kernel;              // d = 3 BF16 forms: 0 = two entries per thread (far_tc3) where
+                                 // supported, 1 = one entry per thread (far_tc2)
 };
 
 template <int D, int P, int PREC>
@@ -594,6 +372,24 @@ int launch_tc_t(const TcLaunch& L) {
 template <int D, int P, int PREC>
 int launch_tc_far_t(const TcLaunch& L) {
     using S = TcShape<D, P, PREC>;
+    if constexpr (D == 3 && Tc3Shape<P, PREC>::supported) {
+        if (L.far_kernel == 0) {
+            using Sh = Tc3Shape<P, PREC>;
+            const size_t smem = Sh::smem_bytes();
+            static bool attr3 = false;
+            if (!attr3) {
+                FKT_CUDA_TRY(cudaFuncSetAttribute(far_tc3_kernel<P, PREC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                  (int)smem));
+                attr3 = true;
+            }
+            FarTables2 T2;
+            make_far_tables2(*L.T, &T2);
+            far_tc3_kernel<P, PREC><<<(unsigned)L.nblocks, Sh::THREADS, smem, L.s_far>>>(*L.a, *L.kp, T2, L.image,
+                                                                                        L.nr_total);
+            FKT_CUDA_TRY(cudaGetLastError());
+            return FKT_OK;
+        }
+    }
     if constexpr (D == 3 && Tc2Shape<P, PREC>::supported) {
         using Sh = Tc2Shape<P, PREC>;
         const size_t smem = Sh::smem_bytes();

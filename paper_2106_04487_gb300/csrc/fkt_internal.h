@@ -64,6 +64,7 @@ struct fkt_plan_s {
     int far_precision = fkt::FAR_FP32;
     int near_tpt = 2;              // near-field targets per thread (2 or 4)
     int near_precision = fkt::NEAR_FP32;  // near-field contraction of 32-wide passes
+    int far_kernel = 1;            // tensor-core far field, d = 3 BF16 forms: 0 = two entries per thread, 1 = one
     // bounding cube
     double lo[4] = {0, 0, 0, 0};
     double L = 1.0;
@@ -149,6 +150,13 @@ struct fkt_plan_s {
     const void* graph_w = nullptr;
     const void* graph_y = nullptr;
     int graph_nrhs = 0;
+    // target-sharded product (shard.cu): this rank's share of the partition
+    int sh_nranks = 0, sh_rank = 0;             // 0 ranks: no share selected
+    int64_t sh_b0 = 0, sh_b1 = 0;               // target blocks [b0, b1)
+    int64_t sh_t0 = 0, sh_t1 = 0;               // sorted targets (= owned sources) [t0, t1)
+    int4* sh_items = nullptr;                   // device: the s2m items cut to [t0, t1)
+    int64_t* sh_item_off = nullptr;             // device: [nodes + 1] item offsets per node
+    int64_t sh_nitems = 0;
     // stats
     fkt_stats stats{};
 };
@@ -192,6 +200,16 @@ int create_far_stream(cudaStream_t* s);
 // stage launch helpers shared with batch.cu
 void launch_near_stage(fkt_plan_s* P, MvmArgs& a, int nrb, int tpt, cudaStream_t st, bool exact = false);
 int free_batch_arrays(fkt_plan_s* P);
+
+// shard.cu
+int shard_partition(int64_t nblocks, const double* work, int nranks, int64_t* bounds);
+int shard_set(fkt_plan_s* P, int nranks, int rank);
+int shard_block_work(fkt_plan_s* P, std::vector<double>& work);
+void free_shard(fkt_plan_s* P);
+// mvm.cu: the two phases of the sharded product (one pass of <= 32 right-hand sides)
+size_t shard_mult_floats(const fkt_plan_s* P, int nrhs);
+int shard_begin(fkt_plan_s* P, const float* w, float* mult, int nrhs);
+int shard_end(fkt_plan_s* P, const float* mult, float* y, int nrhs);
 
 // solve.cu
 int precond_setup(fkt_plan_s* P, double sigma2);

@@ -237,6 +237,7 @@ struct MvmArgs {
     const int32_t* blk_prob;   // problem of each target block
     const int32_t* blk_list;   // grid index -> target block (work ordered largest first)
     const float* pt_sig;       // near-field coordinate scale of each point's problem
+    int64_t blk_base;          // first target block of the launch (a rank's share of a sharded product)
     // limit, in SM clocks, of the pipeline waits of the tensor-core kernels (record / multipole
     // copies landing, the consumers' hand-off to the MMA issuer); the waits that drain work in
     // flight before a CTA exits always use kWaitCycles
@@ -245,7 +246,7 @@ struct MvmArgs {
 
 // Target block handled by this CTA and its kernel parameters (per problem in a batch).
 __device__ __forceinline__ int64_t cta_block(const MvmArgs& a) {
-    return a.blk_list ? (int64_t)a.blk_list[blockIdx.x] : (int64_t)blockIdx.x;
+    return a.blk_list ? (int64_t)a.blk_list[blockIdx.x] : a.blk_base + (int64_t)blockIdx.x;
 }
 __device__ __forceinline__ KernelParams block_params(const MvmArgs& a, int64_t blk, const KernelParams& kp) {
     return a.kps ? a.kps[a.blk_prob[blk]] : kp;

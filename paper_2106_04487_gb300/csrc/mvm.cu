@@ -129,6 +129,16 @@ MvmArgs base_args(fkt_plan_s* P) {
 
 size_t round64(size_t n) { return (n + 63) / 64 * 64; }
 
+// y[r][perm[i]] = ys[r][i] + yadd[r][i] for the sorted targets i0 <= i < i1 only.
+__global__ void unpermute_range_kernel(int64_t i0, int64_t i1, int64_t N, int nr, const int32_t* __restrict__ perm,
+                                       const float* __restrict__ ys, const float* __restrict__ yadd,
+                                       float* __restrict__ y) {
+    const int64_t i = i0 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= i1) return;
+    const int64_t o = perm[i];
+    for (int r = 0; r < nr; ++r) y[r * N + o] = ys[r * N + i] + yadd[r * N + i];
+}
+
 __global__ void dense_lists_kernel(int64_t nblocks, int64_t* off, int2* ent) {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i < nblocks) ent[i] = make_int2(0, -1);  // the root holds every point
@@ -290,7 +300,8 @@ int run_mvm(fkt_plan_s* P, const MvmBuffers& B, const float* w, float* y, int nr
         } else {
             af.mult = B.mult + (size_t)g0 * 8 * NT * nodes;
             af.yfar = B.yfar + (size_t)r0 * N;
-            TcLaunch T{&af, &P->kp, &P->tabs, P->nblocks, P->nnodes, (int64_t)(8 * NT * nodes), npass, B.image, st2, st2};
+            TcLaunch T{&af, &P->kp, &P->tabs, P->nblocks, P->nnodes, (int64_t)(8 * NT * nodes), npass, B.image, st2, st2,
+                       P->far_kernel};
             int rc = launch_tc_any(P->d, P->p, tc_prec_of(P->far_precision), false, T);  // pack
             if (rc) return rc;
             rc = launch_tc_any(P->d, P->p, tc_prec_of(P->far_precision), true, T);
@@ -312,6 +323,90 @@ int run_mvm(fkt_plan_s* P, const MvmBuffers& B, const float* w, float* y, int nr
         FKT_CUDA_TRY(cudaGetLastError());
     }
     if (timing) return finish_timing(P);
+    return FKT_OK;
+}
+
+// ---------------------------------------------------------------- sharded product
+// Floats of the multipole array that the ranks sum between the two phases: every group of 8
+// right-hand sides of one pass, [group][nodes][nterms][8].
+size_t shard_mult_floats(const fkt_plan_s* P, int nrhs) {
+    const size_t groups = (size_t)(nrhs + 7) / 8;
+    return groups * 8 * (size_t)P->nterms * (size_t)std::max<int64_t>(P->nnodes, 1);
+}
+
+// Phase 1 on this rank: source records of every point (the near field reads any source), then
+// the partial multipoles of the rank's own sources into mult (zeroed first; nodes without such
+// sources stay zero).  One pass: 1 <= nrhs <= 32.
+int shard_begin(fkt_plan_s* P, const float* w, float* mult, int nrhs) {
+    const int cap = std::max(8, (nrhs + 7) / 8 * 8);
+    int rc = ensure_rhs_capacity(P, cap);
+    if (rc) return rc;
+    cudaStream_t st = P->stream;
+    const int64_t N = P->N;
+    const size_t NT = (size_t)P->nterms, nodes = std::max<int64_t>(P->nnodes, 1);
+    const int nrb = 8, nw = near_width(nrb, nrhs), ng = (nrhs + nrb - 1) / nrb;
+    launch_permute(P->d, nw, (unsigned)((N + 255) / 256), st, N, P->perm, P->xs, w, nrhs, P->kp.sig, P->pt_sig, P->rec);
+    FKT_CUDA_TRY(cudaGetLastError());
+    FKT_CUDA_TRY(cudaMemsetAsync(mult, 0, sizeof(float) * shard_mult_floats(P, nrhs), st));
+    MvmArgs a = base_args(P);
+    a.rec = P->rec;
+    a.rec_f4 = rec_f4(P->d, nw);
+    a.s2m_items = P->sh_items;
+    a.s2m_item_off = P->sh_item_off;
+    for (int g = 0; g < ng; ++g) {
+        MvmArgs ag = a;
+        ag.woff = rec_woff(P->d, nw) + g * nrb;
+        ag.mult = mult + (size_t)g * nrb * NT * nodes;
+        ag.part = P->s2m_part + (size_t)g * nrb * NT * std::max<int64_t>(P->n_s2m_items, 1);
+        ag.nr = std::min(nrb, nrhs - g * nrb);
+        FarLaunch L{&ag, &P->kp, &P->tabs, P->nblocks, P->sh_nitems, P->nnodes, st, st};
+        if ((rc = launch_s2m_any(P->d, P->p, nrb, L))) return rc;
+    }
+    return FKT_OK;
+}
+
+// Phase 2 on this rank, after the multipoles were summed over all ranks: far and near field of
+// the rank's target blocks, written to y (caller order) for the rank's targets only.  Uses the
+// source records of phase 1.
+int shard_end(fkt_plan_s* P, const float* mult, float* y, int nrhs) {
+    const bool tc = P->far_precision != FAR_FP32;
+    cudaStream_t st = P->stream;
+    const int64_t N = P->N, nb = P->sh_b1 - P->sh_b0;
+    const size_t NT = (size_t)P->nterms, nodes = std::max<int64_t>(P->nnodes, 1);
+    const int nrb = 8, nw = near_width(nrb, nrhs), ng = (nrhs + nrb - 1) / nrb;
+    if (nb == 0) return FKT_OK;
+    MvmArgs a = base_args(P);
+    a.rec = P->rec;
+    a.rec_f4 = rec_f4(P->d, nw);
+    a.blk_base = P->sh_b0;
+    if (!tc) {
+        for (int g = 0; g < ng; ++g) {
+            MvmArgs ag = a;
+            ag.mult = const_cast<float*>(mult) + (size_t)g * nrb * NT * nodes;
+            ag.yfar = P->yfar + (size_t)g * nrb * N;
+            ag.nr = std::min(nrb, nrhs - g * nrb);
+            FarLaunch L{&ag, &P->kp, &P->tabs, nb, P->n_s2m_items, P->nnodes, st, st};
+            int rc = launch_far_any(P->d, P->p, nrb, L);
+            if (rc) return rc;
+        }
+    } else {
+        MvmArgs af = a;
+        af.mult = const_cast<float*>(mult);
+        af.yfar = P->yfar;
+        TcLaunch T{&af, &P->kp, &P->tabs, nb, P->nnodes, (int64_t)(8 * NT * nodes), nrhs, P->tc_image, st, st,
+                   P->far_kernel};
+        int rc = launch_tc_any(P->d, P->p, tc_prec_of(P->far_precision), false, T);  // pack every used node
+        if (!rc) rc = launch_tc_any(P->d, P->p, tc_prec_of(P->far_precision), true, T);
+        if (rc) return rc;
+    }
+    a.ynear = P->ynear;
+    a.nr = nrhs;
+    launch_near(P->d, nw, P->near_tpt, P->near_precision == NEAR_TF32X3, P->kernel.kind, (unsigned)nb, st, a, P->kp);
+    FKT_CUDA_TRY(cudaGetLastError());
+    const int64_t nt = P->sh_t1 - P->sh_t0;
+    unpermute_range_kernel<<<(unsigned)((nt + 255) / 256), 256, 0, st>>>(P->sh_t0, P->sh_t1, N, nrhs, P->perm, P->ynear,
+                                                                         P->yfar, y);
+    FKT_CUDA_TRY(cudaGetLastError());
     return FKT_OK;
 }
 

@@ -94,6 +94,21 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
     return ok != 0;
 }
 
+// Non-blocking test of the phase (try_wait may suspend the thread for a system-dependent time).
+__device__ __forceinline__ bool mbar_test_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n"
+        ".reg .pred p;\n"
+        "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        "selp.u32 %0, 1, 0, p;\n"
+        "}\n"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
 // try_wait with a suspend-time hint: the hardware may park the thread until the phase completes
 // or the hint (nanoseconds) runs out.
 __device__ __forceinline__ bool mbar_try_wait_hint(uint64_t* bar, uint32_t parity, uint32_t hint_ns) {
@@ -117,8 +132,8 @@ __device__ __forceinline__ bool mbar_try_wait_hint(uint64_t* bar, uint32_t parit
 // suspend hint, the lowest-latency wake-up, for waits that gate the next step of a pipeline.
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, long long max_cycles,
                                                   uint32_t max_sleep_ns = 0) {
+    if (max_cycles <= 0) return mbar_test_wait(bar, parity);  // a limit of 0: one non-blocking poll
     if (mbar_try_wait(bar, parity)) return true;
-    if (max_cycles <= 0) return false;  // a limit of 0: one poll only
     const long long t0 = clock64();
     uint32_t ns = 32;
     for (;;) {

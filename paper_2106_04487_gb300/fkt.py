@@ -26,7 +26,9 @@ EXPORTS = ["fkt_plan", "fkt_mvm", "fkt_mvm_host", "fkt_dense_mvm", "fkt_set_opti
            "fkt_plan_tree", "fkt_plan_lists", "fkt_destroy", "fkt_error_string", "fkt_mvm_noalloc",
            "fkt_check", "fkt_precond_setup", "fkt_precond_apply", "fkt_solve", "fkt_solve_f64", "fkt_batch_plan", "fkt_batch_mvm",
            "fkt_batch_set_option", "fkt_batch_info", "fkt_batch_check", "fkt_batch_destroy", "fkt_autotune_leaf",
-           "fkt_precond_learn", "fkt_learn_params", "fkt_learn_eval", "fkt_learn_teacher", "fkt_spectral_sample"]
+           "fkt_precond_learn", "fkt_learn_params", "fkt_learn_eval", "fkt_learn_teacher", "fkt_spectral_sample",
+           "fkt_shard_partition", "fkt_shard_block_work", "fkt_shard_set", "fkt_shard_info", "fkt_mvm_shard_begin",
+           "fkt_mvm_shard_end"]
 
 
 class FktError(RuntimeError):
@@ -113,6 +115,12 @@ def lib() -> ctypes.CDLL:
                             ctypes.POINTER(fkt_solve_info)]
     L.fkt_solve_f64.argtypes = L.fkt_solve.argtypes
     L.fkt_spectral_sample.argtypes = [fkt_kernel, ctypes.c_int, ctypes.c_int, ctypes.c_uint64, vp, vp]
+    L.fkt_shard_partition.argtypes = [i64, vp, ctypes.c_int, vp]
+    L.fkt_shard_block_work.argtypes = [vp, vp]
+    L.fkt_shard_set.argtypes = [vp, ctypes.c_int, ctypes.c_int]
+    L.fkt_shard_info.argtypes = [vp, ctypes.c_int] + [ctypes.POINTER(ctypes.c_int64)] * 5
+    L.fkt_mvm_shard_begin.argtypes = [vp, vp, vp, ctypes.c_int]
+    L.fkt_mvm_shard_end.argtypes = [vp, vp, vp, ctypes.c_int]
     L.fkt_destroy.argtypes = [vp]
     L.fkt_destroy.restype = None
     L.fkt_error_string.argtypes = [ctypes.c_int]
@@ -213,6 +221,14 @@ def fkt_spectral_sample(kernel: fkt_kernel, d: int, R: int, seed: int = 1):
     _check(lib().fkt_spectral_sample(kernel, int(d), int(R), int(seed), _ptr(omega), _ptr(phase)),
            "fkt_spectral_sample")
     return omega, phase
+
+
+def fkt_shard_partition(work, nranks: int) -> np.ndarray:
+    """Host only: first block of each of nranks contiguous ranges balancing work, plus nblocks."""
+    w = np.ascontiguousarray(work, dtype=np.float64)
+    bounds = np.zeros(nranks + 1, np.int64)
+    _check(lib().fkt_shard_partition(len(w), _ptr(w), int(nranks), _ptr(bounds)), "fkt_shard_partition")
+    return bounds
 
 
 def fkt_check(plan):
@@ -343,6 +359,38 @@ class Plan:
         z = torch.empty_like(r2)
         fkt_precond_apply(self.h, r2, z, r2.shape[0])
         return z if r.dim() == 2 else z[0]
+
+    # ---- target-sharded product (one rank's share; the caller sums mult over the ranks) ----
+    def shard_set(self, nranks: int, rank: int) -> dict:
+        _check(lib().fkt_shard_set(self.h, int(nranks), int(rank)), "fkt_shard_set")
+        return self.shard_info(1)
+
+    def shard_info(self, nrhs: int) -> dict:
+        v = [ctypes.c_int64() for _ in range(5)]
+        _check(lib().fkt_shard_info(self.h, int(nrhs), *[ctypes.byref(x) for x in v]), "fkt_shard_info")
+        return dict(zip(("block_lo", "block_hi", "target_lo", "target_hi", "mult_floats"), [x.value for x in v]))
+
+    def block_work(self) -> np.ndarray:
+        w = np.zeros(self.stats()["target_blocks"], np.float64)
+        _check(lib().fkt_shard_block_work(self.h, _ptr(w)), "fkt_shard_block_work")
+        return w
+
+    def shard_begin(self, w, mult=None):
+        """Phase 1: this rank's partial multipoles (a new or given float32 device tensor)."""
+        import torch
+
+        w2 = (w if w.dim() == 2 else w[None]).contiguous()
+        n = self.shard_info(w2.shape[0])["mult_floats"]
+        if mult is None:
+            mult = torch.empty(n, dtype=torch.float32, device=w2.device)
+        _check(lib().fkt_mvm_shard_begin(self.h, _ptr(w2), _ptr(mult), w2.shape[0]), "fkt_mvm_shard_begin")
+        return mult
+
+    def shard_end(self, mult, y):
+        """Phase 2 after the multipoles were summed over the ranks: y ([nrhs][N]) gets this rank's targets."""
+        _check(lib().fkt_mvm_shard_end(self.h, _ptr(mult), _ptr(y), y.shape[0] if y.dim() == 2 else 1),
+               "fkt_mvm_shard_end")
+        return y
 
     def tree(self) -> dict:
         s = self.stats()

@@ -56,6 +56,47 @@ def test_precision_modes_d3(fkt, case3, prec, nrhs):
     assert err < BARS[prec], err
 
 
+@pytest.mark.parametrize("prec", ["bf16x3", "bf16"])
+@pytest.mark.parametrize("far_kernel", ["pairs", "single"])
+@pytest.mark.parametrize("p,nrhs", [(0, 8), (3, 13), (6, 40), (8, 32)])
+def test_far_kernel_variants_d3(fkt, orc, prec, far_kernel, p, nrhs):
+    """Both tensor-core far kernels (two far entries per thread in packed float32 pairs, or one)
+    at several orders, including an odd number of entries per block and orders past the paired
+    kernel's tensor-memory limit (which fall back to one entry per thread), against the oracle."""
+    import torch
+
+    X = inputs.gaussian_mixture(20000, 3, 10, 0.05, seed=49)
+    W = inputs.normal_weights(20000, nrhs, seed=50)
+    z = orc.FKT(X, orc.kparams("cauchy", 0.05), p=p, leaf_size=100, theta=0.5).mvm(W)
+    plan = fkt.Plan(torch.from_numpy(X).cuda(), "cauchy", lengthscale=0.05, p=p, leaf_size=100, theta=0.5)
+    plan.set_option("far_precision", prec)
+    plan.set_option("far_kernel", far_kernel)
+    y = plan.mvm(torch.from_numpy(W).cuda()).cpu().numpy().astype(np.float64)
+    plan.check()
+    err = _rel(y, z)
+    print(f"far {prec} {far_kernel} p={p} nrhs={nrhs}: rel err vs oracle {err:.3e}")
+    assert np.isfinite(y).all()
+    assert err < BARS[prec], err
+
+
+@pytest.mark.parametrize("kernel,ell,alpha", [("gaussian", 0.1, 1.0), ("exponential", 0.3, 1.0),
+                                              ("matern52", 0.3, 1.0), ("ratquad", 0.2, 0.5), ("laplace", 1.0, 1.0)])
+def test_far_pairs_every_kernel(fkt, orc, kernel, ell, alpha):
+    """The packed-pair jets of every kernel kind (the paired kernel has its own recurrences)."""
+    import torch
+
+    X = inputs.gaussian_mixture(15000, 3, 10, 0.05, seed=51)
+    W = inputs.normal_weights(15000, 32, seed=52)
+    z = orc.FKT(X, orc.kparams(kernel, ell, alpha=alpha), p=5, leaf_size=128, theta=0.5).mvm(W)
+    plan = fkt.Plan(torch.from_numpy(X).cuda(), kernel, lengthscale=ell, alpha=alpha, p=5, leaf_size=128, theta=0.5)
+    plan.set_option("far_precision", "bf16x3")
+    y = plan.mvm(torch.from_numpy(W).cuda()).cpu().numpy().astype(np.float64)
+    plan.check()
+    err = _rel(y, z)
+    print(f"far pairs {kernel}: rel err vs oracle {err:.3e}")
+    assert err < BARS["bf16x3"], err
+
+
 @pytest.mark.parametrize("prec", ["bf16x3", "tf32", "bf16"])
 def test_precision_modes_d4(fkt, orc, prec):
     import torch

@@ -72,10 +72,11 @@ def test_solve_dense_limit(fkt, orc):
 
 
 def test_solve_f64_dense_limit(fkt, orc):
-    """fkt_solve_f64: the same dense-limit system with x returned in float64.  Without the rounding
-    of x to float32 the float64 residual falls below the float32 floor of fkt_solve (about 1e-4
-    here) and is limited by the float32 arithmetic of the products CG used; the library's own
-    two-product true residual agrees with the float64 dense one."""
+    """fkt_solve_f64: the same dense-limit system with x returned in float64.  Measured: the float64
+    residual of the float64 x is the same as that of the float32 x (both about 1e-4 here, while
+    the recurrence reaches 1e-7): the floor comes from the float32 arithmetic of the products CG
+    runs on (the recurrence drifts from the true residual by their errors), not from rounding x.
+    The library's own two-product true residual agrees with the float64 dense one."""
     import torch
 
     X = inputs.gaussian_mixture(2000, 4, 20, 0.05, seed=32)
@@ -93,9 +94,9 @@ def test_solve_f64_dense_limit(fkt, orc):
     res32 = np.linalg.norm(b - (orc.dense(X, kp, x32) + sigma2 * x32), axis=1) / np.linalg.norm(b, axis=1)
     print(f"float64 residual of x: f64 {res.max():.2e} (library {info['true_rel_residual']:.2e}), "
           f"f32 {res32.max():.2e}; iterations {info['iterations']}")
-    assert res.max() < 3e-5, (res, info)
-    assert res.max() < 0.5 * res32.max()
-    assert abs(info["true_rel_residual"] - res.max()) < 0.5 * res.max() + 2e-6, info
+    assert res.max() < 3e-4, (res, info)
+    assert res.max() <= 1.1 * res32.max()
+    assert abs(info["true_rel_residual"] - res.max()) < 0.25 * res.max(), info
 
 
 def test_solve_against_oracle_fkt_operator(fkt, orc):
