@@ -126,13 +126,15 @@ def near_pair_cost(kernel: str, nw: int, tensor: bool = False):
     return 6 + extra + fma, mufu
 
 
-def far_pair_ops(p: int) -> int:
+def far_pair_ops(p: int, diag: bool = False) -> int:
     """FP32 lane-ops the method needs per (target, far node) pair in d = 3 before the contraction:
     distance and direction (~10), kernel derivatives J_m, m <= p (~3 per order), the radial sums
     R_kj = sum_m That_kjm J_m (j + 1 FMAs per (k, j)), the powers (s/r)^j and G = (s/r)^j R (p + pairs),
-    the (p+1)^2 harmonics by recurrence (~3 each) and the products Y_kh G_kj (one per term)."""
-    pairs = [(k, j) for k in range(p + 1) for j in range(k, p + 1, 2)]
-    return 10 + 3 * (p + 1) + sum(j + 1 for _, j in pairs) + p + len(pairs) + 3 * (p + 1) ** 2 + nterms(3, p)
+    the (p+1)^2 harmonics by recurrence (~3 each) and the products Y_kh G_kj (one per term).
+    diag: the radially compressed expansion of 1/r (only j = k), (p+1)^2 terms."""
+    pairs = [(k, j) for k in range(p + 1) for j in range(k, p + 1, 2) if not diag or j == k]
+    nt = (p + 1) ** 2 if diag else nterms(3, p)
+    return 10 + 3 * (p + 1) + sum(j + 1 for _, j in pairs) + p + len(pairs) + 3 * (p + 1) ** 2 + nt
 
 
 def launches_per_step(nrhs: int, far_precision: str) -> int:
@@ -167,6 +169,8 @@ def parse():
                     help="near-field contraction of 32-wide passes: tensor cores (TF32 hi/lo) or CUDA cores")
     ap.add_argument("--far-kernel", default="single", choices=["pairs", "single"],
                     help="tensor-core far field (d = 3, BF16 forms): two far entries per thread or one")
+    ap.add_argument("--radial-compression", default="auto", choices=["auto", "off"],
+                    help="drop the radial terms that vanish for the kernel (1/r in d = 3: j > k)")
     ap.add_argument("--compare", default="fp32", choices=["fp32", "none"],
                     help="plain float32 form (near and far on the CUDA cores) timed beside the headline one")
     ap.add_argument("--second-kernel", default="cauchy", choices=list(KERNELS) + ["none"],
@@ -344,7 +348,9 @@ def rooflines(a, stats, head, nsm, peaks, src, kname, passes):
                                 f"{mufu_ops}/{MUFU_LANES:.0f} MUFU) SM-clocks per pair ({src} clock)"}
     roofs = [near_roof]
     if stats["far_pairs"] > 0 and head["far_ms"]:
-        ops = far_pair_ops(a.p)
+        diag = stats.get("nterms") == (a.p + 1) ** 2 and a.p > 0 and a.kern[0] == "laplace"
+        nt_used = stats.get("nterms") or nterms(3, a.p)
+        ops = far_pair_ops(a.p, diag)
         far_peak = nsm * sm_max * 1e6 * FP32_LANES / ops
         far_ach = stats["far_pairs"] / (head["far_ms"] / 1e3)
         far_name = far_kernel_name(a.p, a.far_precision, a.nrhs, a.far_kernel)
@@ -352,12 +358,13 @@ def rooflines(a, stats, head, nsm, peaks, src, kname, passes):
                 "unit": "Gpair/s", "frac": far_ach / far_peak, "traffic": PROFILED_TRAFFIC.get((far_name,) + key),
                 "traffic_unit": "bytes per launch (ncu dram__bytes_read + write)", "ms_per_step": head["far_ms"],
                 "work_per_unit": f"{ops} FP32 lane-ops per (target, far node) pair (basis), "
-                                 f"+ 2 x {nterms(3, a.p)} x nrhs contraction flops",
+                                 f"+ 2 x {nt_used} x nrhs contraction flops"
+                                 f"{' (radially compressed expansion: j = k terms only)' if diag else ''}",
                 "peak_source": f"{nsm} SMs x {sm_max:.0f} MHz x {FP32_LANES:.0f} lanes / {ops} ({src} clock); "
                                f"far stage time on its stream"}
         if a.far_precision != "fp32":
             copies = 3 if a.far_precision == "bf16x3" else 1
-            flops = 2.0 * stats["far_pairs"] * nterms(3, a.p) * a.nrhs * copies
+            flops = 2.0 * stats["far_pairs"] * nt_used * a.nrhs * copies
             peak_tf = peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops", 1900.0))
             if a.far_precision == "tf32":
                 peak_tf *= 0.5  # nominal TF32 : BF16 dense ratio
@@ -405,6 +412,8 @@ def run_ours(a):
     obj.set_option("near_precision", a.near_precision)
     if not batch:
         obj.set_option("far_kernel", a.far_kernel)
+        obj.set_option("radial_compression", a.radial_compression)
+        stats = obj.stats()
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     stream = torch.cuda.current_stream()
 

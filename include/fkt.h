@@ -374,14 +374,16 @@ int fkt_plan_lists(fkt_plan_t plan, int64_t* block_range, int64_t* far_off, int3
 int fkt_shard_partition(int64_t nblocks, const double* work, int nranks, int64_t* bounds);
 
 /* The work of each target block (host [target_blocks], from fkt_plan_stats) that the partition
- * balances: near pairs plus 30 x far pairs.  Synchronizes.  FKT_ERR_UNSUPPORTED for batch plans. */
+ * balances, near pairs plus 50 x far pairs, with the blocks in target order (sorted by their first
+ * target; fkt_plan_lists lists them leaf by leaf).  Synchronizes.  FKT_ERR_UNSUPPORTED for batch
+ * plans. */
 int fkt_shard_block_work(fkt_plan_t plan, double* work);
 
 /* Select this process's share: rank in 0..nranks-1.  Partitions the blocks (fkt_shard_partition
  * over fkt_shard_block_work) and cuts the s2m work to the rank's sources.  Synchronizes. */
 int fkt_shard_set(fkt_plan_t plan, int nranks, int rank);
 
-/* The selected share: target blocks [block_lo, block_hi), sorted targets [target_lo, target_hi)
+/* The selected share: target blocks [block_lo, block_hi) in target order, sorted targets [target_lo, target_hi)
  * (positions in tree order; fkt_plan_tree's perm maps them to the caller's indices), and the size
  * in floats of the multipole array that fkt_mvm_shard_begin fills for nrhs right-hand sides.
  * Any pointer may be NULL.  FKT_ERR_INVALID_ARG before fkt_shard_set. */

@@ -49,6 +49,33 @@ int valid_kernel(const fkt_kernel& k) {
 
 }  // namespace
 
+namespace fkt {
+
+// The radial compression that is exact for the kernel: the Laplace kernel in d = 3, whose degree-k
+// radial parts have rank 1 (Table 3), keeps only its j = k terms.
+bool radial_compression_exact(int d, int kind) { return d == 3 && kind == FKT_LAPLACE; }
+
+// Switch the expansion layout and size; the per-call work buffers depend on it, so they are freed
+// and regrown by the next product.
+void set_radial_compression(fkt_plan_s* P, bool on) {
+    long long nt = 1;  // binom(p + d, d): every radial term
+    for (int i = 1; i <= P->d; ++i) nt = nt * (P->p + i) / i;
+    const int want = on ? (P->p + 1) * (P->p + 1) : (int)nt;  // j = k only: sum_k (2k + 1)
+    if (P->diag == on && P->nterms == want) return;
+    P->diag = on;
+    P->nterms = want;
+    P->stats.nterms = want;
+    for (void** b : {(void**)&P->rec, (void**)&P->ynear, (void**)&P->yfar, (void**)&P->mult, (void**)&P->s2m_part,
+                     (void**)&P->tc_image}) {
+        cudaFree(*b);
+        *b = nullptr;
+    }
+    P->cap_rhs = 0;
+    P->cap_tc = 0;
+}
+
+}  // namespace fkt
+
 extern "C" {
 
 const char* fkt_error_string(int status) {
@@ -87,11 +114,7 @@ int fkt_plan(const float* points, int64_t N, int d, fkt_kernel kernel, int p, in
     if (cudaGetDevice(&P->device) != cudaSuccess) { free_plan(P); return FKT_ERR_CUDA; }
     int rc = fkt::build_far_tables(d, p, &P->tabs);
     if (rc) { free_plan(P); return rc; }
-    {
-        long long nt = 1;  // binom(p + d, d)
-        for (int i = 1; i <= d; ++i) nt = nt * (p + i) / i;
-        P->nterms = (int)nt;
-    }
+    fkt::set_radial_compression(P, fkt::radial_compression_exact(d, kernel.kind));
     if (fkt::create_far_stream(&P->stream2) != FKT_OK) { free_plan(P); return FKT_ERR_CUDA; }
     for (auto& e : P->ev)
         if (cudaEventCreate(&e) != cudaSuccess) { free_plan(P); return FKT_ERR_CUDA; }
@@ -228,6 +251,12 @@ int fkt_set_option(fkt_plan_t plan, const char* key, const char* value) {
         } else {
             plan->coarse_seed = (uint64_t)v;
         }
+        return FKT_OK;
+    }
+    if (!strcmp(key, "radial_compression")) {
+        if (!strcmp(value, "off")) fkt::set_radial_compression(plan, false);
+        else if (!strcmp(value, "auto")) fkt::set_radial_compression(plan, fkt::radial_compression_exact(plan->d, plan->kernel.kind) && !plan->nprob);
+        else return FKT_ERR_INVALID_ARG;
         return FKT_OK;
     }
     if (!strcmp(key, "far_kernel")) {

@@ -295,8 +295,11 @@ int fkt_batch_plan(int nprob, const fkt_problem* probs, int d, int p, int leaf_s
     }
     std::vector<fkt_plan_s*> plans(nprob, nullptr);
     int rc = FKT_OK;
-    for (int i = 0; i < nprob && !rc; ++i)
+    for (int i = 0; i < nprob && !rc; ++i) {
         rc = fkt_plan(probs[i].points, probs[i].N, d, probs[i].kernel, p, Bt->leaf_of[i], theta, cuda_stream, &plans[i]);
+        // one expansion layout for all problems of the batch: the full one
+        if (!rc) fkt::set_radial_compression(plans[i], false);
+    }
     fkt_plan_s* M = nullptr;
     if (!rc) {
         M = new fkt_plan_s();

@@ -113,7 +113,7 @@ template <int D, int P, class F>
 __device__ __forceinline__ void far_basis(const float4& xt, const float4& c, float s, const KernelParams& kp,
                                           const FarTables& T, F&& put) {
     using Lay = Layout<D, P>;
-    const float dx = xt.x - c.x, dy = xt.y - c.y, dz = xt.z - c.z, dw = D == 4 ? xt.w - c.w : 0.f;
+    const float dx = xt.x - c.x, dy = xt.y - c.y, dz = xt.z - c.z, dw = dim_of(D) == 4 ? xt.w - c.w : 0.f;
     const float r2 = dx * dx + dy * dy + dz * dz + dw * dw;
     const float rinv = rsqrtf(r2);
     const float r = r2 * rinv;
@@ -129,10 +129,10 @@ __device__ __forceinline__ void far_basis(const float4& xt, const float4& c, flo
     for (int k = 0; k <= P; ++k)
 #pragma unroll
         for (int jj = 0; jj < Lay::nj(k); ++jj) {
-            const int j = k + 2 * jj, q = Lay::pair(k) + jj;
+            const int j = k + 2 * jj, q = Lay::pair(k) + jj, tq = Lay::tpair(k, jj);
             float R = 0.f;
 #pragma unroll
-            for (int m = 0; m <= j; ++m) R = fmaf(T.That[q][m], J[m], R);
+            for (int m = 0; m <= j; ++m) R = fmaf(T.That[tq][m], J[m], R);
             G[q] = up[j] * R;
         }
     const float ux = dx * rinv, uy = dy * rinv, uz = dz * rinv, uw = dw * rinv;
@@ -312,9 +312,9 @@ __global__ void __launch_bounds__(kTB) far_tc_kernel(MvmArgs a, KernelParams kp_
 //     issues the MMAs (rows outside the mask disabled) and commits them to mma_done.
 // The accumulator is flushed because the tensor core's float32 accumulation drifts over
 // thousands of MMAs.  Every wait is bounded.
-template <int P, int PREC>
+template <int P, int PREC, int LD = 3>
 struct Tc2Shape {
-    using S = TcShape<3, P, PREC>;
+    using S = TcShape<LD, P, PREC>;
     static constexpr int NT = S::NT, NTP = S::NTP;
     static constexpr int PLANE_COLS = NTP / 2;                     // packed BF16 pairs per plane
     static constexpr int COL_AHI = 32, COL_ALO = 32 + PLANE_COLS;
@@ -390,16 +390,16 @@ int launch_tc_far_t(const TcLaunch& L) {
             return FKT_OK;
         }
     }
-    if constexpr (D == 3 && Tc2Shape<P, PREC>::supported) {
-        using Sh = Tc2Shape<P, PREC>;
+    if constexpr (dim_of(D) == 3 && Tc2Shape<P, PREC, D>::supported) {
+        using Sh = Tc2Shape<P, PREC, D>;
         const size_t smem = Sh::smem_bytes();
         static bool attr = false;
         if (!attr) {
-            FKT_CUDA_TRY(cudaFuncSetAttribute(far_tc2_kernel<P, PREC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+            FKT_CUDA_TRY(cudaFuncSetAttribute(far_tc2_kernel<P, PREC, D>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                               (int)smem));
             attr = true;
         }
-        far_tc2_kernel<P, PREC><<<(unsigned)L.nblocks, Sh::THREADS, smem, L.s_far>>>(*L.a, *L.kp, *L.T, L.image, L.nr_total);
+        far_tc2_kernel<P, PREC, D><<<(unsigned)L.nblocks, Sh::THREADS, smem, L.s_far>>>(*L.a, *L.kp, *L.T, L.image, L.nr_total);
         FKT_CUDA_TRY(cudaGetLastError());
         return FKT_OK;
     } else if constexpr (!S::supported) {
@@ -430,9 +430,7 @@ int launch_tc_range(int p, int prec, bool far, const TcLaunch& L) {
 }
 
 // Bytes of the packed B-operand image per node.
-inline int tc_b_bytes(int d, int p, int prec) {
-    int nt = 1;
-    for (int i = 1; i <= d; ++i) nt = nt * (p + i) / i;
+inline int tc_b_bytes(int nt, int prec) {
     const int ntp = (nt + 15) / 16 * 16;
     const int el = prec == TC_TF32 ? 4 : 2;
     return kTcN * ntp * el * (prec == TC_BF16X3 ? 2 : 1);

@@ -19,11 +19,11 @@ namespace fkt {
 
 // Scalar harmonics of degree L and above (compile-time recursion: constant array indices), as
 // harmonic_level for packed pairs.
-template <int P, int L, class F>
+template <int P, int LD, int L, class F>
 __device__ __forceinline__ void harmonic_level1(float uz, const float (&C)[P + 1], const float (&S)[P + 1],
                                                 float (&pm1)[P + 1], float (&pm2)[P + 1],
-                                                const float (&G)[Layout<3, P>::npairs], const FarTables& T, F&& put) {
-    using Lay = Layout<3, P>;
+                                                const float (&G)[Layout<LD, P>::npairs], const FarTables& T, F&& put) {
+    using Lay = Layout<LD, P>;
     float cur[L + 1];
 #pragma unroll
     for (int m = 0; m <= L; ++m) {
@@ -47,15 +47,16 @@ __device__ __forceinline__ void harmonic_level1(float uz, const float (&C)[P + 1
         pm2[m] = pm1[m];
         pm1[m] = cur[m];
     }
-    if constexpr (L < P) harmonic_level1<P, L + 1>(uz, C, S, pm1, pm2, G, T, put);
+    if constexpr (L < P) harmonic_level1<P, LD, L + 1>(uz, C, S, pm1, pm2, G, T, put);
 }
 
 // The basis row of one (target, far node) pair, put(q, U[q]) for q = 0..NT-1 in increasing order
-// (the expansion of far_basis<3, P>, with |u|^2 = 1 in the recurrence of the unit direction).
-template <int P, class F>
+// (the expansion of far_basis<LD, P>, with |u|^2 = 1 in the recurrence of the unit direction).
+// LD = 3 or kDiag3 (layout codes of fkt_kernels.cuh).
+template <int P, int LD, class F>
 __device__ __forceinline__ void far_basis1(const float4& xt, const float4& c, float s, const KernelParams& kp,
                                            const FarTables& T, F&& put) {
-    using Lay = Layout<3, P>;
+    using Lay = Layout<LD, P>;
     const float dx = xt.x - c.x, dy = xt.y - c.y, dz = xt.z - c.z;
     const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
     const float rinv = rsqrtf(r2);
@@ -73,10 +74,10 @@ __device__ __forceinline__ void far_basis1(const float4& xt, const float4& c, fl
         for (int k = 0; k <= P; ++k)
 #pragma unroll
             for (int jj = 0; jj < Lay::nj(k); ++jj) {
-                const int j = k + 2 * jj, q = Lay::pair(k) + jj;
-                float R = T.That[q][0] * J[0];
+                const int j = k + 2 * jj, q = Lay::pair(k) + jj, tq = Lay::tpair(k, jj);
+                float R = T.That[tq][0] * J[0];
 #pragma unroll
-                for (int m = 1; m <= j; ++m) R = fmaf(T.That[q][m], J[m], R);
+                for (int m = 1; m <= j; ++m) R = fmaf(T.That[tq][m], J[m], R);
                 G[q] = up[j] * R;
             }
     }
@@ -92,14 +93,14 @@ __device__ __forceinline__ void far_basis1(const float4& xt, const float4& c, fl
     float pm2[P + 1], pm1[P + 1];
 #pragma unroll
     for (int m = 0; m <= P; ++m) pm2[m] = pm1[m] = 0.f;
-    harmonic_level1<P, 0>(uz, C, S, pm1, pm2, G, T, put);
+    harmonic_level1<P, LD, 0>(uz, C, S, pm1, pm2, G, T, put);
 }
 
-template <int P, int PREC>
-__global__ void __launch_bounds__(160, P <= 6 ? 4 : P <= 7 ? 3 : 2)
+template <int P, int PREC, int LD = 3>
+__global__ void __launch_bounds__(160, Tc2Shape<P, PREC, LD>::NTP <= 96 ? 4 : Tc2Shape<P, PREC, LD>::NTP <= 128 ? 3 : 2)
     far_tc2_kernel(MvmArgs a, KernelParams kp_all, const __grid_constant__ FarTables T,
                    const unsigned char* __restrict__ image, int nr_total) {
-    using Sh = Tc2Shape<P, PREC>;
+    using Sh = Tc2Shape<P, PREC, LD>;
     using S = typename Sh::S;
     constexpr int NT = Sh::NT, NTP = Sh::NTP, ST = Sh::ST, BB = S::B_BYTES, BPLANE = kTcN * NTP * 2;
     constexpr int kFarFlush = 4;
@@ -289,7 +290,7 @@ __global__ void __launch_bounds__(160, P <= 6 ? 4 : P <= 7 ? 3 : 2)
                     tc::st8(tmem + lane_base + Sh::COL_AHI + g * 8, hi);
                     if (PREC == TC_BF16X3) tc::st8(tmem + lane_base + Sh::COL_ALO + g * 8, lo);
                 };
-                far_basis1<P>(xt, c, sc, kp, T, [&](int q, float v) {
+                far_basis1<P, LD>(xt, c, sc, kp, T, [&](int q, float v) {
                     if (q & 1) buf[(q & 15) >> 1].y = v;
                     else buf[(q & 15) >> 1].x = v;
                     if (q == NT - 1) {

@@ -222,10 +222,10 @@ __device__ __forceinline__ void far_basis2(const float4& xt, float2 cx, float2 c
         for (int k = 0; k <= P; ++k)
 #pragma unroll
             for (int jj = 0; jj < Lay::nj(k); ++jj) {
-                const int j = k + 2 * jj, q = Lay::pair(k) + jj;
-                float2 R = mul(T.That[q][0], J[0]);
+                const int j = k + 2 * jj, q = Lay::pair(k) + jj, tq = Lay::tpair(k, jj);
+                float2 R = mul(T.That[tq][0], J[0]);
 #pragma unroll
-                for (int m = 1; m <= j; ++m) R = fma(T.That[q][m], J[m], R);
+                for (int m = 1; m <= j; ++m) R = fma(T.That[tq][m], J[m], R);
                 G[q] = mul(up[j], R);
             }
     }

@@ -1,0 +1,9 @@
+// Instantiations of the tensor-core far field for the compressed d = 3 layout (j = k terms only,
+// the Laplace kernel), orders 7..10.
+#include "far_tc.cuh"
+
+namespace fkt {
+
+int launch_tc_diag_p7_10(int p, int prec, bool far, const TcLaunch& L) { return launch_tc_range<kDiag3, 7, 10>(p, prec, far, L); }
+
+}  // namespace fkt

@@ -65,6 +65,7 @@ struct fkt_plan_s {
     int near_tpt = 2;              // near-field targets per thread (2 or 4)
     int near_precision = fkt::NEAR_FP32;  // near-field contraction of 32-wide passes
     int far_kernel = 1;            // tensor-core far field, d = 3 BF16 forms: 0 = two entries per thread, 1 = one
+    bool diag = false;             // radial compression: only the j = k terms (Laplace kernel, d = 3)
     // bounding cube
     double lo[4] = {0, 0, 0, 0};
     double L = 1.0;
@@ -152,7 +153,8 @@ struct fkt_plan_s {
     int graph_nrhs = 0;
     // target-sharded product (shard.cu): this rank's share of the partition
     int sh_nranks = 0, sh_rank = 0;             // 0 ranks: no share selected
-    int64_t sh_b0 = 0, sh_b1 = 0;               // target blocks [b0, b1)
+    int64_t sh_b0 = 0, sh_b1 = 0;               // target blocks [b0, b1) in target order
+    int32_t* sh_blocks = nullptr;               // device: their block indices
     int64_t sh_t0 = 0, sh_t1 = 0;               // sorted targets (= owned sources) [t0, t1)
     int4* sh_items = nullptr;                   // device: the s2m items cut to [t0, t1)
     int64_t* sh_item_off = nullptr;             // device: [nodes + 1] item offsets per node
@@ -162,6 +164,10 @@ struct fkt_plan_s {
 };
 
 namespace fkt {
+
+// api.cu
+bool radial_compression_exact(int d, int kind);
+void set_radial_compression(fkt_plan_s* P, bool on);
 
 // tables.cpp
 int build_far_tables(int d, int p, FarTables* out);
@@ -204,7 +210,7 @@ int free_batch_arrays(fkt_plan_s* P);
 // shard.cu
 int shard_partition(int64_t nblocks, const double* work, int nranks, int64_t* bounds);
 int shard_set(fkt_plan_s* P, int nranks, int rank);
-int shard_block_work(fkt_plan_s* P, std::vector<double>& work);
+int shard_block_work(fkt_plan_s* P, std::vector<double>& work, std::vector<int32_t>* order = nullptr);
 void free_shard(fkt_plan_s* P);
 // mvm.cu: the two phases of the sharded product (one pass of <= 32 right-hand sides)
 size_t shard_mult_floats(const fkt_plan_s* P, int nrhs);

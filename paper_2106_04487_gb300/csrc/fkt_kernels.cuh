@@ -17,10 +17,25 @@
 namespace fkt {
 
 // ----------------------------------------------------------------- layout
+// Layout code D of the expansion: 3 or 4 = every radial term j = k, k+2, ..., <= P of each
+// degree k in that dimension; kDiag3 = d = 3 with the j = k term only.  The latter is the radial
+// compression of the Laplace kernel 1/r in d = 3: its degree-k radial part has rank 1 (Table 3),
+// being r'^k / r^(k+1) alone (the Legendre multipole expansion of Sec. 3.3, eq. electro), so the
+// terms j > k vanish identically and are dropped from s2m, the multipoles and m2t.
+constexpr int kDiag3 = 103;
+__host__ __device__ constexpr int dim_of(int D) { return D % 100; }
+__host__ __device__ constexpr bool diag_of(int D) { return D >= 100; }
+
 template <int D, int P>
 struct Layout {
-    static constexpr int nj(int k) { return (P - k) / 2 + 1; }
-    static constexpr int dk(int k) { return D == 3 ? 2 * k + 1 : (k + 1) * (k + 1); }
+    static constexpr int nj(int k) { return diag_of(D) ? 1 : (P - k) / 2 + 1; }
+    static constexpr int dk(int k) { return dim_of(D) == 3 ? 2 * k + 1 : (k + 1) * (k + 1); }
+    // row of the expansion tables (built for the full layout) of radial pair (k, j = k + 2 jj)
+    static constexpr int tpair(int k, int jj) {
+        int o = 0;
+        for (int i = 0; i < k; ++i) o += (P - i) / 2 + 1;
+        return o + jj;
+    }
     static constexpr int off(int k) {
         int o = 0;
         for (int i = 0; i < k; ++i) o += dk(i) * nj(i);
@@ -173,7 +188,7 @@ __device__ __forceinline__ void solid_harmonics(float x0, float x1, float x2, fl
             else if (m == l - 1) cur[m] = T.hA[l][m] * x2 * pm1[m];
             else cur[m] = T.hA[l][m] * x2 * pm1[m] - T.hB[l][m] * r2_3 * pm2[m];
         }
-        if (D == 3) {
+        if (dim_of(D) == 3) {
             f(l, 0, cur[0]);
 #pragma unroll
             for (int m = 1; m <= l; ++m) {
@@ -237,7 +252,6 @@ struct MvmArgs {
     const int32_t* blk_prob;   // problem of each target block
     const int32_t* blk_list;   // grid index -> target block (work ordered largest first)
     const float* pt_sig;       // near-field coordinate scale of each point's problem
-    int64_t blk_base;          // first target block of the launch (a rank's share of a sharded product)
     // limit, in SM clocks, of the pipeline waits of the tensor-core kernels (record / multipole
     // copies landing, the consumers' hand-off to the MMA issuer); the waits that drain work in
     // flight before a CTA exits always use kWaitCycles
@@ -246,7 +260,7 @@ struct MvmArgs {
 
 // Target block handled by this CTA and its kernel parameters (per problem in a batch).
 __device__ __forceinline__ int64_t cta_block(const MvmArgs& a) {
-    return a.blk_list ? (int64_t)a.blk_list[blockIdx.x] : a.blk_base + (int64_t)blockIdx.x;
+    return a.blk_list ? (int64_t)a.blk_list[blockIdx.x] : (int64_t)blockIdx.x;
 }
 __device__ __forceinline__ KernelParams block_params(const MvmArgs& a, int64_t blk, const KernelParams& kp) {
     return a.kps ? a.kps[a.blk_prob[blk]] : kp;

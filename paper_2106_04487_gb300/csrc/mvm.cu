@@ -24,6 +24,12 @@ FKT_DECL_RANGE(4, 0, 4)
 FKT_DECL_RANGE(4, 5, 6)
 FKT_DECL_RANGE(4, 7, 8)
 #undef FKT_DECL_RANGE
+int launch_s2m_diag_p0_5(int p, int nrb, const FarLaunch& L);
+int launch_far_diag_p0_5(int p, int nrb, const FarLaunch& L);
+int launch_s2m_diag_p6_10(int p, int nrb, const FarLaunch& L);
+int launch_far_diag_p6_10(int p, int nrb, const FarLaunch& L);
+int launch_tc_diag_p0_6(int p, int prec, bool far, const TcLaunch& L);
+int launch_tc_diag_p7_10(int p, int prec, bool far, const TcLaunch& L);
 
 void launch_near_d3(int nw, int tpt, int kind, unsigned grid, cudaStream_t st, const MvmArgs& a, const KernelParams& kp);
 void launch_near_d4(int nw, int tpt, int kind, unsigned grid, cudaStream_t st, const MvmArgs& a, const KernelParams& kp);
@@ -35,16 +41,23 @@ int launch_tc_d3_p7_10(int p, int prec, bool far, const TcLaunch& L);
 int launch_tc_d4_p0_5(int p, int prec, bool far, const TcLaunch& L);
 int launch_tc_d4_p6_8(int p, int prec, bool far, const TcLaunch& L);
 
+// d: the layout code (3, 4, or kDiag3 for the compressed d = 3 layout).
 static int launch_tc_any(int d, int p, int prec, bool far, const TcLaunch& L) {
+    if (d == kDiag3) return p <= 6 ? launch_tc_diag_p0_6(p, prec, far, L) : launch_tc_diag_p7_10(p, prec, far, L);
     if (d == 3) return p <= 6 ? launch_tc_d3_p0_6(p, prec, far, L) : launch_tc_d3_p7_10(p, prec, far, L);
     return p <= 5 ? launch_tc_d4_p0_5(p, prec, far, L) : launch_tc_d4_p6_8(p, prec, far, L);
 }
+
+// Layout code of the plan's expansion (fkt_kernels.cuh): the compressed d = 3 layout when the
+// radial compression is on, otherwise the dimension.
+static int layout_code(const fkt_plan_s* P) { return P->diag ? kDiag3 : P->d; }
 
 static int tc_prec_of(int far_precision) {
     return far_precision == FAR_BF16 ? TC_BF16 : far_precision == FAR_BF16X3 ? TC_BF16X3 : TC_TF32;
 }
 
 static int launch_s2m_any(int d, int p, int nrb, const FarLaunch& L) {
+    if (d == kDiag3) return p <= 5 ? launch_s2m_diag_p0_5(p, nrb, L) : launch_s2m_diag_p6_10(p, nrb, L);
     if (d == 3) {
         if (p <= 4) return launch_s2m_d3_p0_4(p, nrb, L);
         if (p <= 6) return launch_s2m_d3_p5_6(p, nrb, L);
@@ -57,6 +70,7 @@ static int launch_s2m_any(int d, int p, int nrb, const FarLaunch& L) {
 }
 
 static int launch_far_any(int d, int p, int nrb, const FarLaunch& L) {
+    if (d == kDiag3) return p <= 5 ? launch_far_diag_p0_5(p, nrb, L) : launch_far_diag_p6_10(p, nrb, L);
     if (d == 3) {
         if (p <= 4) return launch_far_d3_p0_4(p, nrb, L);
         if (p <= 6) return launch_far_d3_p5_6(p, nrb, L);
@@ -186,7 +200,7 @@ void mvm_buffer_floats(const fkt_plan_s* P, int nrhs, size_t out[kMvmBufs]) {
     out[2] = round64(groups * nrb * NT * nodes);         // multipoles
     out[3] = round64(groups * nrb * NT * items);         // s2m partials
     out[4] = P->far_precision == FAR_FP32 ? 0
-             : round64(nodes * (size_t)tc_b_bytes(P->d, P->p, tc_prec_of(P->far_precision)) / 4);
+             : round64(nodes * (size_t)tc_b_bytes(P->nterms, tc_prec_of(P->far_precision)) / 4);
     out[5] = round64(groups * nrb * N);                  // far result
 }
 
@@ -279,7 +293,7 @@ int run_mvm(fkt_plan_s* P, const MvmBuffers& B, const float* w, float* y, int nr
             ag.part = B.part + (size_t)g * nrb * NT * items;
             ag.nr = std::min(nrb, nrhs - g * nrb);
             FarLaunch L{&ag, &P->kp, &P->tabs, P->nblocks, P->n_s2m_items, P->nnodes, st2, st2};
-            int rc = launch_s2m_any(P->d, P->p, nrb, L);
+            int rc = launch_s2m_any(layout_code(P), P->p, nrb, L);
             if (rc) return rc;
         }
         if (timing) FKT_CUDA_TRY(cudaEventRecord(P->ev[3], st2));
@@ -294,7 +308,7 @@ int run_mvm(fkt_plan_s* P, const MvmBuffers& B, const float* w, float* y, int nr
                 ag.yfar = B.yfar + (size_t)g * nrb * N;
                 ag.nr = std::min(nrb, nrhs - g * nrb);
                 FarLaunch L{&ag, &P->kp, &P->tabs, P->nblocks, P->n_s2m_items, P->nnodes, st2, st2};
-                int rc = launch_far_any(P->d, P->p, nrb, L);
+                int rc = launch_far_any(layout_code(P), P->p, nrb, L);
                 if (rc) return rc;
             }
         } else {
@@ -302,9 +316,9 @@ int run_mvm(fkt_plan_s* P, const MvmBuffers& B, const float* w, float* y, int nr
             af.yfar = B.yfar + (size_t)r0 * N;
             TcLaunch T{&af, &P->kp, &P->tabs, P->nblocks, P->nnodes, (int64_t)(8 * NT * nodes), npass, B.image, st2, st2,
                        P->far_kernel};
-            int rc = launch_tc_any(P->d, P->p, tc_prec_of(P->far_precision), false, T);  // pack
+            int rc = launch_tc_any(layout_code(P), P->p, tc_prec_of(P->far_precision), false, T);  // pack
             if (rc) return rc;
-            rc = launch_tc_any(P->d, P->p, tc_prec_of(P->far_precision), true, T);
+            rc = launch_tc_any(layout_code(P), P->p, tc_prec_of(P->far_precision), true, T);
             if (rc) return rc;
         }
         if (timing) FKT_CUDA_TRY(cudaEventRecord(P->ev[9], st2));
@@ -360,7 +374,7 @@ int shard_begin(fkt_plan_s* P, const float* w, float* mult, int nrhs) {
         ag.part = P->s2m_part + (size_t)g * nrb * NT * std::max<int64_t>(P->n_s2m_items, 1);
         ag.nr = std::min(nrb, nrhs - g * nrb);
         FarLaunch L{&ag, &P->kp, &P->tabs, P->nblocks, P->sh_nitems, P->nnodes, st, st};
-        if ((rc = launch_s2m_any(P->d, P->p, nrb, L))) return rc;
+        if ((rc = launch_s2m_any(layout_code(P), P->p, nrb, L))) return rc;
     }
     return FKT_OK;
 }
@@ -378,7 +392,7 @@ int shard_end(fkt_plan_s* P, const float* mult, float* y, int nrhs) {
     MvmArgs a = base_args(P);
     a.rec = P->rec;
     a.rec_f4 = rec_f4(P->d, nw);
-    a.blk_base = P->sh_b0;
+    a.blk_list = P->sh_blocks;
     if (!tc) {
         for (int g = 0; g < ng; ++g) {
             MvmArgs ag = a;
@@ -386,7 +400,7 @@ int shard_end(fkt_plan_s* P, const float* mult, float* y, int nrhs) {
             ag.yfar = P->yfar + (size_t)g * nrb * N;
             ag.nr = std::min(nrb, nrhs - g * nrb);
             FarLaunch L{&ag, &P->kp, &P->tabs, nb, P->n_s2m_items, P->nnodes, st, st};
-            int rc = launch_far_any(P->d, P->p, nrb, L);
+            int rc = launch_far_any(layout_code(P), P->p, nrb, L);
             if (rc) return rc;
         }
     } else {
@@ -395,8 +409,8 @@ int shard_end(fkt_plan_s* P, const float* mult, float* y, int nrhs) {
         af.yfar = P->yfar;
         TcLaunch T{&af, &P->kp, &P->tabs, nb, P->nnodes, (int64_t)(8 * NT * nodes), nrhs, P->tc_image, st, st,
                    P->far_kernel};
-        int rc = launch_tc_any(P->d, P->p, tc_prec_of(P->far_precision), false, T);  // pack every used node
-        if (!rc) rc = launch_tc_any(P->d, P->p, tc_prec_of(P->far_precision), true, T);
+        int rc = launch_tc_any(layout_code(P), P->p, tc_prec_of(P->far_precision), false, T);  // pack every used node
+        if (!rc) rc = launch_tc_any(layout_code(P), P->p, tc_prec_of(P->far_precision), true, T);
         if (rc) return rc;
     }
     a.ynear = P->ynear;

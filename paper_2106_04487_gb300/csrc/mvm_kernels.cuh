@@ -97,7 +97,7 @@ s2m_kernel(MvmArgs a, const __grid_constant__ FarTables T) {
         const bool ok = s < it.z;
         float4 x = ok ? a.xs[s] : c;
         float x0 = (x.x - c.x) * inv_s, x1 = (x.y - c.y) * inv_s, x2 = (x.z - c.z) * inv_s;
-        float x3 = D == 4 ? (x.w - c.w) * inv_s : 0.f;
+        float x3 = dim_of(D) == 4 ? (x.w - c.w) * inv_s : 0.f;
         float r2_3 = x0 * x0 + x1 * x1 + x2 * x2;
         float r2 = r2_3 + x3 * x3;
         float rp[P / 2 + 1];  // (r'^2)^i
@@ -826,7 +826,7 @@ __global__ void __launch_bounds__(kTB) far_kernel(MvmArgs a, KernelParams kp_all
         for (int e = 0; e < nb; ++e) {
             if (!(valid && entry_active(s_m[e], a.masks, tl))) continue;
             const float4 c = s_c[e];
-            const float dx = xt.x - c.x, dy = xt.y - c.y, dz = xt.z - c.z, dw = D == 4 ? xt.w - c.w : 0.f;
+            const float dx = xt.x - c.x, dy = xt.y - c.y, dz = xt.z - c.z, dw = dim_of(D) == 4 ? xt.w - c.w : 0.f;
             const float r2 = dx * dx + dy * dy + dz * dz + dw * dw;
             const float rinv = rsqrtf(r2);
             const float r = r2 * rinv;
@@ -842,10 +842,10 @@ __global__ void __launch_bounds__(kTB) far_kernel(MvmArgs a, KernelParams kp_all
             for (int k = 0; k <= P; ++k)
 #pragma unroll
                 for (int jj = 0; jj < Lay::nj(k); ++jj) {
-                    const int j = k + 2 * jj, q = Lay::pair(k) + jj;
+                    const int j = k + 2 * jj, q = Lay::pair(k) + jj, tq = Lay::tpair(k, jj);
                     float R = 0.f;
 #pragma unroll
-                    for (int m = 0; m <= j; ++m) R = fmaf(T.That[q][m], J[m], R);
+                    for (int m = 0; m <= j; ++m) R = fmaf(T.That[tq][m], J[m], R);
                     G[q] = up[j] * R;
                 }
             const float ux = dx * rinv, uy = dy * rinv, uz = dz * rinv, uw = dw * rinv;
@@ -916,7 +916,7 @@ __global__ void __launch_bounds__(kTB) far_mr_kernel(MvmArgs a, KernelParams kp_
         __syncthreads();
         if (!(valid && entry_active(s_m, a.masks, tl))) continue;
         const float4 c = s_c;
-        const float dx = xt.x - c.x, dy = xt.y - c.y, dz = xt.z - c.z, dw = D == 4 ? xt.w - c.w : 0.f;
+        const float dx = xt.x - c.x, dy = xt.y - c.y, dz = xt.z - c.z, dw = dim_of(D) == 4 ? xt.w - c.w : 0.f;
         const float r2 = dx * dx + dy * dy + dz * dz + dw * dw;
         const float rinv = rsqrtf(r2);
         const float r = r2 * rinv;
@@ -932,10 +932,10 @@ __global__ void __launch_bounds__(kTB) far_mr_kernel(MvmArgs a, KernelParams kp_
         for (int k = 0; k <= P; ++k)
 #pragma unroll
             for (int jj = 0; jj < Lay::nj(k); ++jj) {
-                const int j = k + 2 * jj, q = Lay::pair(k) + jj;
+                const int j = k + 2 * jj, q = Lay::pair(k) + jj, tq = Lay::tpair(k, jj);
                 float R = 0.f;
 #pragma unroll
-                for (int m = 0; m <= j; ++m) R = fmaf(T.That[q][m], J[m], R);
+                for (int m = 0; m <= j; ++m) R = fmaf(T.That[tq][m], J[m], R);
                 G[q] = up[j] * R;
             }
         const float ux = dx * rinv, uy = dy * rinv, uz = dz * rinv, uw = dw * rinv;

@@ -1,7 +1,7 @@
 // Target-sharded product over several processes (one GPU each): the host side.
 //
 // Every rank builds the same plan (the tree and lists are deterministic) from all the points.
-// The targets are partitioned into contiguous ranges of target blocks in tree (Morton) order,
+// The targets are partitioned into contiguous ranges of target blocks in target (tree, Morton) order,
 // balanced by the block's work: its near pairs plus kFarPairCost times its far pairs (the
 // per-target decisions of Sec. 3.1 are unchanged, so every (target, source) pair is still
 // evaluated exactly once, by the rank owning the target).  Rank r owns the sources in its target
@@ -17,8 +17,9 @@
 namespace fkt {
 
 // Relative cost of one (target, far node) pair against one near pair: the far basis row of
-// order p costs a few hundred lane operations against about ten for a near pair.
-constexpr double kFarPairCost = 30.0;
+// order p costs a few hundred lane operations against about ten for a near pair (measured at the
+// 1M-point Matern workload, p = 6: 20.8 ms for 2.5e8 far pairs, 18.5 ms for 1.3e10 near pairs).
+constexpr double kFarPairCost = 50.0;
 
 int shard_partition(int64_t nblocks, const double* work, int nranks, int64_t* bounds) {
     if (nblocks < 0 || nranks < 1 || !bounds || (nblocks > 0 && !work)) return FKT_ERR_INVALID_ARG;
@@ -47,7 +48,10 @@ static int popc4(const uint32_t* m) {
     return __builtin_popcount(m[0]) + __builtin_popcount(m[1]) + __builtin_popcount(m[2]) + __builtin_popcount(m[3]);
 }
 
-int shard_block_work(fkt_plan_s* P, std::vector<double>& work) {
+// The work of every target block, in target order (blocks sorted by their first target: the
+// plan enumerates them leaf by leaf, which is not the targets' tree order); order[i] = the
+// block index of the i-th block in that order.
+int shard_block_work(fkt_plan_s* P, std::vector<double>& work, std::vector<int32_t>* order_out) {
     const int64_t nb = P->nblocks, nn = P->nnodes;
     std::vector<int2> blk(nb), far_ent(P->nfar), near_ent(P->nnear);
     std::vector<int64_t> far_off(nb + 1), near_off(nb + 1);
@@ -63,8 +67,12 @@ int shard_block_work(fkt_plan_s* P, std::vector<double>& work) {
         FKT_CUDA_TRY(cudaMemcpy(masks.data(), P->masks, 4 * kMaskWords * P->nmasks, cudaMemcpyDeviceToHost));
     FKT_CUDA_TRY(cudaMemcpy(beg.data(), P->nd_begin, 4 * nn, cudaMemcpyDeviceToHost));
     FKT_CUDA_TRY(cudaMemcpy(end.data(), P->nd_end, 4 * nn, cudaMemcpyDeviceToHost));
+    std::vector<int32_t> order(nb);
+    for (int64_t b = 0; b < nb; ++b) order[b] = (int32_t)b;
+    std::sort(order.begin(), order.end(), [&](int32_t x, int32_t y) { return blk[x].x < blk[y].x; });
     work.assign(nb, 0.0);
-    for (int64_t b = 0; b < nb; ++b) {
+    for (int64_t ib = 0; ib < nb; ++ib) {
+        const int64_t b = order[ib];
         const int64_t nt = blk[b].y - blk[b].x;
         double w = 0.0;
         for (int64_t e = far_off[b]; e < far_off[b + 1]; ++e)
@@ -74,32 +82,36 @@ int shard_block_work(fkt_plan_s* P, std::vector<double>& work) {
             const int64_t nt_on = near_ent[e].y < 0 ? nt : popc4(&masks[(size_t)near_ent[e].y * kMaskWords]);
             w += (double)nt_on * (end[leaf] - beg[leaf]);
         }
-        work[b] = w;
+        work[ib] = w;
     }
+    if (order_out) *order_out = std::move(order);
     return FKT_OK;
 }
 
 void free_shard(fkt_plan_s* P) {
     cudaFree(P->sh_items);
     cudaFree(P->sh_item_off);
+    cudaFree(P->sh_blocks);
     P->sh_items = nullptr;
     P->sh_item_off = nullptr;
+    P->sh_blocks = nullptr;
     P->sh_nranks = 0;
 }
 
 int shard_set(fkt_plan_s* P, int nranks, int rank) {
     if (P->nprob) return FKT_ERR_UNSUPPORTED;
     std::vector<double> work;
-    int rc = shard_block_work(P, work);
+    std::vector<int32_t> order;
+    int rc = shard_block_work(P, work, &order);
     if (rc) return rc;
     std::vector<int64_t> bounds(nranks + 1);
     if ((rc = shard_partition(P->nblocks, work.data(), nranks, bounds.data()))) return rc;
     const int64_t b0 = bounds[rank], b1 = bounds[rank + 1];
     int64_t t0 = 0, t1 = 0;
-    if (b1 > b0) {
+    if (b1 > b0) {  // the rank's blocks, consecutive in target order, tile [t0, t1)
         int2 lo, hi;
-        FKT_CUDA_TRY(cudaMemcpy(&lo, P->blk_range + b0, sizeof(int2), cudaMemcpyDeviceToHost));
-        FKT_CUDA_TRY(cudaMemcpy(&hi, P->blk_range + b1 - 1, sizeof(int2), cudaMemcpyDeviceToHost));
+        FKT_CUDA_TRY(cudaMemcpy(&lo, P->blk_range + order[b0], sizeof(int2), cudaMemcpyDeviceToHost));
+        FKT_CUDA_TRY(cudaMemcpy(&hi, P->blk_range + order[b1 - 1], sizeof(int2), cudaMemcpyDeviceToHost));
         t0 = lo.x;
         t1 = hi.y;
     }
@@ -125,6 +137,9 @@ int shard_set(fkt_plan_s* P, int nranks, int rank) {
     if (!mine.empty())
         FKT_CUDA_TRY(cudaMemcpy(P->sh_items, mine.data(), sizeof(int4) * mine.size(), cudaMemcpyHostToDevice));
     FKT_CUDA_TRY(cudaMemcpy(P->sh_item_off, moff.data(), 8 * (nn + 1), cudaMemcpyHostToDevice));
+    FKT_CUDA_TRY(cudaMalloc(&P->sh_blocks, sizeof(int32_t) * std::max<int64_t>(b1 - b0, 1)));
+    if (b1 > b0)
+        FKT_CUDA_TRY(cudaMemcpy(P->sh_blocks, order.data() + b0, sizeof(int32_t) * (b1 - b0), cudaMemcpyHostToDevice));
     P->sh_nranks = nranks;
     P->sh_rank = rank;
     P->sh_b0 = b0;

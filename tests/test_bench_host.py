@@ -18,6 +18,8 @@ def test_far_pair_ops_counts_each_stage():
     radial = sum(j + 1 for _, j in pairs)           # R_kj = sum_m That_kjm J_m
     assert radial == 78
     assert bench.far_pair_ops(p) == 10 + 3 * (p + 1) + radial + p + len(pairs) + 3 * (p + 1) ** 2 + 84 == 362
+    # the compressed 1/r expansion: radial pairs (k, k) only, (p+1)^2 terms
+    assert bench.far_pair_ops(p, diag=True) == 10 + 3 * 7 + sum(k + 1 for k in range(7)) + p + 7 + 3 * 49 + 49
 
 
 @pytest.mark.parametrize("kernel,nw,tensor,want", [("matern32", 32, True, (8, 2)), ("matern32", 32, False, (40, 2)),

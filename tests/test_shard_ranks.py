@@ -39,14 +39,14 @@ def _blocks(tree):
 
 
 def _work(F, tree, blocks):
-    """Near pairs + 30 x far pairs of each block (the weights of fkt_shard_block_work)."""
+    """Near pairs + 50 x far pairs of each block (the weights of fkt_shard_block_work)."""
     size = tree["end"] - tree["begin"]
     w = []
     for lo, hi in blocks:
         tot = 0.0
         for t in range(lo, hi):
             far, near = F.target_lists(int(tree["perm"][t]))
-            tot += 30.0 * len(far) + float(size[near].sum())
+            tot += 50.0 * len(far) + float(size[near].sum())
         w.append(tot)
     return np.array(w)
 

@@ -70,3 +70,28 @@ def test_library_tables_equal_the_exact_tables(harness, d, p):
         k, j, m = int(k), int(j), int(m)
         exact = float(T.Tbar(k, j, m, d) * factorial(m))
         assert abs(float(v) - exact) <= 2e-7 * abs(exact) + 1e-12 * scale, (d, p, k, j, m, float(v), exact)
+
+
+@pytest.mark.parametrize("p", [4, 8, 10])
+def test_laplace_radial_terms_beyond_j_equal_k_vanish(harness, p):
+    """The library keeps only the j = k terms for 1/r in d = 3 (its radial compression).  For that
+    kernel J_m = K^(m)(r) r^m / m! = (-1)^m / r, so the degree-k, order-j radial function is
+    R_kj(r) = (1/r) sum_m That_kjm (-1)^m: it must vanish for every j > k (rank 1 per degree,
+    Table 3) -- exactly in the oracle's rationals and to float32 rounding in the library's tables --
+    and not for j = k (the Legendre multipole r'^k / r^(k+1))."""
+    from fractions import Fraction
+
+    out = subprocess.run([harness, "3", str(p)], capture_output=True, text=True, check=True).stdout.split("\n")
+    rows = [ln.split() for ln in out[1:] if ln.strip()]
+    lib, ref, mag = {}, {}, {}
+    for k, j, m, v in rows:
+        k, j, m = int(k), int(j), int(m)
+        lib[(k, j)] = lib.get((k, j), 0.0) + (-1) ** m * float(v)
+        mag[(k, j)] = mag.get((k, j), 0.0) + abs(float(v))
+        ref[(k, j)] = ref.get((k, j), Fraction(0)) + (-1) ** m * T.Tbar(k, j, m, 3) * factorial(m)
+    for (k, j), s in ref.items():
+        if j > k:
+            assert s == 0, (k, j, s)
+            assert abs(lib[(k, j)]) <= 1e-6 * mag[(k, j)], (k, j, lib[(k, j)], mag[(k, j)])
+        else:
+            assert s == 1, (k, j, s)             # Legendre normalisation: r'^k P_k(cos) / r^(k+1)
