@@ -67,6 +67,8 @@ WORKLOADS = {
     "batch256": dict(desc="256 problems, N log-uniform [2000, 200000], unit ball, kernels gaussian l=0.1 / "
                           "laplace 1/r / ratquad alpha=1 l=0.2", n=0, points=None, kernel=None, p=4, theta=0.5,
                      leaf=512, nrhs=8, near="fp32", far="bf16x3", weights="normal", err_targets=150),
+    "pipes": dict(desc="arithmetic pipe rates", n=0, points=None, kernel=None, p=0, theta=0.5, leaf=1, nrhs=1,
+                  near="fp32", far="fp32", weights="normal", err_targets=0),
     "gpsolve": dict(desc="d=4 N=100000 gaussian-mixture(20 comps, std 0.05)", n=100_000,
                     points=lambda n: inputs.gaussian_mixture(n, 4, 20, 0.05), kernel=("matern52", 0.3, 1.0, 1.0),
                     p=6, theta=0.3, leaf=256, nrhs=8, near="fp32", far="fp32", weights="normal", err_targets=0),
@@ -78,7 +80,7 @@ GP_SIGMA2 = 1e-2
 # workload (kernel, p, theta, leaf, nrhs, N); see profiles/.  Any other workload reports null.
 PROFILED_TRAFFIC = {
     ("near_tc_kernel<3,matern32>", "matern32", 6, 0.375, 256, 32, 1_000_000): 0.9078e9 + 0.1297e9,
-    ("far_tc2_kernel<6,bf16x3>", "matern32", 6, 0.375, 256, 32, 1_000_000): 1.4863e9 + 0.1535e9,
+    ("far_tc2_kernel<6,bf16x3>", "matern32", 6, 0.375, 256, 32, 1_000_000): 1.4729e9 + 0.1317e9,
 }
 
 # Per-SM lane rates of GB300 used by the ALU rooflines: FP32 pipe 128 lanes/clock; the MUFU (XU)
@@ -816,8 +818,37 @@ def run_reference(a):
             "e2e": {"value": rec["value"], "unit": "MVM/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
+def run_pipes(a):
+    """Lane-operation throughput of the FP32, FP32x2 and MUFU pipes (fkt_probe_pipe_rate) with the SM
+    clock sampled during the runs: the per-SM, per-clock rates the ALU rooflines divide by."""
+    import torch
+
+    from paper_2106_04487_gb300 import fkt
+
+    torch.cuda.set_device(0)
+    nsm = torch.cuda.get_device_properties(0).multi_processor_count
+    fkt.fkt_probe_pipe_rate("ffma", 1 << 12)  # load the module, wake the clocks
+    rates = {}
+    with ClockSampler(0) as clk:
+        for op in fkt.PIPE_OPS:
+            fkt.fkt_probe_pipe_rate(op, 1 << 14)
+            rates[op] = max(fkt.fkt_probe_pipe_rate(op, 1 << 16) for _ in range(3))
+    c = clk.summary()
+    mhz = c["sm_mhz"] or load_peaks()[0].get("sm_max_mhz", 2070.0)
+    per_clk = {op: r / (nsm * mhz * 1e6) for op, r in rates.items()}
+    return {"metric": "pipe lane-ops per SM per clock", "value": per_clk["ex2"], "unit": "lanes/SM/clock (ex2)",
+            "n_gpus": 1, "higher_is_better": True, "data": "synthetic",
+            "config": {"workload": "pipes: 8 CTAs x 256 threads per SM, 8 independent chains, 2^16 iterations",
+                       "lane_ops_per_second": rates, "lanes_per_sm_per_clock": per_clk, "sms": nsm,
+                       "sm_mhz_used": mhz},
+            "clocks": c}
+
+
 def main():
     a = parse()
+    if a.workload == "pipes":
+        print(json.dumps(run_pipes(a)))
+        return
     if a.impl == "reference":
         out = run_reference(a)
     elif a.workload == "gpsolve":

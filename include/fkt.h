@@ -433,6 +433,14 @@ int fkt_mvm_shard_end(fkt_plan_t plan, const float* mult, float* y, int nrhs);
 #define FKT_NOALLOC_SCRATCH_BYTES (48u << 20)
 int fkt_mvm_noalloc(fkt_plan_t plan, const float* w, float* y, int nrhs);
 
+/* Measurement helper (not part of the method): lane-operation throughput of one arithmetic pipe
+ * on the current device -- op 0 FP32 FMA, 1 MUFU ex2.approx, 2 MUFU rsqrt.approx, 3 MUFU
+ * sqrt.approx, 4 MUFU rcp.approx, 5 packed FP32x2 FMA (two lane-ops per instruction) -- from a
+ * grid of 8 x 256-thread CTAs per SM running 8 independent chains of iters operations per thread,
+ * timed with CUDA events.  It is the denominator of the near and far kernels' ALU rooflines.
+ * 1 <= iters <= 2^32.  Synchronizes the device. */
+int fkt_probe_pipe_rate(int op, int64_t iters, double* lane_ops_per_second);
+
 /* Failure detection: synchronise the plan's stream, then report FKT_ERR_TIMEOUT if any
  * bounded device-side wait of this plan's kernels ran out since the last check (the kernel
  * recorded it and stopped instead of hanging; results of that call are invalid), or

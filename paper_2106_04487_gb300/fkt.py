@@ -28,7 +28,7 @@ EXPORTS = ["fkt_plan", "fkt_mvm", "fkt_mvm_host", "fkt_dense_mvm", "fkt_set_opti
            "fkt_batch_set_option", "fkt_batch_info", "fkt_batch_check", "fkt_batch_destroy", "fkt_autotune_leaf",
            "fkt_precond_learn", "fkt_learn_params", "fkt_learn_eval", "fkt_learn_teacher", "fkt_spectral_sample",
            "fkt_shard_partition", "fkt_shard_block_work", "fkt_shard_set", "fkt_shard_info", "fkt_mvm_shard_begin",
-           "fkt_mvm_shard_end"]
+           "fkt_mvm_shard_end", "fkt_probe_pipe_rate"]
 
 
 class FktError(RuntimeError):
@@ -121,6 +121,7 @@ def lib() -> ctypes.CDLL:
     L.fkt_shard_info.argtypes = [vp, ctypes.c_int] + [ctypes.POINTER(ctypes.c_int64)] * 5
     L.fkt_mvm_shard_begin.argtypes = [vp, vp, vp, ctypes.c_int]
     L.fkt_mvm_shard_end.argtypes = [vp, vp, vp, ctypes.c_int]
+    L.fkt_probe_pipe_rate.argtypes = [ctypes.c_int, i64, ctypes.POINTER(ctypes.c_double)]
     L.fkt_destroy.argtypes = [vp]
     L.fkt_destroy.restype = None
     L.fkt_error_string.argtypes = [ctypes.c_int]
@@ -229,6 +230,16 @@ def fkt_shard_partition(work, nranks: int) -> np.ndarray:
     bounds = np.zeros(nranks + 1, np.int64)
     _check(lib().fkt_shard_partition(len(w), _ptr(w), int(nranks), _ptr(bounds)), "fkt_shard_partition")
     return bounds
+
+
+PIPE_OPS = {"ffma": 0, "ex2": 1, "rsqrt": 2, "sqrt": 3, "rcp": 4, "ffma2": 5}
+
+
+def fkt_probe_pipe_rate(op: str, iters: int = 1 << 16) -> float:
+    """Lane operations per second of one arithmetic pipe on the current device."""
+    v = ctypes.c_double()
+    _check(lib().fkt_probe_pipe_rate(PIPE_OPS[op], int(iters), ctypes.byref(v)), "fkt_probe_pipe_rate")
+    return v.value
 
 
 def fkt_check(plan):

@@ -46,12 +46,18 @@ def test_compressed_laplace_matches_oracle(fkt, orc, p, far, nrhs):
     plan.check()
     z = orc.FKT(X, orc.kparams("laplace", 1.0, scale=scale), p=p, leaf_size=128, theta=0.5).mvm(W)
     e2, einf = assert_bars(y, z, BARS[far], f"compressed laplace p={p} {far}")
-    # the uncompressed layout on the same plan gives the same product
+    # the uncompressed layout on the same plan gives the same product (at p = 10 the BF16 hi/lo
+    # operands of the 286-term full expansion exceed the tensor-core kernels' on-chip memory:
+    # only the compressed 121-term expansion runs there)
     plan.set_option("radial_compression", "off")
     assert plan.stats()["nterms"] == (p + 1) * (p + 2) * (p + 3) // 6
-    y_full = plan.mvm(Wd).cpu().numpy().astype(np.float64)
-    plan.check()
-    assert_bars(y_full, z, BARS[far], f"uncompressed laplace p={p} {far}")
+    if p == 10 and far == "bf16x3":
+        with pytest.raises(fkt.FktError):
+            plan.mvm(Wd)
+    else:
+        y_full = plan.mvm(Wd).cpu().numpy().astype(np.float64)
+        plan.check()
+        assert_bars(y_full, z, BARS[far], f"uncompressed laplace p={p} {far}")
     plan.set_option("radial_compression", "auto")
     assert plan.stats()["nterms"] == (p + 1) ** 2
     print(f"laplace p={p} {far} nrhs={nrhs}: compressed vs oracle {e2:.2e} / {einf:.2e}")
