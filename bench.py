@@ -96,7 +96,9 @@ def nterms(d: int, p: int) -> int:
 
 
 def near_kernel_name(kname: str, nw: int, near_precision: str = "fp32") -> str:
-    if nw == 32 and near_precision == "tf32x3":
+    if nw == 32 and near_precision == "f16x3" and kname != "laplace":
+        return f"near_tc2_kernel<3,{kname}>"
+    if nw == 32 and near_precision in ("tf32x3", "f16x3"):
         return f"near_tc_kernel<3,{kname}>"
     base = "near_kernel" if nw == 1 else "near_wide_kernel" if nw == 8 else "near_tile_kernel"
     return f"{base}<3,{kname},{nw}>"
@@ -167,7 +169,7 @@ def parse():
     ap.add_argument("--leaf", type=int, default=None)
     ap.add_argument("--nrhs", type=int, default=None)
     ap.add_argument("--far-precision", default=None, choices=["bf16x3", "tf32", "bf16", "fp32"])
-    ap.add_argument("--near-precision", default=None, choices=["tf32x3", "fp32"],
+    ap.add_argument("--near-precision", default=None, choices=["tf32x3", "f16x3", "fp32"],
                     help="near-field contraction of 32-wide passes: tensor cores (TF32 hi/lo) or CUDA cores")
     ap.add_argument("--far-kernel", default="single", choices=["pairs", "single"],
                     help="tensor-core far field (d = 3, BF16 forms): two far entries per thread or one")
@@ -332,7 +334,7 @@ def rooflines(a, stats, head, nsm, peaks, src, kname, passes):
     """Roofline of the near and far kernels of the headline form, dominant first."""
     sm_max = peaks.get("sm_max_mhz", 2070.0)
     nw = 1 if (a.nrhs == 1 and a.far_precision == "fp32") else (8 if a.nrhs <= 8 else 16 if a.nrhs <= 16 else 32)
-    near_tc = nw == 32 and a.near_precision == "tf32x3"
+    near_tc = nw == 32 and a.near_precision in ("tf32x3", "f16x3")
     fp32_ops, mufu_ops = near_pair_cost(kname, nw, near_tc)
     slots = max(fp32_ops / FP32_LANES, mufu_ops / MUFU_LANES)  # SM clocks per pair
     peak_pairs = nsm * sm_max * 1e6 / slots

@@ -26,7 +26,7 @@ void free_plan(fkt_plan_s* P) {
                     P->nd_centre, P->nd_rho2, P->nd_cf, P->nd_scale, P->nd_used, P->blk_range, P->far_off,
                     P->near_off, P->far_ent, P->near_ent, P->masks, P->s2m_items, P->s2m_node_items,
                     P->s2m_item_off, P->rec, P->ynear, P->yfar, P->mult, P->s2m_part, P->tc_image, P->hbuf_w, P->hbuf_y,
-                    P->d_err, P->dense_off, P->dense_ent};
+                    P->d_err, P->d_wmax, P->dense_off, P->dense_ent};
     for (void* b : bufs)
         if (b) cudaFree(b);
     fkt::free_learn(P);
@@ -118,7 +118,8 @@ int fkt_plan(const float* points, int64_t N, int d, fkt_kernel kernel, int p, in
     if (fkt::create_far_stream(&P->stream2) != FKT_OK) { free_plan(P); return FKT_ERR_CUDA; }
     for (auto& e : P->ev)
         if (cudaEventCreate(&e) != cudaSuccess) { free_plan(P); return FKT_ERR_CUDA; }
-    if (cudaMalloc(&P->d_err, sizeof(int)) != cudaSuccess || cudaMemsetAsync(P->d_err, 0, sizeof(int), P->stream) != cudaSuccess) {
+    if (cudaMalloc(&P->d_err, sizeof(int)) != cudaSuccess || cudaMemsetAsync(P->d_err, 0, sizeof(int), P->stream) != cudaSuccess ||
+        cudaMalloc(&P->d_wmax, sizeof(unsigned) * 32) != cudaSuccess) {
         free_plan(P);
         return FKT_ERR_OOM;
     }
@@ -285,6 +286,7 @@ int fkt_set_option(fkt_plan_t plan, const char* key, const char* value) {
     if (!strcmp(key, "near_precision")) {
         if (!strcmp(value, "fp32")) plan->near_precision = fkt::NEAR_FP32;
         else if (!strcmp(value, "tf32x3")) plan->near_precision = fkt::NEAR_TF32X3;
+        else if (!strcmp(value, "f16x3")) plan->near_precision = fkt::NEAR_F16X3;
         else return FKT_ERR_INVALID_ARG;
         return FKT_OK;
     }

@@ -316,7 +316,8 @@ int fkt_batch_plan(int nprob, const fkt_problem* probs, int d, int p, int leaf_s
         if (fkt::create_far_stream(&M->stream2) != FKT_OK) rc = FKT_ERR_CUDA;
         for (auto& e : M->ev)
             if (!rc && cudaEventCreate(&e) != cudaSuccess) rc = FKT_ERR_CUDA;
-        if (!rc && (cudaMalloc(&M->d_err, sizeof(int)) != cudaSuccess || cudaMemset(M->d_err, 0, sizeof(int)) != cudaSuccess))
+        if (!rc && (cudaMalloc(&M->d_err, sizeof(int)) != cudaSuccess || cudaMemset(M->d_err, 0, sizeof(int)) != cudaSuccess ||
+                    cudaMalloc(&M->d_wmax, sizeof(unsigned) * 32) != cudaSuccess))
             rc = FKT_ERR_OOM;
         if (!rc) rc = fkt::merge_plans(plans, M);
     }

@@ -45,7 +45,7 @@ struct KernelParams {
 };
 
 enum FarPrecision { FAR_FP32 = 0, FAR_TF32 = 1, FAR_BF16 = 2, FAR_BF16X3 = 3 };
-enum NearPrecision { NEAR_FP32 = 0, NEAR_TF32X3 = 1 };
+enum NearPrecision { NEAR_FP32 = 0, NEAR_TF32X3 = 1, NEAR_F16X3 = 2 };
 
 }  // namespace fkt
 
@@ -113,6 +113,7 @@ struct fkt_plan_s {
     float* hbuf_y = nullptr;
     int hbuf_cap = 0;              // right-hand sides the staging buffers hold
     int* d_err = nullptr;          // device error word (bounded waits that ran out)
+    unsigned* d_wmax = nullptr;    // device [32]: largest |w| per right-hand side of a pass (FP16 near field)
     int64_t* dense_off = nullptr;  // one-entry lists (the root) per target block, for fkt_dense_mvm
     int2* dense_ent = nullptr;
     // block-Jacobi preconditioner: inverse of K(X_b, X_b) + sigma2 I per target block

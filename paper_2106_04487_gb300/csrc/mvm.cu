@@ -35,6 +35,8 @@ void launch_near_d3(int nw, int tpt, int kind, unsigned grid, cudaStream_t st, c
 void launch_near_d4(int nw, int tpt, int kind, unsigned grid, cudaStream_t st, const MvmArgs& a, const KernelParams& kp);
 void launch_near_tc_d3(int kind, unsigned grid, cudaStream_t st, const MvmArgs& a, const KernelParams& kp);
 void launch_near_tc_d4(int kind, unsigned grid, cudaStream_t st, const MvmArgs& a, const KernelParams& kp);
+void launch_near_tc2_d3(int kind, unsigned grid, cudaStream_t st, const MvmArgs& a, const KernelParams& kp, unsigned* wmax);
+void launch_near_tc2_d4(int kind, unsigned grid, cudaStream_t st, const MvmArgs& a, const KernelParams& kp, unsigned* wmax);
 
 int launch_tc_d3_p0_6(int p, int prec, bool far, const TcLaunch& L);
 int launch_tc_d3_p7_10(int p, int prec, bool far, const TcLaunch& L);
@@ -85,12 +87,21 @@ static int launch_far_any(int d, int p, int nrb, const FarLaunch& L) {
 namespace {
 
 // Near field launch: nw right-hand sides per pass (1, 8, 16, 32); targets per thread tpt = 2 or 4
-// (4 only for one right-hand side); tc: the 32-wide pass on the tensor cores (TF32 hi/lo split).
-void launch_near(int d, int nw, int tpt, bool tc, int kind, unsigned grid, cudaStream_t st, const MvmArgs& a,
-                 const KernelParams& kp) {
+// (4 only for one right-hand side); tc: the 32-wide pass on the tensor cores -- tc = 1 TF32 hi/lo
+// operands, tc = 2 FP16 hi/lo operands with double buffering (wmax: 32 words of device scratch for
+// the weights' per-right-hand-side scale), which the 1/r kernel leaves for TF32 (its values are
+// unbounded).
+void launch_near(int d, int nw, int tpt, int tc, int kind, unsigned grid, cudaStream_t st, const MvmArgs& a,
+                 const KernelParams& kp, unsigned* wmax) {
     if (tc && nw == 32) {
-        if (d == 3) launch_near_tc_d3(kind, grid, st, a, kp);
-        else launch_near_tc_d4(kind, grid, st, a, kp);
+        if (tc == 2 && kind != FKT_LAPLACE && wmax) {
+            if (d == 3) launch_near_tc2_d3(kind, grid, st, a, kp, wmax);
+            else launch_near_tc2_d4(kind, grid, st, a, kp, wmax);
+        } else if (d == 3) {
+            launch_near_tc_d3(kind, grid, st, a, kp);
+        } else {
+            launch_near_tc_d4(kind, grid, st, a, kp);
+        }
         return;
     }
     if (d == 3) launch_near_d3(nw, tpt, kind, grid, st, a, kp);
@@ -164,17 +175,22 @@ __global__ void dense_lists_kernel(int64_t nblocks, int64_t* off, int2* ent) {
 // Near field of every target block: one launch, or for a batch one launch per kernel kind over
 // that kind's blocks (largest first, so uneven problems balance across the SMs).  exact: keep
 // the float32 CUDA-core kernels whatever near_precision says (the exact dense product).
+static int near_tc_mode(const fkt_plan_s* P, bool exact) {
+    if (exact) return 0;
+    return P->near_precision == NEAR_TF32X3 ? 1 : P->near_precision == NEAR_F16X3 ? 2 : 0;
+}
+
 void launch_near_stage(fkt_plan_s* P, MvmArgs& a, int nrb, int tpt, cudaStream_t st, bool exact) {
-    const bool tc = !exact && P->near_precision == NEAR_TF32X3;
+    const int tc = near_tc_mode(P, exact);
     if (P->nprob == 0) {
         a.blk_list = nullptr;
-        launch_near(P->d, nrb, tpt, tc, P->kernel.kind, (unsigned)P->nblocks, st, a, P->kp);
+        launch_near(P->d, nrb, tpt, tc, P->kernel.kind, (unsigned)P->nblocks, st, a, P->kp, P->d_wmax);
         return;
     }
     for (size_t i = 0; i < P->kind_list.size(); ++i) {
         if (P->kind_list_n[i] == 0) continue;
         a.blk_list = P->kind_list[i];
-        launch_near(P->d, nrb, tpt, tc, P->kind_of_list[i], (unsigned)P->kind_list_n[i], st, a, P->kp);
+        launch_near(P->d, nrb, tpt, tc, P->kind_of_list[i], (unsigned)P->kind_list_n[i], st, a, P->kp, P->d_wmax);
     }
     a.blk_list = P->far_list;  // the far stage that follows walks all blocks, most work first
 }
@@ -415,7 +431,7 @@ int shard_end(fkt_plan_s* P, const float* mult, float* y, int nrhs) {
     }
     a.ynear = P->ynear;
     a.nr = nrhs;
-    launch_near(P->d, nw, P->near_tpt, P->near_precision == NEAR_TF32X3, P->kernel.kind, (unsigned)nb, st, a, P->kp);
+    launch_near(P->d, nw, P->near_tpt, near_tc_mode(P, false), P->kernel.kind, (unsigned)nb, st, a, P->kp, P->d_wmax);
     FKT_CUDA_TRY(cudaGetLastError());
     const int64_t nt = P->sh_t1 - P->sh_t0;
     unpermute_range_kernel<<<(unsigned)((nt + 255) / 256), 256, 0, st>>>(P->sh_t0, P->sh_t1, N, nrhs, P->perm, P->ynear,

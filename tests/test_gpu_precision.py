@@ -115,19 +115,20 @@ def test_precision_modes_d4(fkt, orc, prec):
 
 # The tensor-core near field (32-wide passes) keeps the float32 bar: the hi/lo split leaves at most
 # about 2^-20 of each product.
+@pytest.mark.parametrize("near", ["tf32x3", "f16x3"])
 @pytest.mark.parametrize("far", ["fp32", "bf16x3"])
 @pytest.mark.parametrize("nrhs", [20, 32, 40])
-def test_near_tensor_core_d3(fkt, case3, far, nrhs):
+def test_near_tensor_core_d3(fkt, case3, far, nrhs, near):
     import torch
 
     X, W, z = case3
     plan = fkt.Plan(torch.from_numpy(X).cuda(), "matern32", lengthscale=0.2, p=6, leaf_size=128, theta=0.5)
     plan.set_option("far_precision", far)
-    plan.set_option("near_precision", "tf32x3")
+    plan.set_option("near_precision", near)
     y = plan.mvm(torch.from_numpy(W[:nrhs]).cuda()).cpu().numpy().astype(np.float64)
     plan.check()
     err = _rel(y, z[:nrhs])
-    print(f"d=3 near tf32x3, far {far}, nrhs={nrhs}: rel err vs oracle {err:.3e}")
+    print(f"d=3 near {near}, far {far}, nrhs={nrhs}: rel err vs oracle {err:.3e}")
     assert np.isfinite(y).all()
     assert err < BARS[far], err
 
@@ -136,7 +137,8 @@ def test_near_tensor_core_d3(fkt, case3, far, nrhs):
                                                ("cauchy", 0.05, 3, 200), ("exponential", 0.3, 3, 96),
                                                ("ratquad", 0.2, 3, 128), ("matern52", 0.3, 4, 128),
                                                ("gaussian", 0.2, 4, 77)])
-def test_near_tensor_core_kernels(fkt, orc, kernel, ell, d, leaf):
+@pytest.mark.parametrize("near", ["tf32x3", "f16x3"])
+def test_near_tensor_core_kernels(fkt, orc, kernel, ell, d, leaf, near):
     """Every kernel kind, d = 3 and 4, ragged leaves (sizes not multiples of the 8-source MMA
     step), duplicated points (Laplace skips r = 0 pairs) against the oracle FKT."""
     import torch
@@ -147,11 +149,36 @@ def test_near_tensor_core_kernels(fkt, orc, kernel, ell, d, leaf):
     W = inputs.normal_weights(n, 32, seed=45)
     z = orc.FKT(X, orc.kparams(kernel, ell), p=4, leaf_size=leaf, theta=0.5).mvm(W)
     plan = fkt.Plan(torch.from_numpy(X).cuda(), kernel, lengthscale=ell, p=4, leaf_size=leaf, theta=0.5)
-    plan.set_option("near_precision", "tf32x3")
+    plan.set_option("near_precision", near)
     y = plan.mvm(torch.from_numpy(W).cuda()).cpu().numpy().astype(np.float64)
     plan.check()
     err = _rel(y, z)
-    print(f"{kernel} d={d} leaf={leaf} near tf32x3: rel err vs oracle {err:.3e}")
+    print(f"{kernel} d={d} leaf={leaf} near {near}: rel err vs oracle {err:.3e}")
+    assert err < BARS["fp32"], err
+
+
+def test_near_f16_weight_ranges(fkt, orc):
+    """The FP16 near field scales each right-hand side's weights by a power of two (its largest
+    |w| into [2^13, 2^14)) and the kernel values by 2^14: right-hand sides from 1e-30 to 1e30 in
+    size, an all-zero one and one with a single non-zero weight keep the float32 bar."""
+    import torch
+
+    X = inputs.gaussian_mixture(9000, 3, 10, 0.05, seed=53)
+    W = inputs.normal_weights(9000, 32, seed=54).astype(np.float64)
+    W *= np.logspace(-30, 30, 32)[:, None]
+    W[3] = 0.0
+    W[4] = 0.0
+    W[4, 17] = 2.5
+    W = W.astype(np.float32)
+    z = orc.FKT(X, orc.kparams("gaussian", 0.1), p=4, leaf_size=128, theta=0.5).mvm(W)
+    plan = fkt.Plan(torch.from_numpy(X).cuda(), "gaussian", lengthscale=0.1, p=4, leaf_size=128, theta=0.5)
+    plan.set_option("near_precision", "f16x3")
+    y = plan.mvm(torch.from_numpy(W).cuda()).cpu().numpy().astype(np.float64)
+    plan.check()
+    assert np.all(y[3] == 0.0)
+    rows = [r for r in range(32) if r != 3]
+    err = _rel(y[rows], z[rows])
+    print(f"f16x3 weight ranges: rel err vs oracle {err:.3e}")
     assert err < BARS["fp32"], err
 
 
