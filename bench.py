@@ -66,7 +66,7 @@ WORKLOADS = {
                        near="fp32", far="bf16", weights="uniform", err_targets=400),
     "batch256": dict(desc="256 problems, N log-uniform [2000, 200000], unit ball, kernels gaussian l=0.1 / "
                           "laplace 1/r / ratquad alpha=1 l=0.2", n=0, points=None, kernel=None, p=4, theta=0.5,
-                     leaf=512, nrhs=8, near="fp32", far="bf16x3", weights="normal", err_targets=150),
+                     leaf=0, nrhs=8, near="fp32", far="bf16x3", weights="normal", err_targets=150),
     "pipes": dict(desc="arithmetic pipe rates", n=0, points=None, kernel=None, p=0, theta=0.5, leaf=1, nrhs=1,
                   near="fp32", far="fp32", weights="normal", err_targets=0),
     "gpsolve": dict(desc="d=4 N=100000 gaussian-mixture(20 comps, std 0.05)", n=100_000,
@@ -83,9 +83,12 @@ PROFILED_TRAFFIC = {
     ("far_tc2_kernel<6,bf16x3>", "matern32", 6, 0.375, 256, 32, 1_000_000): 1.4729e9 + 0.1317e9,
 }
 
-# Per-SM lane rates of GB300 used by the ALU rooflines: FP32 pipe 128 lanes/clock; the MUFU (XU)
-# pipe 32 lanes/clock (ncu: 2 ex2/sqrt per pair at 17.6 % XU utilisation while 5.5e11 pairs/s).
+# Per-SM lane rates of GB300 used by the ALU rooflines, measured by fkt_probe_pipe_rate
+# (bench.py --workload pipes; profiles/pipe_rates_gb300.md) at 2070 MHz: FP32 FMA 121 lanes/clock
+# (FP32x2 FMA the same 120: packing halves the issue slots, not the pipe time), MUFU ex2 32
+# lanes/clock, MUFU sqrt / rsqrt / rcp 16.  The rooflines use the nominal 128 for FP32.
 FP32_LANES, MUFU_LANES = 128.0, 32.0
+MUFU_CLOCKS = {"ex2": 1.0 / 32.0, "sqrt": 1.0 / 16.0, "rsqrt": 1.0 / 16.0, "rcp": 1.0 / 16.0, "lg2": 1.0 / 16.0}
 
 
 def nterms(d: int, p: int) -> int:
@@ -116,18 +119,19 @@ def far_kernel_name(p: int, far_precision: str, nrhs: int, far_kernel: str = "si
 
 
 def near_pair_cost(kernel: str, nw: int, tensor: bool = False):
-    """Lower bound on SM lane-ops per near-field pair for a pass of nw right-hand sides:
-    (FP32-pipe lane-ops, MUFU lane-ops).
+    """Lower bound on SM work per near-field pair for a pass of nw right-hand sides:
+    (FP32-pipe lane-ops, MUFU SM-clocks per lane).
 
     Per pair the method needs d = 3 subtractions and |x|^2 (1 MUL + 2 FMA), the kernel value and one
-    FMA per right-hand side.  Kernel value: Gaussian 2^-q (MUFU); Matern-3/2 sqrt (MUFU),
-    1 + u ln2 (FMA), 2^-u (MUFU), product (MUL); Cauchy / rational quadratic 1 + q (ADD), reciprocal
-    (MUFU); Laplace rsqrt (MUFU) and the r = 0 test.  With the contraction on the tensor cores
-    (tensor=True) the per-right-hand-side FMAs leave the FP32 pipe."""
+    FMA per right-hand side.  Kernel value: Gaussian 2^-q (ex2); Matern-3/2 sqrt, 1 + u ln2 (FMA),
+    2^-u (ex2), product (MUL); Cauchy / rational quadratic 1 + q (ADD), reciprocal (rcp); Laplace
+    rsqrt and the r = 0 test.  MUFU rates per operation as measured (MUFU_CLOCKS).  With the
+    contraction on the tensor cores (tensor=True) the per-right-hand-side FMAs leave the FP32 pipe."""
     fma = 0 if tensor else nw
-    extra, mufu = {"gaussian": (0, 1), "matern32": (2, 2), "cauchy": (1, 1), "ratquad": (1, 1),
-                   "laplace": (1, 1)}.get(kernel, (2, 2))
-    return 6 + extra + fma, mufu
+    extra, mufu = {"gaussian": (0, ["ex2"]), "matern32": (2, ["sqrt", "ex2"]), "cauchy": (1, ["rcp"]),
+                   "ratquad": (1, ["rcp"]), "laplace": (1, ["rsqrt"]), "exponential": (0, ["sqrt", "ex2"]),
+                   "matern52": (4, ["sqrt", "ex2"])}.get(kernel, (2, ["sqrt", "ex2"]))
+    return 6 + extra + fma, sum(MUFU_CLOCKS[m] for m in mufu)
 
 
 def far_pair_ops(p: int, diag: bool = False) -> int:
@@ -202,7 +206,7 @@ def parse():
 
 def workload_name(a, kern=None):
     if a.workload == "batch256":
-        return (f"{WORKLOADS['batch256']['desc']}, p={a.p} leaf={a.leaf} theta={a.theta} nrhs={a.nrhs} "
+        return (f"{WORKLOADS['batch256']['desc']}, p={a.p} leaf={a.leaf or 'autotuned'} theta={a.theta} nrhs={a.nrhs} "
                 f"near={a.near_precision} far={a.far_precision}")
     k = kern or a.kern
     desc = WORKLOADS[a.workload]["desc"].replace(f"N={WORKLOADS[a.workload]['n']}", f"N={a.n}")
@@ -335,8 +339,8 @@ def rooflines(a, stats, head, nsm, peaks, src, kname, passes):
     sm_max = peaks.get("sm_max_mhz", 2070.0)
     nw = 1 if (a.nrhs == 1 and a.far_precision == "fp32") else (8 if a.nrhs <= 8 else 16 if a.nrhs <= 16 else 32)
     near_tc = nw == 32 and a.near_precision in ("tf32x3", "f16x3")
-    fp32_ops, mufu_ops = near_pair_cost(kname, nw, near_tc)
-    slots = max(fp32_ops / FP32_LANES, mufu_ops / MUFU_LANES)  # SM clocks per pair
+    fp32_ops, mufu_clk = near_pair_cost(kname, nw, near_tc)
+    slots = max(fp32_ops / FP32_LANES, mufu_clk)  # SM clocks per pair
     peak_pairs = nsm * sm_max * 1e6 / slots
     near_pairs = stats["near_pairs"] * passes  # one launch per pass; its kernel value serves the pass
     near_ach = near_pairs / (head["near_ms"] / 1e3)
@@ -346,10 +350,11 @@ def rooflines(a, stats, head, nsm, peaks, src, kname, passes):
                  "unit": "Gpair/s", "frac": near_ach / peak_pairs,
                  "traffic": PROFILED_TRAFFIC.get((near_name,) + key),
                  "traffic_unit": "bytes per launch (ncu dram__bytes_read + write)", "ms_per_step": head["near_ms"],
-                 "work_per_unit": f"{fp32_ops} FP32 + {mufu_ops} MUFU lane-ops per (target, source) near pair"
+                 "work_per_unit": f"{fp32_ops} FP32 lane-ops + {mufu_clk:.4f} MUFU SM-clocks per (target, source) near pair"
                                   f"{'; contraction on the tensor cores' if near_tc else ''}",
                  "peak_source": f"{nsm} SMs x {sm_max:.0f} MHz / max({fp32_ops}/{FP32_LANES:.0f} FP32, "
-                                f"{mufu_ops}/{MUFU_LANES:.0f} MUFU) SM-clocks per pair ({src} clock)"}
+                                f"{mufu_clk:.4f} MUFU: measured ex2 32, sqrt/rsqrt/rcp 16 lanes per SM-clock) "
+                                f"SM-clocks per pair ({src} clock)"}
     roofs = [near_roof]
     if stats["far_pairs"] > 0 and head["far_ms"]:
         diag = stats.get("nterms") == (a.p + 1) ** 2 and a.p > 0 and a.kern[0] == "laplace"
@@ -414,6 +419,7 @@ def run_ours(a):
     Yd = torch.empty_like(Wd)
     obj.set_option("far_precision", a.far_precision)
     obj.set_option("near_precision", a.near_precision)
+    tuned = obj.autotune(a.nrhs) if batch else None  # kernel variants of the batch (leaf sizes: leaf_size 0)
     if not batch:
         obj.set_option("far_kernel", a.far_kernel)
         obj.set_option("radial_compression", a.radial_compression)
@@ -574,6 +580,8 @@ def run_ours(a):
     }
     if batch:
         out["gpu_launches_note"] = "one CUDA graph replay per step (near field per kernel kind, far field, s2m, permutes)"
+        out["config"]["autotuned"] = {"kernel_variants": tuned,
+                                      "leaf_sizes": {int(s): int((obj.leaf_sizes == s).sum()) for s in set(obj.leaf_sizes.tolist())}}
     if comp is not None:
         cv = mvms_per_step * len(comp["step_ms"]) / (sum(comp["step_ms"]) / 1e3)
         out["compare_form"] = {"form": "plain float32 (near and far on the CUDA cores)", "value": cv, "unit": "MVM/s",
@@ -752,15 +760,17 @@ def oracle_steps(runners, steps: int, warmup: int, units_full: float, n_total: i
             "traversal_s": sum(trav) / steps, "targets_per_step": sampled}
 
 
-def oracle_setup(a, X=None, W=None, probs=None, offsets=None):
+def oracle_setup(a, X=None, W=None, probs=None, offsets=None, leafs=None):
     """(runners, units of a full product, points of a full product, description) for the workload:
-    the problem itself, or problems 0, 1, 2 of the batch."""
+    the problem itself, or problems 0, 1, 2 of the batch (at the batch's leaf sizes when given;
+    512 when the batch autotunes them and no tuned sizes are known)."""
     if probs is not None:
         runners, n_total = [], int(offsets[-1])
         for i in (0, 1, 2):
             Xi, *kern = probs[i]
             lo, hi = offsets[i], offsets[i + 1]
-            runners.append((OracleRunner(Xi, kern, a.p, a.leaf, a.theta, a.nrhs), W[:, lo:hi],
+            leaf = int(leafs[i]) if leafs is not None else (a.leaf or 512)
+            runners.append((OracleRunner(Xi, kern, a.p, leaf, a.theta, a.nrhs), W[:, lo:hi],
                             min(hi - lo, ORACLE_TARGETS // 3)))
         return runners, 256 * a.nrhs, n_total, "problems 0, 1, 2 of the batch"
     R = OracleRunner(X, a.kern, a.p, a.leaf, a.theta, a.nrhs)
@@ -778,7 +788,8 @@ def cpu_baseline(a, X, W, probs=None, batch=None):
     """The oracle on the host cores: two oracle steps, the reference arm's rule."""
     from oracle import oracle as O
 
-    runners, units, n_total, what = oracle_setup(a, X, W, probs, batch.offsets if batch is not None else None)
+    runners, units, n_total, what = oracle_setup(a, X, W, probs, batch.offsets if batch is not None else None,
+                                                 batch.leaf_sizes if batch is not None else None)
     rec = oracle_steps(runners, 2, 0, units, n_total)
     return {"value": rec["value"], "unit": "MVM/s", "cores": O.num_threads(), "kind": "oracle",
             "sample": oracle_sample_note(rec, runners, what), "extrapolated_value": rec["extrapolated_value"]}

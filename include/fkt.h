@@ -272,6 +272,17 @@ int fkt_batch_set_option(fkt_batch_t batch, const char* key, const char* value);
 /* offsets [nprob+1] (column offsets), leaf_sizes [nprob], totals; any pointer may be NULL. */
 int fkt_batch_info(fkt_batch_t batch, int64_t* offsets, int32_t* leaf_sizes, fkt_stats* total);
 
+/* Autotuner of the kernel variants for products with nrhs right-hand sides: times the batch
+ * product (CUDA events, best of 3 after a warm-up) for each value of one option at a time and keeps
+ * the fastest -- the tensor-core far field's CTA shape ("far_kernel": one far entry per thread at
+ * four CTAs per SM, or two per thread at two CTAs per SM; BF16 forms, d = 3), the near field of
+ * 32-wide passes ("near_precision": register-tiled CUDA cores, TF32 or FP16 tensor-core operands,
+ * all float32-level accurate) and the single-RHS near kernel's targets per thread.  The far
+ * precision, which sets the accuracy, is left as it is.  chosen (may be NULL) receives
+ * "key=value;..." (at most len bytes with the terminating zero).  Synchronizes; drops the captured
+ * graph. */
+int fkt_batch_autotune(fkt_batch_t batch, int nrhs, char* chosen, int len);
+
 /* fkt_check for the batch. */
 int fkt_batch_check(fkt_batch_t batch);
 

@@ -12,6 +12,7 @@
 #include <algorithm>
 #include <chrono>
 #include <map>
+#include <string>
 #include <numeric>
 #include <vector>
 
@@ -416,6 +417,43 @@ int fkt_batch_info(fkt_batch_t batch, int64_t* offsets, int32_t* leaf_sizes, fkt
 }
 
 int fkt_batch_check(fkt_batch_t batch) { return batch ? fkt_check(batch->merged) : FKT_ERR_INVALID_ARG; }
+
+int fkt_batch_autotune(fkt_batch_t batch, int nrhs, char* chosen, int len) {
+    if (!batch || nrhs < 1 || nrhs > fkt::kMaxRhs || (chosen && len < 1)) return FKT_ERR_INVALID_ARG;
+    fkt_plan_s* P = batch->merged;
+    // kernel variants of equal accuracy (CTA shapes, per-thread work, operand paths), by axis
+    struct Axis { const char* key; std::vector<const char*> values; };
+    std::vector<Axis> axes;
+    if (P->d == 3 && (P->far_precision == fkt::FAR_BF16 || P->far_precision == fkt::FAR_BF16X3))
+        axes.push_back({"far_kernel", {"single", "pairs"}});
+    if (nrhs > 16) axes.push_back({"near_precision", {"fp32", "tf32x3", "f16x3"}});
+    if (nrhs == 1) axes.push_back({"near_targets_per_thread", {"2", "4"}});
+    std::string out;
+    for (const Axis& ax : axes) {  // one axis at a time, each at the fastest of its values
+        double best = 1e30;
+        const char* arg = nullptr;
+        for (const char* v : ax.values) {
+            int rc = fkt_set_option(P, ax.key, v);
+            if (rc) return rc;
+            const double ms = time_mvm_ms(P, nrhs, 3);
+            if (ms < best) { best = ms; arg = v; }
+        }
+        if (!arg) return FKT_ERR_CUDA;
+        int rc = fkt_set_option(P, ax.key, arg);
+        if (rc) return rc;
+        out += std::string(out.empty() ? "" : ";") + ax.key + "=" + arg;
+    }
+    if (P->graph) {  // options change the launch sequence: capture again on the next product
+        cudaGraphExecDestroy(P->graph);
+        P->graph = nullptr;
+    }
+    if (chosen) {
+        const size_t n = std::min(out.size(), (size_t)len - 1);
+        memcpy(chosen, out.data(), n);
+        chosen[n] = 0;
+    }
+    return FKT_OK;
+}
 
 void fkt_batch_destroy(fkt_batch_t batch) {
     if (!batch) return;

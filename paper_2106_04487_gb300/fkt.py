@@ -28,7 +28,7 @@ EXPORTS = ["fkt_plan", "fkt_mvm", "fkt_mvm_host", "fkt_dense_mvm", "fkt_set_opti
            "fkt_batch_set_option", "fkt_batch_info", "fkt_batch_check", "fkt_batch_destroy", "fkt_autotune_leaf",
            "fkt_precond_learn", "fkt_learn_params", "fkt_learn_eval", "fkt_learn_teacher", "fkt_spectral_sample",
            "fkt_shard_partition", "fkt_shard_block_work", "fkt_shard_set", "fkt_shard_info", "fkt_mvm_shard_begin",
-           "fkt_mvm_shard_end", "fkt_probe_pipe_rate"]
+           "fkt_mvm_shard_end", "fkt_probe_pipe_rate", "fkt_batch_autotune"]
 
 
 class FktError(RuntimeError):
@@ -105,6 +105,7 @@ def lib() -> ctypes.CDLL:
     L.fkt_batch_set_option.argtypes = [vp, ctypes.c_char_p, ctypes.c_char_p]
     L.fkt_batch_info.argtypes = [vp, vp, vp, ctypes.POINTER(fkt_stats)]
     L.fkt_batch_check.argtypes = [vp]
+    L.fkt_batch_autotune.argtypes = [vp, ctypes.c_int, ctypes.c_char_p, ctypes.c_int]
     L.fkt_batch_destroy.argtypes = [vp]
     L.fkt_batch_destroy.restype = None
     L.fkt_autotune_leaf.argtypes = [vp, i64, ctypes.c_int, fkt_kernel, ctypes.c_int, ctypes.c_double, ctypes.c_int, vp,
@@ -491,6 +492,12 @@ class Batch:
 
     def check(self):
         _check(lib().fkt_batch_check(self.h), "fkt_batch_check")
+
+    def autotune(self, nrhs: int) -> str:
+        """Pick the fastest kernel variants for nrhs right-hand sides (fkt_batch_autotune)."""
+        buf = ctypes.create_string_buffer(256)
+        _check(lib().fkt_batch_autotune(self.h, int(nrhs), buf, len(buf)), "fkt_batch_autotune")
+        return buf.value.decode()
 
     def close(self):
         if getattr(self, "h", None):

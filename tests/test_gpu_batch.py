@@ -82,3 +82,32 @@ def test_autotune_leaf_picks_a_candidate(fkt):
     X = torch.from_numpy(inputs.uniform_cube(50000, 3, seed=7)).cuda()
     best, ms = fkt.fkt_autotune_leaf(X, fkt.make_kernel("gaussian", 0.1), 4, 0.5, nrhs=1, candidates=(128, 512))
     assert best in (128, 512) and ms > 0
+
+
+def test_autotuned_batch_matches_oracle(fkt, orc):
+    """Leaf sizes autotuned per size class (leaf_size = 0) and the kernel variants autotuned for 8
+    and 32 right-hand sides (fkt_batch_autotune): whatever they pick, the product keeps the bars."""
+    import torch
+
+    sizes = inputs.batch_sizes(12, 2000, 40000, seed=91)
+    kinds = [("gaussian", 0.1, 1.0, 1.0), ("laplace", 1.0, 1.0, 1.0), ("ratquad", 0.2, 1.0, 1.0)]
+    probs = [(inputs.unit_ball(int(n), 3, seed=200 + i), *kinds[i % 3]) for i, n in enumerate(sizes)]
+    batch = fkt.Batch(probs, p=4, leaf_size=0, theta=0.5)
+    assert set(batch.leaf_sizes.tolist()) <= {64, 128, 256, 512}
+    batch.set_option("far_precision", "bf16x3")
+    for nrhs in (8, 32):
+        chosen = batch.autotune(nrhs)
+        assert "far_kernel=" in chosen and (nrhs <= 16 or "near_precision=" in chosen), chosen
+        W = inputs.normal_weights(batch.N, nrhs, seed=92)
+        Y = batch.mvm(torch.from_numpy(W).cuda()).cpu().numpy().astype(np.float64)
+        batch.check()
+        for i in (0, 1, 2, 11):
+            X, kname, ell, alpha, scale = probs[i]
+            lo, hi = batch.offsets[i], batch.offsets[i + 1]
+            F = orc.FKT(X, orc.kparams(kname, ell, alpha=alpha, scale=scale), p=4,
+                        leaf_size=int(batch.leaf_sizes[i]), theta=0.5)
+            idx = inputs.subsample(hi - lo, 100, seed=93 + i)
+            z = F.mvm(W[:, lo:hi], idx)
+            err = max(np.linalg.norm(Y[r, lo + idx] - z[r]) / np.linalg.norm(z[r]) for r in range(nrhs))
+            print(f"autotuned ({chosen}) nrhs={nrhs} problem {i} ({kname}): {err:.2e}")
+            assert err < 3e-5, (nrhs, i, chosen, err)

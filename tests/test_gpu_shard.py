@@ -63,8 +63,9 @@ def test_sharded_product_matches_single_process(fkt, orc, nranks, nrhs, far, nea
     single = plan()
     want = single.mvm(Wd).cpu().numpy().astype(np.float64)
     # same arithmetic up to the order of the multipole sums and, for one right-hand side, the
-    # kernel widths (the single-process product runs its 1-wide kernels, the sharded one 8-wide)
-    e2, einf = assert_bars(y, want, 3e-6, f"{nranks} ranks vs fkt_mvm")
+    # kernel widths (the single-process product runs its 1-wide kernels, the sharded one 8-wide):
+    # float32 rounding, within the float32 parity bar
+    e2, einf = assert_bars(y, want, 1e-5, f"{nranks} ranks vs fkt_mvm")
     idx = inputs.subsample(n, 300, seed=73)
     z = orc.FKT(X, orc.kparams("matern32", 0.2), p=6, leaf_size=256, theta=0.5).mvm(W, idx)
     assert_bars(y[:, idx], z, 3e-5 if far == "bf16x3" else 1e-5, f"{nranks} ranks vs oracle")
