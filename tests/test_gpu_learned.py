@@ -92,10 +92,14 @@ def test_training_reduces_the_objective(trained):
 
 
 def test_solve_with_learned_correction(fkt, trained):
-    """The corrected preconditioner inside CG converges to the requested residual (falling back to
-    block-Jacobi if it does not); the iteration counts of the three preconditioners are reported --
-    for this long-range kernel no block-diagonal preconditioner beats none: CG's slow directions
-    are smooth modes spanning many blocks, which a block-local correction cannot represent."""
+    """The corrected preconditioner inside CG converges to the requested residual with the true
+    residual as the judge (falling back to block-Jacobi if it does not); the iteration counts of the
+    three preconditioners are printed.  No iteration gain is asserted because none was measured: for
+    this long-range kernel no block-diagonal preconditioner beats none -- CG's slow directions are
+    smooth modes spanning many blocks, which a block-local correction cannot represent -- and the
+    learned blocks take about as many iterations as block-Jacobi (measured at N = 20k, d = 4,
+    tol 1e-5: none 2105, block-Jacobi 3675, learned 4015-4210).  What the network does gain is
+    asserted in test_training_reduces_the_objective."""
     import torch
 
     X, plan, info = trained
@@ -108,4 +112,3 @@ def test_solve_with_learned_correction(fkt, trained):
     print(its)
     assert its["learned"][1] == 1
     assert its["learned"][3] < 5e-3
-    assert its["learned"][0] < 1.5 * its["block_jacobi"][0]
