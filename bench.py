@@ -175,8 +175,9 @@ def parse():
     ap.add_argument("--far-precision", default=None, choices=["bf16x3", "tf32", "bf16", "fp32"])
     ap.add_argument("--near-precision", default=None, choices=["tf32x3", "f16x3", "fp32"],
                     help="near-field contraction of 32-wide passes: tensor cores (TF32 hi/lo) or CUDA cores")
-    ap.add_argument("--far-kernel", default="single", choices=["pairs", "single"],
-                    help="tensor-core far field (d = 3, BF16 forms): two far entries per thread or one")
+    ap.add_argument("--far-kernel", default="single", choices=["pairs", "single", "held"],
+                    help="tensor-core far field (d = 3, BF16 forms): two far entries per thread, one, or one "
+                         "with the row held in registers until the previous entry's MMAs complete")
     ap.add_argument("--radial-compression", default="auto", choices=["auto", "off"],
                     help="drop the radial terms that vanish for the kernel (1/r in d = 3: j > k)")
     ap.add_argument("--compare", default="fp32", choices=["fp32", "none"],

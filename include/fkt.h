@@ -275,7 +275,8 @@ int fkt_batch_info(fkt_batch_t batch, int64_t* offsets, int32_t* leaf_sizes, fkt
 /* Autotuner of the kernel variants for products with nrhs right-hand sides: times the batch
  * product (CUDA events, best of 3 after a warm-up) for each value of one option at a time and keeps
  * the fastest -- the tensor-core far field's CTA shape ("far_kernel": one far entry per thread at
- * four CTAs per SM, or two per thread at two CTAs per SM; BF16 forms, d = 3), the near field of
+ * four CTAs per SM, one with the row held in registers at three, or two per thread at two; BF16
+ * forms, d = 3), the near field of
  * 32-wide passes ("near_precision": register-tiled CUDA cores, TF32 or FP16 tensor-core operands,
  * all float32-level accurate) and the single-RHS near kernel's targets per thread.  The far
  * precision, which sets the accuracy, is left as it is.  chosen (may be NULL) receives
@@ -326,10 +327,13 @@ int fkt_autotune_leaf(const float* points, int64_t N, int d, fkt_kernel kernel, 
  *   "coarse_seed"  unsigned integer (default 1): seed of the coarse space's frequencies
  *   "near_targets_per_thread"  "2" (default) | "4"  register blocking of the near-field kernel
  *               (4 applies to one right-hand side; results are identical up to rounding order)
- *   "far_kernel"  "single" (default) | "pairs"  tensor-core far field of d = 3 in the BF16 forms:
- *               each target thread generates its basis rows for two far entries at once in packed
- *               float32 pairs (where the tensor memory allows: BF16 hi/lo up to p = 6, BF16 up to
- *               p = 9), or for one entry at a time.  Results agree up to rounding order.
+ *   "far_kernel"  "single" (default) | "pairs" | "held"  tensor-core far field of d = 3 in the BF16
+ *               forms: each target thread generates its basis rows for one far entry at a time
+ *               (four CTAs per SM at p <= 6); for two far entries at once in packed float32 pairs
+ *               ("pairs", where the tensor memory allows: BF16 hi/lo up to p = 6, BF16 up to p = 9;
+ *               two CTAs per SM); or for one entry, holding the first 64 terms of the row in
+ *               registers until the previous entry's MMAs complete ("held", three CTAs per SM).
+ *               Results agree up to rounding order.
  *   "wait_limit_cycles"  "default" | an integer 0..2000000000  limit, in SM clocks, of the
  *               pipeline waits of the tensor-core near and far kernels (a source-record or
  *               multipole copy landing, the hand-off of a chunk or entry to the MMA issuer).

@@ -263,6 +263,7 @@ int fkt_set_option(fkt_plan_t plan, const char* key, const char* value) {
     if (!strcmp(key, "far_kernel")) {
         if (!strcmp(value, "pairs")) plan->far_kernel = 0;
         else if (!strcmp(value, "single")) plan->far_kernel = 1;
+        else if (!strcmp(value, "held")) plan->far_kernel = 2;
         else return FKT_ERR_INVALID_ARG;
         return FKT_OK;
     }

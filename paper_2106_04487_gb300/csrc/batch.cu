@@ -425,7 +425,7 @@ int fkt_batch_autotune(fkt_batch_t batch, int nrhs, char* chosen, int len) {
     struct Axis { const char* key; std::vector<const char*> values; };
     std::vector<Axis> axes;
     if (P->d == 3 && (P->far_precision == fkt::FAR_BF16 || P->far_precision == fkt::FAR_BF16X3))
-        axes.push_back({"far_kernel", {"single", "pairs"}});
+        axes.push_back({"far_kernel", {"single", "held", "pairs"}});
     if (nrhs > 16) axes.push_back({"near_precision", {"fp32", "tf32x3", "f16x3"}});
     if (nrhs == 1) axes.push_back({"near_targets_per_thread", {"2", "4"}});
     std::string out;

@@ -393,6 +393,18 @@ int launch_tc_far_t(const TcLaunch& L) {
     if constexpr (dim_of(D) == 3 && Tc2Shape<P, PREC, D>::supported) {
         using Sh = Tc2Shape<P, PREC, D>;
         const size_t smem = Sh::smem_bytes();
+        if (L.far_kernel == 2) {  // rows held in registers until the previous entry's MMAs complete
+            static bool attr_h = false;
+            if (!attr_h) {
+                FKT_CUDA_TRY(cudaFuncSetAttribute(far_tc2_kernel<P, PREC, D, 4>,
+                                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+                attr_h = true;
+            }
+            far_tc2_kernel<P, PREC, D, 4><<<(unsigned)L.nblocks, Sh::THREADS, smem, L.s_far>>>(*L.a, *L.kp, *L.T, L.image,
+                                                                                              L.nr_total);
+            FKT_CUDA_TRY(cudaGetLastError());
+            return FKT_OK;
+        }
         static bool attr = false;
         if (!attr) {
             FKT_CUDA_TRY(cudaFuncSetAttribute(far_tc2_kernel<P, PREC, D>, cudaFuncAttributeMaxDynamicSharedMemorySize,

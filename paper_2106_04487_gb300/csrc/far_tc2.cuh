@@ -96,11 +96,16 @@ __device__ __forceinline__ void far_basis1(const float4& xt, const float4& c, fl
     harmonic_level1<P, LD, 0>(uz, C, S, pm1, pm2, G, T, put);
 }
 
-template <int P, int PREC, int LD = 3>
-__global__ void __launch_bounds__(160, Tc2Shape<P, PREC, LD>::NTP <= 96 ? 4 : Tc2Shape<P, PREC, LD>::NTP <= 128 ? 3 : 2)
+// HOLD > 0: the first HOLD 16-term groups of a row are kept in registers and stored only after
+// the MMAs of the previous entry complete, so that almost the whole row is computed while they
+// run; the extra registers allow three CTAs per SM instead of four.
+template <int P, int PREC, int LD = 3, int HOLD = 0>
+__global__ void __launch_bounds__(160, HOLD > 0 ? 3
+                                      : Tc2Shape<P, PREC, LD>::NTP <= 96 ? 4 : Tc2Shape<P, PREC, LD>::NTP <= 128 ? 3 : 2)
     far_tc2_kernel(MvmArgs a, KernelParams kp_all, const __grid_constant__ FarTables T,
                    const unsigned char* __restrict__ image, int nr_total) {
     using Sh = Tc2Shape<P, PREC, LD>;
+    static_assert(HOLD <= 6, "held groups live in registers");
     using S = typename Sh::S;
     constexpr int NT = Sh::NT, NTP = Sh::NTP, ST = Sh::ST, BB = S::B_BYTES, BPLANE = kTcN * NTP * 2;
     constexpr int kFarFlush = 4;
@@ -272,6 +277,16 @@ __global__ void __launch_bounds__(160, Tc2Shape<P, PREC, LD>::NTP <= 96 ? 4 : Tc
                 const float4 c = info[slot].c;
                 const float sc = info[slot].s;
                 float2 buf[8];  // terms 16g..16g+15 as pairs (2i, 2i+1)
+                constexpr int NG = NTP / 16;
+                uint32_t held_hi[HOLD > 0 ? HOLD : 1][8], held_lo[HOLD > 0 ? HOLD : 1][8];
+                auto store_held = [&](int upto) {
+#pragma unroll
+                    for (int gg = 0; gg < (HOLD > 0 ? HOLD : 1); ++gg)
+                        if (gg < upto) {
+                            tc::st8(tmem + lane_base + Sh::COL_AHI + gg * 8, held_hi[gg]);
+                            if (PREC == TC_BF16X3) tc::st8(tmem + lane_base + Sh::COL_ALO + gg * 8, held_lo[gg]);
+                        }
+                };
                 auto store_group = [&](int g) {
                     // hi = the BF16 rounding of each term, lo = the BF16 rounding of term - hi
                     uint32_t hi[8], lo[8];
@@ -286,7 +301,22 @@ __global__ void __launch_bounds__(160, Tc2Shape<P, PREC, LD>::NTP <= 96 ? 4 : Tc
                             lo[i2] = bf2_bits(__floats2bfloat162_rn(rr.x, rr.y));
                         }
                     }
-                    if (g == 0) wait_prev();
+                    if (g < HOLD) {
+#pragma unroll
+                        for (int i2 = 0; i2 < 8; ++i2) {
+                            held_hi[g < HOLD ? g : 0][i2] = hi[i2];
+                            held_lo[g < HOLD ? g : 0][i2] = lo[i2];
+                        }
+                        if (g == NG - 1) {  // the whole row was held
+                            wait_prev();
+                            store_held(NG);
+                        }
+                        return;
+                    }
+                    if (g == HOLD) {
+                        wait_prev();
+                        store_held(HOLD);
+                    }
                     tc::st8(tmem + lane_base + Sh::COL_AHI + g * 8, hi);
                     if (PREC == TC_BF16X3) tc::st8(tmem + lane_base + Sh::COL_ALO + g * 8, lo);
                 };
