@@ -26,7 +26,7 @@ void free_plan(fkt_plan_s* P) {
                     P->nd_centre, P->nd_rho2, P->nd_cf, P->nd_scale, P->nd_used, P->blk_range, P->far_off,
                     P->near_off, P->far_ent, P->near_ent, P->masks, P->s2m_items, P->s2m_node_items,
                     P->s2m_item_off, P->rec, P->ynear, P->yfar, P->mult, P->s2m_part, P->tc_image, P->hbuf_w, P->hbuf_y,
-                    P->d_err, P->d_wmax, P->dense_off, P->dense_ent};
+                    P->d_err, P->d_wmax, P->dense_off, P->dense_ent, P->nd_img, P->nimg};
     for (void* b : bufs)
         if (b) cudaFree(b);
     fkt::free_learn(P);
@@ -125,6 +125,7 @@ int fkt_plan(const float* points, int64_t N, int d, fkt_kernel kernel, int p, in
     }
     rc = fkt::build_tree(P, points);
     if (!rc) rc = fkt::build_lists(P);
+    if (!rc) rc = fkt::build_near_image_index(P);
     if (!rc && cudaStreamSynchronize(P->stream) != cudaSuccess) rc = FKT_ERR_CUDA;
     if (rc) { free_plan(P); return rc; }
     fkt_stats& s = P->stats;

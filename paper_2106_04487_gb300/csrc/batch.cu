@@ -321,6 +321,7 @@ int fkt_batch_plan(int nprob, const fkt_problem* probs, int d, int p, int leaf_s
                     cudaMalloc(&M->d_wmax, sizeof(unsigned) * 32) != cudaSuccess))
             rc = FKT_ERR_OOM;
         if (!rc) rc = fkt::merge_plans(plans, M);
+        if (!rc) rc = fkt::build_near_image_index(M);
     }
     for (auto* Q : plans)
         if (Q) free_plan_all(Q);

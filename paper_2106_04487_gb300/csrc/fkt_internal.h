@@ -18,6 +18,14 @@ constexpr int kMaskWords = kTB / 32;
 constexpr int kMaxRhs = 64;
 constexpr int kMaxTerms = 495;    // binom(8+4, 4); binom(10+3, 3) = 286
 constexpr long long kWaitCycles = 2000000000;  // ~1 s at 2 GHz: a device-side wait this long is a fault
+// Near-field image of a 32-wide pass on the tensor cores: per leaf, its sources in groups of 4
+// (the leaf starting at a multiple of 8 image positions, zero-padded to a multiple of 8), each
+// group 272 floats: the TF32 hi parts of the 4 x 32 weights in the MMA's K-major core-matrix
+// order (right-hand side n, source k: float 4n + k), the lo parts the same way, then the
+// negated, kernel-scaled coordinates -x[4], -y[4], -z[4], -u[4].
+constexpr int kNearGroupFloats = 272;
+constexpr int kNearGroupBytes = 4 * kNearGroupFloats;     // 1088: the MMA's leading-dimension offset
+constexpr int kNearChunkBytes = 8 * kNearGroupBytes;      // one 32-source chunk
 
 // Far-field coefficient tables handed to the kernels by value (they land in the
 // constant bank).  Index conventions:
@@ -109,6 +117,10 @@ struct fkt_plan_s {
     float* s2m_part = nullptr;     // per-item partial multipoles [items][nterms][nrhs]
     unsigned char* tc_image = nullptr;  // packed tensor-core operands of the multipoles
     int cap_tc = 0;                // far_precision the image was sized for (0: none)
+    int32_t* nd_img = nullptr;     // per node: image position of a leaf's first source (-1: not a leaf)
+    int64_t img_pos = 0;           // image positions of all leaves (each leaf padded to a multiple of 8)
+    float* nimg = nullptr;         // near-field image of one 32-wide pass (tensor-core near field)
+    size_t cap_nimg = 0;           // floats allocated for it
     float* hbuf_w = nullptr;       // device staging for fkt_mvm_host
     float* hbuf_y = nullptr;
     int hbuf_cap = 0;              // right-hand sides the staging buffers hold
@@ -189,15 +201,18 @@ struct MvmBuffers {
     float* part;
     unsigned char* image;  // tensor-core operand image of the multipoles (far_precision != fp32)
     float* yfar;           // far-field result, tree order
+    float* nimg;           // near-field image of one pass (32-wide passes on the TF32 tensor-core kernel)
 };
-constexpr int kMvmBufs = 6;
+constexpr int kMvmBufs = 7;
 // Floats each buffer needs for nrhs right-hand sides (each rounded up to 64 floats), in the
-// order rec, ynear, mult, part, image, yfar.
+// order rec, ynear, mult, part, image, yfar, nimg.
 void mvm_buffer_floats(const fkt_plan_s* P, int nrhs, size_t out[kMvmBufs]);
 int run_mvm(fkt_plan_s* P, const MvmBuffers& B, const float* w, float* y, int nrhs, bool timing);
 int launch_mvm(fkt_plan_s* P, const float* w, float* y, int nrhs);
 int launch_dense(fkt_plan_s* P, const float* w, float* y, int nrhs);
 int ensure_rhs_capacity(fkt_plan_s* P, int nrhs);
+// nd_img and img_pos from the tree (host scan over the leaves); once per plan or merged batch.
+int build_near_image_index(fkt_plan_s* P);
 
 // The plan's second stream (s2m and the far field), non-blocking.  (A higher priority for it
 // makes the far field overlap the near field but gives no net speed-up: both stages compete for

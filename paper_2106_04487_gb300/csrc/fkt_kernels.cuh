@@ -235,6 +235,7 @@ struct MvmArgs {
     const float* nd_scale;
     const int4* s2m_items;
     const int64_t* s2m_item_off;
+    const int32_t* nd_img;     // image position of each leaf's first source (near-field image)
     int64_t nnodes;
     // per pass (one group of NR right-hand sides)
     const float4* rec;         // source records in tree order: rec_f4 float4 per point (point, then weights)
@@ -245,6 +246,7 @@ struct MvmArgs {
     float* part;               // s2m partials, [items][nterms][NR]
     float* y;                  // output (original order), [nrhs][N]; this group starts at y
     float* yfar;               // far-field result of this group (tree order), [NR][N]
+    const float* nimg;         // near-field image of this pass (32-wide tensor-core passes)
     int nr;                    // right-hand sides actually present in this group (<= NR)
     int* err;                  // device error word: 1 = a bounded wait ran out
     // batches of independent problems (all null for a single problem)

@@ -5,6 +5,8 @@
 // per pass (the kernel value of a pair serves every right-hand side of the pass), s2m and the
 // float32 far field per group of 8 (or 1 for a single right-hand side), the tensor-core far
 // field once per pass.
+#include <climits>
+#include <vector>
 #include <algorithm>
 
 #include "mvm_kernels.cuh"
@@ -33,6 +35,8 @@ int launch_tc_diag_p7_10(int p, int prec, bool far, const TcLaunch& L);
 
 void launch_near_d3(int nw, int tpt, int kind, unsigned grid, cudaStream_t st, const MvmArgs& a, const KernelParams& kp);
 void launch_near_d4(int nw, int tpt, int kind, unsigned grid, cudaStream_t st, const MvmArgs& a, const KernelParams& kp);
+void launch_near_image(int64_t nnodes, const int32_t* nd_leaf, const int32_t* nd_begin, const int32_t* nd_end,
+                       const int32_t* nd_img, const float4* rec, int rec_f4, float* img, cudaStream_t st);
 void launch_near_tc_d3(int kind, unsigned grid, cudaStream_t st, const MvmArgs& a, const KernelParams& kp);
 void launch_near_tc_d4(int kind, unsigned grid, cudaStream_t st, const MvmArgs& a, const KernelParams& kp);
 void launch_near_tc2_d3(int kind, unsigned grid, cudaStream_t st, const MvmArgs& a, const KernelParams& kp, unsigned* wmax);
@@ -142,6 +146,7 @@ MvmArgs base_args(fkt_plan_s* P) {
     a.nd_scale = P->nd_scale;
     a.s2m_items = P->s2m_items;
     a.s2m_item_off = P->s2m_item_off;
+    a.nd_img = P->nd_img;
     a.nnodes = P->nnodes;
     a.err = P->d_err;
     a.kps = P->kps;
@@ -180,8 +185,27 @@ static int near_tc_mode(const fkt_plan_s* P, bool exact) {
     return P->near_precision == NEAR_TF32X3 ? 1 : P->near_precision == NEAR_F16X3 ? 2 : 0;
 }
 
+// Whether a near stage of nw-wide passes runs the TF32 tensor-core kernel, which reads the pass's
+// near-field image (the FP16 kernel leaves the 1/r kernel to it).
+static bool near_uses_image(const fkt_plan_s* P, int tc, int nw) {
+    if (nw != 32 || tc == 0) return false;
+    if (tc == 1) return true;
+    if (P->nprob == 0) return P->kernel.kind == FKT_LAPLACE;
+    for (int k : P->kind_of_list)
+        if (k == FKT_LAPLACE) return true;
+    return false;
+}
+
+// The pass's near-field image from its source records (a.rec), when the near stage reads it.
+static void pack_near_image(fkt_plan_s* P, const MvmArgs& a, int tc, int nw, cudaStream_t st) {
+    if (!near_uses_image(P, tc, nw)) return;
+    launch_near_image(P->nnodes, P->nd_leaf, P->nd_begin, P->nd_end, P->nd_img, a.rec, a.rec_f4,
+                      const_cast<float*>(a.nimg), st);
+}
+
 void launch_near_stage(fkt_plan_s* P, MvmArgs& a, int nrb, int tpt, cudaStream_t st, bool exact) {
     const int tc = near_tc_mode(P, exact);
+    pack_near_image(P, a, tc, nrb, st);
     if (P->nprob == 0) {
         a.blk_list = nullptr;
         launch_near(P->d, nrb, tpt, tc, P->kernel.kind, (unsigned)P->nblocks, st, a, P->kp, P->d_wmax);
@@ -218,6 +242,9 @@ void mvm_buffer_floats(const fkt_plan_s* P, int nrhs, size_t out[kMvmBufs]) {
     out[4] = P->far_precision == FAR_FP32 ? 0
              : round64(nodes * (size_t)tc_b_bytes(P->nterms, tc_prec_of(P->far_precision)) / 4);
     out[5] = round64(groups * nrb * N);                  // far result
+    out[6] = near_uses_image(P, near_tc_mode(P, false), nw)  // near-field image of one pass
+                 ? round64((size_t)(P->img_pos / 4) * kNearGroupFloats)
+                 : 0;
 }
 
 int ensure_rhs_capacity(fkt_plan_s* P, int nrhs) {
@@ -240,6 +267,13 @@ int ensure_rhs_capacity(fkt_plan_s* P, int nrhs) {
         FKT_CUDA_TRY(cudaMalloc(&P->s2m_part, sizeof(float) * f[3]));
         FKT_CUDA_TRY(cudaMalloc(&P->yfar, sizeof(float) * f[5]));
         P->cap_rhs = cap;
+    }
+    if (f[6] > P->cap_nimg) {
+        cudaFree(P->nimg);
+        P->nimg = nullptr;
+        P->cap_nimg = 0;
+        FKT_CUDA_TRY(cudaMalloc(&P->nimg, sizeof(float) * f[6]));
+        P->cap_nimg = f[6];
     }
     if (f[4] && P->cap_tc != P->far_precision + 1) {
         cudaFree(P->tc_image);
@@ -295,6 +329,7 @@ int run_mvm(fkt_plan_s* P, const MvmBuffers& B, const float* w, float* y, int nr
         MvmArgs a = base_args(P);
         a.rec = B.rec;
         a.rec_f4 = rec_f4(P->d, nw);
+        a.nimg = B.nimg;
         launch_permute(P->d, nw, pgrid, st, N, P->perm, P->xs, w + (size_t)r0 * N, npass, P->kp.sig, P->pt_sig, B.rec);
         FKT_CUDA_TRY(cudaGetLastError());
         // fork: s2m and the far field on the second stream, the near field on the plan stream
@@ -431,12 +466,39 @@ int shard_end(fkt_plan_s* P, const float* mult, float* y, int nrhs) {
     }
     a.ynear = P->ynear;
     a.nr = nrhs;
+    a.nimg = P->nimg;
+    pack_near_image(P, a, near_tc_mode(P, false), nw, st);
     launch_near(P->d, nw, P->near_tpt, near_tc_mode(P, false), P->kernel.kind, (unsigned)nb, st, a, P->kp, P->d_wmax);
     FKT_CUDA_TRY(cudaGetLastError());
     const int64_t nt = P->sh_t1 - P->sh_t0;
     unpermute_range_kernel<<<(unsigned)((nt + 255) / 256), 256, 0, st>>>(P->sh_t0, P->sh_t1, N, nrhs, P->perm, P->ynear,
                                                                          P->yfar, y);
     FKT_CUDA_TRY(cudaGetLastError());
+    return FKT_OK;
+}
+
+int build_near_image_index(fkt_plan_s* P) {
+    const int64_t nn = P->nnodes;
+    cudaFree(P->nd_img);
+    P->nd_img = nullptr;
+    P->img_pos = 0;
+    if (nn <= 0) return FKT_OK;
+    std::vector<int32_t> leaf(nn), b(nn), e(nn), img(nn, -1);
+    FKT_CUDA_TRY(cudaMemcpyAsync(leaf.data(), P->nd_leaf, 4 * nn, cudaMemcpyDeviceToHost, P->stream));
+    FKT_CUDA_TRY(cudaMemcpyAsync(b.data(), P->nd_begin, 4 * nn, cudaMemcpyDeviceToHost, P->stream));
+    FKT_CUDA_TRY(cudaMemcpyAsync(e.data(), P->nd_end, 4 * nn, cudaMemcpyDeviceToHost, P->stream));
+    FKT_CUDA_TRY(cudaStreamSynchronize(P->stream));
+    int64_t pos = 0;
+    for (int64_t i = 0; i < nn; ++i) {
+        if (!leaf[i]) continue;
+        img[i] = (int32_t)pos;
+        pos += (int64_t)(e[i] - b[i] + 7) / 8 * 8;
+        if (pos > INT32_MAX) return FKT_ERR_INVALID_ARG;
+    }
+    FKT_CUDA_TRY(cudaMalloc(&P->nd_img, 4 * nn));
+    FKT_CUDA_TRY(cudaMemcpyAsync(P->nd_img, img.data(), 4 * nn, cudaMemcpyHostToDevice, P->stream));
+    FKT_CUDA_TRY(cudaStreamSynchronize(P->stream));
+    P->img_pos = pos;
     return FKT_OK;
 }
 
@@ -448,7 +510,7 @@ int create_far_stream(cudaStream_t* s) {
 int launch_mvm(fkt_plan_s* P, const float* w, float* y, int nrhs) {
     int rc = ensure_rhs_capacity(P, nrhs);
     if (rc) return rc;
-    MvmBuffers B{P->rec, P->ynear, P->mult, P->s2m_part, P->tc_image, P->yfar};
+    MvmBuffers B{P->rec, P->ynear, P->mult, P->s2m_part, P->tc_image, P->yfar, P->nimg};
     return run_mvm(P, B, w, y, nrhs, P->timing);
 }
 

@@ -4,18 +4,21 @@
 // the dense product (Algorithm 1, the near-field sum of eq. nbody over the leaf)
 //     z[t][r] += sum_s K(|x_t - x_s|) w[s][r]        (128 x 32) += (128 x 32) (32 x 32).
 // The CUDA cores evaluate the kernel values in float32, one target row per thread, and write the
-// row straight into tensor memory as the A operand (tcgen05.st); the chunk's weights, bulk-copied
-// as source records, are rearranged in shared memory into the B operand; one thread issues
-// tcgen05.mma (kind::tf32, A from tensor memory, M = 128 targets, N = 32 right-hand sides, K = 8
-// sources per instruction) into a float32 accumulator in tensor memory.
+// row straight into tensor memory as the A operand (tcgen05.st); one thread issues tcgen05.mma
+// (kind::tf32, A from tensor memory, M = 128 targets, N = 32 right-hand sides, K = 8 sources per
+// instruction) into a float32 accumulator in tensor memory.  The B operand (the chunk's weights,
+// split hi/lo) and the chunk's source coordinates come ready-made from the pass's near-field
+// image (near_image_kernel, once per pass): the bulk copy lands them in shared memory in the
+// layout the MMA and the target threads read, so no thread rearranges weights per chunk.
 //
-// float32 accuracy from TF32 operands: every factor v is split into hi = v rounded to TF32 (10
-// mantissa bits) and lo = v - hi (exact in float32, |lo| <= 2^-11 |v|); the tensor core adds
+// float32 accuracy from TF32 operands: every factor v is split into hi = v with 10 mantissa bits
+// (the weights rounded to nearest once per pass; the kernel values truncated, one instruction
+// per value) and lo = v - hi (exact in float32, |lo| <= 2^-10 |v|); the tensor core adds
 // hi*hi + hi*lo + lo*hi.  The dropped lo*lo and the truncation of lo to TF32 leave at most about
-// 2^-20 of each product, with random sign.  The tensor core's own float32 accumulation is not
+// 2^-20 of each product.  The tensor core's own float32 accumulation is not
 // round-to-nearest: summed over the thousands of MMAs of a target block it drifts by about 2^-24
 // per MMA in one direction (measured: 2e-5 relative after ~600 MMAs).  So every few chunks each
-// thread adds its accumulator row into float32 registers (round-to-nearest) and zeroes it.
+// thread adds its accumulator row into float32 sums (round-to-nearest) and zeroes it.
 #pragma once
 
 #include "mvm_kernels.cuh"
@@ -25,13 +28,13 @@ namespace fkt {
 struct NearTcShape {
     static constexpr int NR = 32;                     // right-hand sides (the MMA's N)
     static constexpr int CH = 32;                     // sources per chunk (4 MMA K-steps of 8)
-    static constexpr int ST = 4;                      // record stages in flight
-    static constexpr int F4 = (4 + NR + 3) / 4;       // float4s per source record (point + weights)
+    static constexpr int ST = 4;                      // chunk stages in flight
     static constexpr int CONSUMERS = 4;               // warps that own the 128 TMEM lanes / targets
     static constexpr int THREADS = 32 * (CONSUMERS + 1);  // + one producer / MMA-issuer warp
     static constexpr int TMEM_COLS = 128;             // accumulator 32 + A hi 32 + A lo 32
     static constexpr int COL_AHI = 32, COL_ALO = 64;
     static constexpr int FLUSH = 4;                   // chunks (12 MMAs each) per float32 flush
+    static constexpr int SMEM_BYTES = ST * kNearChunkBytes + NR * CONSUMERS * 32 * 4;  // stages + float32 sums
 };
 
 namespace tc {
@@ -155,10 +158,11 @@ __device__ __forceinline__ float2 kval2(float2 q, const KernelParams& kp) {
     }
 }
 
-// Two kernel values -> their TF32 hi parts (bits) and float32 lo = v - hi.
+// Two kernel values -> their TF32 hi parts (bits: v truncated to 10 mantissa bits) and float32
+// lo = v - hi (exact, same sign as v, |lo| < 2^-10 |v|).
 __device__ __forceinline__ void split2(float2 v, uint32_t& h0, uint32_t& h1, uint32_t& l0, uint32_t& l1) {
-    h0 = (__float_as_uint(v.x) + 0x1000u) & 0xFFFFE000u;
-    h1 = (__float_as_uint(v.y) + 0x1000u) & 0xFFFFE000u;
+    h0 = __float_as_uint(v.x) & 0xFFFFE000u;
+    h1 = __float_as_uint(v.y) & 0xFFFFE000u;
     const float2 lo = __ffma2_rn(make_float2(__uint_as_float(h0), __uint_as_float(h1)), make_float2(-1.f, -1.f), v);
     l0 = __float_as_uint(lo.x);
     l1 = __float_as_uint(lo.y);
@@ -175,7 +179,7 @@ __device__ __forceinline__ void add_partial(uint32_t taddr, float acc[32]) {
     for (int r = 0; r < 32; ++r) acc[r] += d[r];
 }
 
-// Per record stage: what the producer resolved for the chunk it holds.
+// Per chunk stage: what the producer resolved for the chunk it holds.
 struct NearChunkInfo {
     int n;                     // sources in the chunk
     uint32_t on[kMaskWords];   // targets (TMEM lanes) that use the chunk's leaf
@@ -183,15 +187,15 @@ struct NearChunkInfo {
 
 // One CTA per 128-target block, warp-specialised:
 //   warps 0-3 (consumers, thread = target = TMEM lane): per chunk c of up to 32 sources, wait for
-//     its records; wait (named barrier) until the MMAs of chunk c-1 are complete, which frees the
-//     A columns and the B planes; every FLUSH chunks add the accumulator rows into float32
-//     registers and zero them; rearrange their share of the weights into the B planes; a warp
-//     with a target in the chunk's mask evaluates its rows (float32 kernel values, split hi/lo)
-//     into tensor memory; then arrive on the ready barrier.
+//     its image stage; a warp with a target in the chunk's mask evaluates its rows (float32
+//     kernel values against the stage's coordinates, split hi/lo) into registers; wait (named
+//     barrier) until the MMAs of chunk c-1 are complete, which frees the A columns; every FLUSH
+//     chunks add the accumulator rows into the float32 sums and zero them; store the rows into
+//     tensor memory; then arrive on the ready barrier.
 //   warp 4 (producer / MMA issuer, lane 0 works): resolves chunk metadata from the lists and
-//     bulk-copies source records ST chunks ahead; per chunk syncs on the ready barrier, issues 3
-//     MMAs per 8 sources (rows outside the mask disabled), refills the chunk's record stage,
-//     waits for the MMAs and arrives on the MMA barrier.
+//     bulk-copies image chunks ST ahead; per chunk syncs on the ready barrier, issues 3 MMAs per
+//     8 sources (B straight from the stage; rows outside the mask disabled), waits for them,
+//     arrives on the MMA barrier and refills the stage.
 // Hand-offs between the roles use named barriers, so waiting warps are descheduled instead of
 // polling.  Both roles run the same number of rounds (the block's chunk count, counted by all
 // threads up front) whatever happens: a bounded mbarrier wait that runs out sets s_fail, which
@@ -199,18 +203,17 @@ struct NearChunkInfo {
 template <int D, int KIND>
 __global__ void __launch_bounds__(NearTcShape::THREADS, 4) near_tc_kernel(MvmArgs a, KernelParams kp_all) {
     using S = NearTcShape;
-    constexpr int CH = S::CH, ST = S::ST, F4 = S::F4, NR = S::NR, NC = S::CONSUMERS;
+    constexpr int CH = S::CH, ST = S::ST, NR = S::NR, NC = S::CONSUMERS, GF = kNearGroupFloats;
     constexpr uint32_t IDESC = tc::instr_desc(2u, 128u, (uint32_t)NR);
     constexpr uint32_t kBarReady = 1, kBarMma = 2, kBarThreads = S::THREADS;
-    __shared__ __align__(128) float4 stage[ST][CH * F4];
-    __shared__ __align__(128) float bpl[2][CH * NR];        // B hi / lo: K-major core matrices
-    __shared__ __align__(16) float s_src[NC][4][CH];        // per consumer warp: -x, -y, -z, -u (SoA)
+    extern __shared__ __align__(128) unsigned char near_smem[];
+    float* stage = reinterpret_cast<float*>(near_smem);                              // [ST][8 groups][GF]
+    float(*s_acc)[NC * 32] = reinterpret_cast<float(*)[NC * 32]>(near_smem + ST * kNearChunkBytes);  // [NR][128]
     __shared__ NearChunkInfo info[ST];
     __shared__ __align__(8) uint64_t full[ST], mma_done;
     __shared__ uint32_t tmem_base;
     __shared__ uint32_t s_valid[kMaskWords];
     __shared__ int s_fail, s_nch;
-    __shared__ float s_acc[NR][NC * 32];                     // float32 sums of the accumulator rows
     const int tl = threadIdx.x, warp = tl >> 5, lane = tl & 31;
     const int64_t blk = cta_block(a);
     const KernelParams kp = block_params(a, blk, kp_all);
@@ -251,25 +254,25 @@ __global__ void __launch_bounds__(NearTcShape::THREADS, 4) near_tc_kernel(MvmArg
 
     if (warp == NC) {
         // ---------------------------------------------------------------- producer / issuer
-        // The whole warp walks the chunk sequence in step: every lane holds the leaf range and
-        // row mask of one entry of a 32-entry window (loaded together, one memory latency per 32
-        // entries), lane 0 issues the copies.
+        // The whole warp walks the chunk sequence in step: every lane holds the image position,
+        // source count and row mask of one entry of a 32-entry window (loaded together, one
+        // memory latency per 32 entries), lane 0 issues the copies.
         int64_t wbase = e0;
-        int wbeg = 0, wend = 0;
+        int wimg = 0, wn = 0;
         uint32_t wm[kMaskWords] = {0u, 0u, 0u, 0u};
         auto load_window = [&]() {
             const int64_t e = wbase + lane;
-            wbeg = wend = 0;
+            wimg = wn = 0;
             if (e < e1) {
                 const int2 ent = a.near_ent[e];
-                wbeg = a.nd_begin[ent.x];
-                wend = a.nd_end[ent.x];
+                wimg = a.nd_img[ent.x];
+                wn = a.nd_end[ent.x] - a.nd_begin[ent.x];
 #pragma unroll
                 for (int w = 0; w < kMaskWords; ++w)
                     wm[w] = (ent.y < 0 ? 0xFFFFFFFFu : __ldg(&a.masks[(int64_t)ent.y * kMaskWords + w])) & s_valid[w];
             }
         };
-        int ei = 0, cb = 0, cend = 0, issued = 0;
+        int ei = 0, img0 = 0, cb = 0, cend = 0, issued = 0;
         bool pdone = wbase >= e1;
         auto settle = [&]() {  // warp-uniform: advance to the next entry with sources left
             while (!pdone && cb >= cend) {
@@ -280,8 +283,9 @@ __global__ void __launch_bounds__(NearTcShape::THREADS, 4) near_tc_kernel(MvmArg
                     load_window();
                 }
                 if (wbase + ei >= e1) { pdone = true; break; }
-                cb = __shfl_sync(0xffffffffu, wbeg, ei);
-                cend = __shfl_sync(0xffffffffu, wend, ei);
+                img0 = __shfl_sync(0xffffffffu, wimg, ei);
+                cend = __shfl_sync(0xffffffffu, wn, ei);
+                cb = 0;
             }
         };
         auto produce = [&]() {  // warp-collective
@@ -296,9 +300,9 @@ __global__ void __launch_bounds__(NearTcShape::THREADS, 4) near_tc_kernel(MvmArg
                 in.n = n;
 #pragma unroll
                 for (int w = 0; w < kMaskWords; ++w) in.on[w] = on[w];
-                const uint32_t bytes = (uint32_t)n * F4 * 16u;
+                const uint32_t bytes = (uint32_t)((n + 7) / 8) * 2u * kNearGroupBytes;
                 ptx::mbar_arrive_expect_tx(&full[slot], bytes);
-                ptx::bulk_g2s(&stage[slot][0], a.rec + (int64_t)cb * F4, bytes, &full[slot]);
+                ptx::bulk_g2s(stage + slot * 8 * GF, a.nimg + (int64_t)((img0 + cb) / 4) * GF, bytes, &full[slot]);
             }
             ++issued;
             cb += CH;
@@ -306,8 +310,9 @@ __global__ void __launch_bounds__(NearTcShape::THREADS, 4) near_tc_kernel(MvmArg
         };
         if (!pdone) {
             load_window();
-            cb = __shfl_sync(0xffffffffu, wbeg, 0);
-            cend = __shfl_sync(0xffffffffu, wend, 0);
+            img0 = __shfl_sync(0xffffffffu, wimg, 0);
+            cend = __shfl_sync(0xffffffffu, wn, 0);
+            cb = 0;
             settle();
         }
         for (int s = 0; s < ST; ++s) produce();
@@ -320,9 +325,10 @@ __global__ void __launch_bounds__(NearTcShape::THREADS, 4) near_tc_kernel(MvmArg
                 const NearChunkInfo in = info[slot];
                 const uint32_t off[kMaskWords] = {~in.on[0], ~in.on[1], ~in.on[2], ~in.on[3]};
                 const int nks = (in.n + 7) / 8;
+                const float* sg = stage + slot * 8 * GF;
                 for (int ks = 0; ks < nks; ++ks) {
-                    const uint64_t bh = tc::smem_desc(&bpl[0][ks * 256], 512, 128);
-                    const uint64_t bl = tc::smem_desc(&bpl[1][ks * 256], 512, 128);
+                    const uint64_t bh = tc::smem_desc(sg + 2 * ks * GF, kNearGroupBytes, 128);
+                    const uint64_t bl = tc::smem_desc(sg + 2 * ks * GF + 128, kNearGroupBytes, 128);
                     const uint32_t ahi = tmem + S::COL_AHI + ks * 8, alo = tmem + S::COL_ALO + ks * 8;
                     tc::mma_tf32_ts_masked(tmem, ahi, bh, IDESC, off);
                     tc::mma_tf32_ts_masked(tmem, ahi, bl, IDESC, off);
@@ -336,8 +342,8 @@ __global__ void __launch_bounds__(NearTcShape::THREADS, 4) near_tc_kernel(MvmArg
             }
             __syncwarp();
             ptx::named_arrive(kBarMma, kBarThreads);
-            // after releasing the consumers: every consumer has read stage `slot`, refill it ST
-            // chunks ahead (the list lookups for the chunk after it no longer delay the release)
+            // after releasing the consumers: every consumer has read stage `slot` and its MMAs
+            // are complete, refill it ST chunks ahead
             if (__all_sync(0xffffffffu, !s_fail)) {  // warp-uniform: produce() shuffles
                 if (lane == 0) ptx::fence_proxy_async_smem();
                 produce();
@@ -375,34 +381,28 @@ __global__ void __launch_bounds__(NearTcShape::THREADS, 4) near_tc_kernel(MvmArg
                 for (int r = 0; r < 16; ++r) s_acc[h + r][tl] += d[r];
             }
         };
-        bool dirty = false;  // this warp's accumulator rows hold products not yet added to acc
+        bool dirty = false;  // this warp's accumulator rows hold products not yet added to the sums
         for (int c = 0; c < nch; ++c) {
             const int slot = c % ST;
             const bool got = ptx::mbar_wait_bounded(&full[slot], (uint32_t)((c / ST) & 1), a.wait_cycles);
             if (!__all_sync(0xffffffffu, got)) s_fail = 1;
             const int n = info[slot].n;
             const uint32_t mword = s_fail ? 0u : info[slot].on[warp];
-            const float4* sb = &stage[slot][0];
+            const float* sg = stage + slot * 8 * GF + 256;  // coordinates of the stage's first group
             // this row's kernel values against the chunk, before waiting for the MMAs of chunk
             // c-1: the wait then overlaps useful work (registers; rows of targets outside the
-            // mask are computed anyway when their warp is busy, and left out by the MMA)
+            // mask are computed anyway when their warp is busy, and left out by the MMA).
+            // Columns past the chunk's end meet zero weights (zero-padded groups) or are never
+            // read (K-steps past ceil(n/8)).
             uint32_t khi[CH], klo[CH];
             if (mword != 0u) {
-                {   // this warp's SoA copy of the chunk's negated coordinates (zeros past the
-                    // chunk's end: those columns meet zero weights in B)
-                    const float4 r = lane < n ? sb[lane * F4] : make_float4(0.f, 0.f, 0.f, 0.f);
-                    s_src[warp][0][lane] = -r.x;
-                    s_src[warp][1][lane] = -r.y;
-                    s_src[warp][2][lane] = -r.z;
-                    if (D == 4) s_src[warp][3][lane] = -r.w;
-                }
-                __syncwarp();
 #pragma unroll
                 for (int j4 = 0; j4 < CH; j4 += 4) {
                     if (j4 < 16 || n > 16) {  // the MMA reads only ceil(n/8) K-steps
-                        const float4 X = *reinterpret_cast<const float4*>(&s_src[warp][0][j4]);
-                        const float4 Y = *reinterpret_cast<const float4*>(&s_src[warp][1][j4]);
-                        const float4 Z = *reinterpret_cast<const float4*>(&s_src[warp][2][j4]);
+                        const float* g = sg + (j4 / 4) * GF;
+                        const float4 X = *reinterpret_cast<const float4*>(g);
+                        const float4 Y = *reinterpret_cast<const float4*>(g + 4);
+                        const float4 Z = *reinterpret_cast<const float4*>(g + 8);
                         float2 q[2];
 #pragma unroll
                         for (int hh = 0; hh < 2; ++hh) {
@@ -412,7 +412,7 @@ __global__ void __launch_bounds__(NearTcShape::THREADS, 4) near_tc_kernel(MvmArg
                             q[hh] = __ffma2_rn(dx, dx, __ffma2_rn(dy, dy, __fmul2_rn(dz, dz)));
                         }
                         if (D == 4) {
-                            const float4 W = *reinterpret_cast<const float4*>(&s_src[warp][3][j4]);
+                            const float4 W = *reinterpret_cast<const float4*>(g + 12);
                             const float2 dw0 = __fadd2_rn(tx2[3], make_float2(W.x, W.y));
                             const float2 dw1 = __fadd2_rn(tx2[3], make_float2(W.z, W.w));
                             q[0] = __ffma2_rn(dw0, dw0, q[0]);
@@ -436,22 +436,6 @@ __global__ void __launch_bounds__(NearTcShape::THREADS, 4) near_tc_kernel(MvmArg
                 dirty = false;
                 stored = true;
             }
-            if (work) {
-                // B operand: consumer warp w rearranges sources 4w..4w+3 and 16+4w..16+4w+3;
-                // lane = right-hand side.  Element (n, k) sits at float (k/4)*128 + n*4 + k%4.
-#pragma unroll
-                for (int kg = warp; kg < CH / 4; kg += NC) {
-                    uint32_t h[4], l[4];
-#pragma unroll
-                    for (int i = 0; i < 4; ++i) {
-                        const int k = 4 * kg + i;
-                        const float v = k < n ? reinterpret_cast<const float*>(sb + k * F4)[4 + lane] : 0.f;
-                        split_tf32(v, h[i], l[i]);
-                    }
-                    *reinterpret_cast<uint4*>(&bpl[0][kg * 128 + lane * 4]) = make_uint4(h[0], h[1], h[2], h[3]);
-                    *reinterpret_cast<uint4*>(&bpl[1][kg * 128 + lane * 4]) = make_uint4(l[0], l[1], l[2], l[3]);
-                }
-            }
             if (work && mword != 0u) {  // A operand: the row into tensor memory
                 tc::st16(tmem + lane_base + S::COL_AHI, khi);
                 tc::st16(tmem + lane_base + S::COL_ALO, klo);
@@ -463,8 +447,7 @@ __global__ void __launch_bounds__(NearTcShape::THREADS, 4) near_tc_kernel(MvmArg
                 stored = true;
             }
             if (stored) tc::wait_st();
-            // publish: B planes to the async proxy, A rows to the issuer
-            ptx::fence_proxy_async_smem();
+            // publish the A rows to the issuer
             tc::fence_before_sync();
             __syncwarp();
             ptx::named_arrive(kBarReady, kBarThreads);
@@ -485,16 +468,38 @@ __global__ void __launch_bounds__(NearTcShape::THREADS, 4) near_tc_kernel(MvmArg
     if (warp == 0) tc::dealloc(tmem, S::TMEM_COLS);
 }
 
+// Near-field image of one 32-wide pass from its source records (layout: kNearGroupFloats).
+// One CTA per node (non-leaves return); warp w packs the leaf's groups w, w + 8, ...: lane n
+// loads the weights of right-hand side n of the group's 4 sources (coalesced along the record),
+// splits them into TF32 hi / lo and stores 16 bytes of each plane; lanes 0-15 store the negated
+// coordinates.  Positions past the leaf's last source get zero weights and coordinates.
+__global__ void near_image_kernel(int64_t nnodes, const int32_t* __restrict__ nd_leaf,
+                                  const int32_t* __restrict__ nd_begin, const int32_t* __restrict__ nd_end,
+                                  const int32_t* __restrict__ nd_img, const float4* __restrict__ rec, int rec_f4,
+                                  float* __restrict__ img);
+
+// One launch of a near_tc_kernel instantiation with its dynamic shared memory (the attribute is
+// set on the first launch of each instantiation).
+template <void (*K)(MvmArgs, KernelParams)>
+void launch_near_tc_one(unsigned grid, cudaStream_t st, const MvmArgs& a, const KernelParams& kp) {
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(K, cudaFuncAttributeMaxDynamicSharedMemorySize, NearTcShape::SMEM_BYTES);
+        attr = true;
+    }
+    K<<<grid, NearTcShape::THREADS, NearTcShape::SMEM_BYTES, st>>>(a, kp);
+}
+
 template <int D>
 void launch_near_tc_dim(int kind, unsigned grid, cudaStream_t st, const MvmArgs& a, const KernelParams& kp) {
     switch (kind) {
-    case FKT_GAUSSIAN: near_tc_kernel<D, FKT_GAUSSIAN><<<grid, NearTcShape::THREADS, 0, st>>>(a, kp); break;
-    case FKT_EXPONENTIAL: near_tc_kernel<D, FKT_EXPONENTIAL><<<grid, NearTcShape::THREADS, 0, st>>>(a, kp); break;
-    case FKT_MATERN32: near_tc_kernel<D, FKT_MATERN32><<<grid, NearTcShape::THREADS, 0, st>>>(a, kp); break;
-    case FKT_MATERN52: near_tc_kernel<D, FKT_MATERN52><<<grid, NearTcShape::THREADS, 0, st>>>(a, kp); break;
-    case FKT_CAUCHY: near_tc_kernel<D, FKT_CAUCHY><<<grid, NearTcShape::THREADS, 0, st>>>(a, kp); break;
-    case FKT_RATQUAD: near_tc_kernel<D, FKT_RATQUAD><<<grid, NearTcShape::THREADS, 0, st>>>(a, kp); break;
-    default: near_tc_kernel<D, FKT_LAPLACE><<<grid, NearTcShape::THREADS, 0, st>>>(a, kp); break;
+    case FKT_GAUSSIAN: launch_near_tc_one<near_tc_kernel<D, FKT_GAUSSIAN>>(grid, st, a, kp); break;
+    case FKT_EXPONENTIAL: launch_near_tc_one<near_tc_kernel<D, FKT_EXPONENTIAL>>(grid, st, a, kp); break;
+    case FKT_MATERN32: launch_near_tc_one<near_tc_kernel<D, FKT_MATERN32>>(grid, st, a, kp); break;
+    case FKT_MATERN52: launch_near_tc_one<near_tc_kernel<D, FKT_MATERN52>>(grid, st, a, kp); break;
+    case FKT_CAUCHY: launch_near_tc_one<near_tc_kernel<D, FKT_CAUCHY>>(grid, st, a, kp); break;
+    case FKT_RATQUAD: launch_near_tc_one<near_tc_kernel<D, FKT_RATQUAD>>(grid, st, a, kp); break;
+    default: launch_near_tc_one<near_tc_kernel<D, FKT_LAPLACE>>(grid, st, a, kp); break;
     }
 }
 

@@ -64,5 +64,6 @@ extern "C" int fkt_mvm_noalloc(fkt_plan_t plan, const float* w, float* y, int nr
     B.part = (q += f[2]);
     B.image = reinterpret_cast<unsigned char*>(q += f[3]);
     B.yfar = (q += f[4]);
+    B.nimg = (q += f[5]);
     return run_mvm(plan, B, w, y, nrhs, false);
 }
