@@ -31,10 +31,10 @@ struct NearTcShape {
     static constexpr int ST = 4;                      // chunk stages in flight
     static constexpr int CONSUMERS = 4;               // warps that own the 128 TMEM lanes / targets
     static constexpr int THREADS = 32 * (CONSUMERS + 1);  // + one producer / MMA-issuer warp
-    static constexpr int TMEM_COLS = 128;             // accumulator 32 + A hi 32 + A lo 32
-    static constexpr int COL_AHI = 32, COL_ALO = 64;
+    static constexpr int TMEM_COLS = 128;             // accumulator 32 + A hi 32 + A lo 32 + float32 sums 32
+    static constexpr int COL_AHI = 32, COL_ALO = 64, COL_SUM = 96;
     static constexpr int FLUSH = 4;                   // chunks (12 MMAs each) per float32 flush
-    static constexpr int SMEM_BYTES = ST * kNearChunkBytes + NR * CONSUMERS * 32 * 4;  // stages + float32 sums
+    static constexpr int SMEM_BYTES = ST * kNearChunkBytes;  // chunk stages
 };
 
 namespace tc {
@@ -86,6 +86,28 @@ __device__ __forceinline__ void mma_bf16_ts_masked(uint32_t d_tmem, uint32_t a_t
         : "memory");
 }
 
+// 4 consecutive 32-bit columns of this thread's TMEM lane.
+__device__ __forceinline__ void st4(uint32_t taddr, const uint32_t v[4]) {
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x4.b32 [%0], {%1, %2, %3, %4};" ::"r"(taddr), "r"(v[0]), "r"(v[1]),
+                 "r"(v[2]), "r"(v[3])
+                 : "memory");
+}
+// One K-step of the BF16 hi/lo product, D += Ahi Bhi^T + Ahi Blo^T + Alo Bhi^T, in one asm block
+// (operands moved to uniform registers once), rows with a set bit in off[] untouched.
+__device__ __forceinline__ void mma3_bf16_ts_masked(uint32_t d_tmem, uint32_t ahi, uint32_t alo, uint64_t bhi,
+                                                    uint64_t blo, uint32_t idesc, const uint32_t off[4]) {
+    asm volatile(
+        "{\n"
+        ".reg .pred p;\n"
+        "setp.ne.b32 p, 1, 0;\n"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %3, %5, {%6, %7, %8, %9}, p;\n"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %4, %5, {%6, %7, %8, %9}, p;\n"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], [%2], %3, %5, {%6, %7, %8, %9}, p;\n"
+        "}\n" ::"r"(d_tmem),
+        "r"(ahi), "r"(alo), "l"(bhi), "l"(blo), "r"(idesc), "r"(off[0]), "r"(off[1]), "r"(off[2]), "r"(off[3])
+        : "memory");
+}
+
 // 8 consecutive 32-bit columns of this thread's TMEM lane.
 __device__ __forceinline__ void st8(uint32_t taddr, const uint32_t v[8]) {
     asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"r"(taddr), "r"(v[0]),
@@ -102,6 +124,24 @@ __device__ __forceinline__ void st32_zero(uint32_t taddr) {
         : "memory");
 }
 __device__ __forceinline__ void wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
+
+// One K-step of the hi/lo product: D[tmem] += Ahi Bhi^T + Ahi Blo^T + Alo Bhi^T (TF32 operands,
+// A in tensor memory, B in shared memory) in one asm block, so the operands are moved to uniform
+// registers once for the three MMAs; accumulator rows (TMEM lanes) with a set bit in off[0..3]
+// (lane i: bit i % 32 of off[i / 32]) are left untouched.
+__device__ __forceinline__ void mma3_tf32_ts_masked(uint32_t d_tmem, uint32_t ahi, uint32_t alo, uint64_t bhi,
+                                                    uint64_t blo, uint32_t idesc, const uint32_t off[4]) {
+    asm volatile(
+        "{\n"
+        ".reg .pred p;\n"
+        "setp.ne.b32 p, 1, 0;\n"
+        "tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %3, %5, {%6, %7, %8, %9}, p;\n"
+        "tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %4, %5, {%6, %7, %8, %9}, p;\n"
+        "tcgen05.mma.cta_group::1.kind::tf32 [%0], [%2], %3, %5, {%6, %7, %8, %9}, p;\n"
+        "}\n" ::"r"(d_tmem),
+        "r"(ahi), "r"(alo), "l"(bhi), "l"(blo), "r"(idesc), "r"(off[0]), "r"(off[1]), "r"(off[2]), "r"(off[3])
+        : "memory");
+}
 
 // D[tmem] += A[tmem] * B[smem]^T (TF32 operands) leaving the accumulator rows (TMEM lanes) whose
 // bit is set in off[0..3] (lane i: bit i % 32 of off[i / 32]) untouched.
@@ -207,8 +247,7 @@ __global__ void __launch_bounds__(NearTcShape::THREADS, 4) near_tc_kernel(MvmArg
     constexpr uint32_t IDESC = tc::instr_desc(2u, 128u, (uint32_t)NR);
     constexpr uint32_t kBarReady = 1, kBarMma = 2, kBarThreads = S::THREADS;
     extern __shared__ __align__(128) unsigned char near_smem[];
-    float* stage = reinterpret_cast<float*>(near_smem);                              // [ST][8 groups][GF]
-    float(*s_acc)[NC * 32] = reinterpret_cast<float(*)[NC * 32]>(near_smem + ST * kNearChunkBytes);  // [NR][128]
+    float* stage = reinterpret_cast<float*>(near_smem);  // [ST][8 groups][GF]
     __shared__ NearChunkInfo info[ST];
     __shared__ __align__(8) uint64_t full[ST], mma_done;
     __shared__ uint32_t tmem_base;
@@ -316,6 +355,7 @@ __global__ void __launch_bounds__(NearTcShape::THREADS, 4) near_tc_kernel(MvmArg
             settle();
         }
         for (int s = 0; s < ST; ++s) produce();
+        const uint64_t desc0 = tc::smem_desc(stage, kNearGroupBytes, 128);  // B hi of stage 0, K-step 0
         int waited_mma = 0, committed = 0;
         for (int c = 0; c < nch; ++c) {
             const int slot = c % ST;
@@ -325,14 +365,13 @@ __global__ void __launch_bounds__(NearTcShape::THREADS, 4) near_tc_kernel(MvmArg
                 const NearChunkInfo in = info[slot];
                 const uint32_t off[kMaskWords] = {~in.on[0], ~in.on[1], ~in.on[2], ~in.on[3]};
                 const int nks = (in.n + 7) / 8;
-                const float* sg = stage + slot * 8 * GF;
+                // descriptors: the stage base plus byte offsets / 16 in the start-address field
+                // (shared addresses stay below 2^18 bytes, so the 14-bit field cannot carry)
+                const uint64_t d0 = desc0 + (uint64_t)(slot * (kNearChunkBytes >> 4));
                 for (int ks = 0; ks < nks; ++ks) {
-                    const uint64_t bh = tc::smem_desc(sg + 2 * ks * GF, kNearGroupBytes, 128);
-                    const uint64_t bl = tc::smem_desc(sg + 2 * ks * GF + 128, kNearGroupBytes, 128);
-                    const uint32_t ahi = tmem + S::COL_AHI + ks * 8, alo = tmem + S::COL_ALO + ks * 8;
-                    tc::mma_tf32_ts_masked(tmem, ahi, bh, IDESC, off);
-                    tc::mma_tf32_ts_masked(tmem, ahi, bl, IDESC, off);
-                    tc::mma_tf32_ts_masked(tmem, alo, bh, IDESC, off);
+                    const uint64_t bh = d0 + (uint64_t)(ks * (2 * kNearGroupBytes >> 4));
+                    tc::mma3_tf32_ts_masked(tmem, tmem + S::COL_AHI + ks * 8, tmem + S::COL_ALO + ks * 8, bh, bh + 32,
+                                            IDESC, off);
                 }
                 tc::commit(&mma_done);
                 ++committed;
@@ -368,17 +407,18 @@ __global__ void __launch_bounds__(NearTcShape::THREADS, 4) near_tc_kernel(MvmArg
             tx2[3] = make_float2(x.w * kp.sig, x.w * kp.sig);
         }
         tc::st32_zero(tmem + lane_base);  // accumulator rows start at zero; every MMA accumulates
+        tc::st32_zero(tmem + lane_base + S::COL_SUM);
         tc::wait_st();
-#pragma unroll
-        for (int r = 0; r < NR; ++r) s_acc[r][tl] = 0.f;
-        // accumulator row -> the float32 sums in shared memory, 16 columns at a time
+        // accumulator row -> the float32 sums (tensor-memory columns COL_SUM..), 8 columns at a time
         auto flush = [&]() {
 #pragma unroll
-            for (int h = 0; h < NR; h += 16) {
-                float d[16];
-                tc::ld16(tmem + lane_base + h, d);
+            for (int h = 0; h < NR; h += 4) {
+                float d[4], sum[4];
+                tc::ld4x2(tmem + lane_base + h, tmem + lane_base + S::COL_SUM + h, d, sum);
+                uint32_t u[4];
 #pragma unroll
-                for (int r = 0; r < 16; ++r) s_acc[h + r][tl] += d[r];
+                for (int r = 0; r < 4; ++r) u[r] = __float_as_uint(sum[r] + d[r]);
+                tc::st4(tmem + lane_base + S::COL_SUM + h, u);
             }
         };
         bool dirty = false;  // this warp's accumulator rows hold products not yet added to the sums
@@ -455,12 +495,21 @@ __global__ void __launch_bounds__(NearTcShape::THREADS, 4) near_tc_kernel(MvmArg
         if (nch >= 1) ptx::named_sync(kBarMma, kBarThreads);  // the MMAs of the last chunk are done
         tc::fence_after_sync();
         const bool ok = !s_fail;
-        if (ok && dirty) flush();
-        __syncwarp();
-        if (ok && valid)
+        if (ok && dirty) {
+            flush();
+            tc::wait_st();
+        }
+        if (ok) {
 #pragma unroll
-            for (int r = 0; r < NR; ++r)
-                if (r < a.nr) acc_store(a, r, t, s_acc[r][tl] * kp.scale);
+            for (int h = 0; h < NR; h += 16) {
+                float sum[16];
+                tc::ld16(tmem + lane_base + S::COL_SUM + h, sum);
+                if (valid)
+#pragma unroll
+                    for (int r = 0; r < 16; ++r)
+                        if (h + r < a.nr) acc_store(a, h + r, t, sum[r] * kp.scale);
+            }
+        }
         if (!ok && tl == 0) atomicExch(a.err, 1);
     }
     tc::fence_before_sync();
