@@ -191,6 +191,8 @@ __global__ void __launch_bounds__(160, HOLD > 0 ? 3
         };
         if (ne > 0) load_window();
         while (issued < ST && issued < ne) produce();
+        const uint64_t desc0 = tc::smem_desc(Bbuf, 128, S::SBO_A);  // B hi of stage 0, K-step 0
+        static_assert(BB % 16 == 0 && BPLANE % 16 == 0, "descriptor offsets in 16-byte units");
         int committed = 0, waited = 0;
         for (int i = 0; i < ne; ++i) {
             ptx::named_sync(kBarReady, kBarThreads);  // the rows of entry i are in tensor memory
@@ -200,17 +202,18 @@ __global__ void __launch_bounds__(160, HOLD > 0 ? 3
                 uint32_t off[kMaskWords];
 #pragma unroll
                 for (int w = 0; w < kMaskWords; ++w) off[w] = ~info[slot].on[w];
-                const unsigned char* B = Bbuf + slot * BB;
+                // descriptors: stage 0's base plus byte offsets / 16 in the start-address field
+                // (shared addresses stay below 2^18 bytes, so the 14-bit field cannot carry)
+                const uint64_t d0 = desc0 + (uint64_t)(slot * (BB >> 4));
 #pragma unroll 1
                 for (int ks = 0; ks < NTP / 16; ++ks) {
-                    const uint64_t bh = tc::smem_desc(B + ks * 256, 128, S::SBO_A);
+                    const uint64_t bh = d0 + (uint64_t)(ks * 16);
                     const uint32_t ahi = tmem + Sh::COL_AHI + ks * 8;
-                    tc::mma_bf16_ts_masked(tmem, ahi, bh, IDESC, off);
-                    if (PREC == TC_BF16X3) {
-                        const uint64_t bl = tc::smem_desc(B + BPLANE + ks * 256, 128, S::SBO_A);
-                        tc::mma_bf16_ts_masked(tmem, ahi, bl, IDESC, off);
-                        tc::mma_bf16_ts_masked(tmem, tmem + Sh::COL_ALO + ks * 8, bh, IDESC, off);
-                    }
+                    if (PREC == TC_BF16X3)
+                        tc::mma3_bf16_ts_masked(tmem, ahi, tmem + Sh::COL_ALO + ks * 8, bh, bh + (uint64_t)(BPLANE >> 4),
+                                                IDESC, off);
+                    else
+                        tc::mma_bf16_ts_masked(tmem, ahi, bh, IDESC, off);
                 }
                 tc::commit(&mma_done);
                 ++committed;
