@@ -436,8 +436,9 @@ int fkt_mvm_shard_end(fkt_plan_t plan, const float* mult, float* y, int nrhs);
  *     every GPU that loads libfkt.so holds it until the process exits.  A call with one
  *     right-hand side needs 4 * (6 N + nterms * (nodes + s2m chunks)) bytes, about 35 MB at
  *     N = 1M, d = 3, p = 6, leaf 256 (each part rounded up to 256 bytes); more right-hand
- *     sides need proportionally more.  Requests that do not fit return FKT_ERR_SCRATCH_LIMIT and
- *     enqueue nothing.
+ *     sides need proportionally more, and passes of 17-32 right-hand sides on the TF32 near
+ *     kernel also need the pass's near-field image, about 272 bytes per point.  Requests that
+ *     do not fit return FKT_ERR_SCRATCH_LIMIT and enqueue nothing.
  *   - The first call on a device looks up the array's device address (cudaGetSymbolAddress)
  *     with that device current; make that first call before any stream capture.
  *   - All calls share the one array and it keeps the last call's contents.  Nothing in it
