@@ -33,17 +33,23 @@ def _rel(a, b):
     return max(np.linalg.norm(a[i] - b[i]) / np.linalg.norm(b[i]) for i in range(len(b)))
 
 
-@pytest.mark.parametrize("far_precision,nrhs", [("fp32", 1), ("fp32", 11), ("bf16x3", 11), ("bf16x3", 3)])
-def test_noalloc_matches_fkt_mvm_on_two_calls(fkt, far_precision, nrhs):
+@pytest.mark.parametrize("far_precision,nrhs,near_precision", [("fp32", 1, "fp32"), ("fp32", 11, "fp32"),
+                                                                ("bf16x3", 11, "fp32"), ("bf16x3", 3, "fp32"),
+                                                                ("bf16x3", 20, "tf32x3"), ("fp32", 32, "tf32x3")])
+def test_noalloc_matches_fkt_mvm_on_two_calls(fkt, far_precision, nrhs, near_precision):
     """Both far-field paths: float32 on the CUDA cores, and the tensor-core path whose packed
-    multipole image is also carved out of the scratch; nrhs 3 and 11 leave partial groups of 8."""
+    multipole image is also carved out of the scratch; nrhs 3 and 11 leave partial groups of 8.
+    With 20 or 32 right-hand sides on the TF32 near kernel the pass's near-field image is carved
+    out of the scratch too (at N = 20k, where everything fits the 48 MiB)."""
     import torch
 
-    X = torch.from_numpy(inputs.gaussian_mixture(60000, 3, 10, 0.05, seed=21)).cuda()
+    n = 60000 if near_precision == "fp32" else 20000
+    X = torch.from_numpy(inputs.gaussian_mixture(n, 3, 10, 0.05, seed=21)).cuda()
     plan = fkt.Plan(X, "matern32", lengthscale=0.2, p=6, leaf_size=256, theta=0.5)
     plan.set_option("far_precision", far_precision)
+    plan.set_option("near_precision", near_precision)
     for call, seed in enumerate((22, 23)):          # two calls in a row share the scratch
-        w = torch.from_numpy(inputs.normal_weights(60000, nrhs, seed=seed)).cuda()
+        w = torch.from_numpy(inputs.normal_weights(n, nrhs, seed=seed)).cuda()
         want = plan.mvm(w).cpu().numpy()             # the existing entry point
         got = torch.full_like(w, float("nan"))
         fkt.fkt_mvm_noalloc(plan.h, w, got, nrhs)
