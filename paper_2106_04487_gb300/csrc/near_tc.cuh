@@ -143,6 +143,53 @@ __device__ __forceinline__ void mma3_tf32_ts_masked(uint32_t d_tmem, uint32_t ah
         : "memory");
 }
 
+// Every K-step of one near chunk (nks = 1..4 steps of 8 sources) in one asm block: for K-step k
+// the hi/lo product D += Ahi_k Bhi_k^T + Ahi_k Blo_k^T + Alo_k Bhi_k^T, with A column offsets 8k
+// and B descriptors bh + 136 k (hi) and bh + 136 k + 32 (lo) in 16-byte units (the near-field
+// image's 2176-byte K-steps, lo plane 512 bytes after hi).  The operands enter once for all
+// twelve MMAs; rows with a set bit in off[] are left untouched.
+__device__ __forceinline__ void near_chunk_mma(uint32_t d_tmem, uint32_t ahi, uint32_t alo, uint64_t bh, int nks,
+                                               uint32_t idesc, const uint32_t off[4]) {
+    asm volatile(
+        "{\n"
+        ".reg .pred p, q1, q2, q3;\n"
+        ".reg .b64 h0, l0, h1, l1, h2, l2, h3, l3;\n"
+        ".reg .b32 ah1, al1, ah2, al2, ah3, al3;\n"
+        "setp.ne.b32 p, 1, 0;\n"
+        "setp.gt.s32 q1, %4, 1;\n"
+        "setp.gt.s32 q2, %4, 2;\n"
+        "setp.gt.s32 q3, %4, 3;\n"
+        "mov.b64 h0, %3;\n"
+        "add.s64 l0, %3, 32;\n"
+        "add.s64 h1, %3, 136;\n"
+        "add.s64 l1, %3, 168;\n"
+        "add.s64 h2, %3, 272;\n"
+        "add.s64 l2, %3, 304;\n"
+        "add.s64 h3, %3, 408;\n"
+        "add.s64 l3, %3, 440;\n"
+        "add.u32 ah1, %1, 8;\n"
+        "add.u32 al1, %2, 8;\n"
+        "add.u32 ah2, %1, 16;\n"
+        "add.u32 al2, %2, 16;\n"
+        "add.u32 ah3, %1, 24;\n"
+        "add.u32 al3, %2, 24;\n"
+        "tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], h0, %5, {%6, %7, %8, %9}, p;\n"
+        "tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], l0, %5, {%6, %7, %8, %9}, p;\n"
+        "tcgen05.mma.cta_group::1.kind::tf32 [%0], [%2], h0, %5, {%6, %7, %8, %9}, p;\n"
+        "@q1 tcgen05.mma.cta_group::1.kind::tf32 [%0], [ah1], h1, %5, {%6, %7, %8, %9}, p;\n"
+        "@q1 tcgen05.mma.cta_group::1.kind::tf32 [%0], [ah1], l1, %5, {%6, %7, %8, %9}, p;\n"
+        "@q1 tcgen05.mma.cta_group::1.kind::tf32 [%0], [al1], h1, %5, {%6, %7, %8, %9}, p;\n"
+        "@q2 tcgen05.mma.cta_group::1.kind::tf32 [%0], [ah2], h2, %5, {%6, %7, %8, %9}, p;\n"
+        "@q2 tcgen05.mma.cta_group::1.kind::tf32 [%0], [ah2], l2, %5, {%6, %7, %8, %9}, p;\n"
+        "@q2 tcgen05.mma.cta_group::1.kind::tf32 [%0], [al2], h2, %5, {%6, %7, %8, %9}, p;\n"
+        "@q3 tcgen05.mma.cta_group::1.kind::tf32 [%0], [ah3], h3, %5, {%6, %7, %8, %9}, p;\n"
+        "@q3 tcgen05.mma.cta_group::1.kind::tf32 [%0], [ah3], l3, %5, {%6, %7, %8, %9}, p;\n"
+        "@q3 tcgen05.mma.cta_group::1.kind::tf32 [%0], [al3], h3, %5, {%6, %7, %8, %9}, p;\n"
+        "}\n" ::"r"(d_tmem),
+        "r"(ahi), "r"(alo), "l"(bh), "r"(nks), "r"(idesc), "r"(off[0]), "r"(off[1]), "r"(off[2]), "r"(off[3])
+        : "memory");
+}
+
 // D[tmem] += A[tmem] * B[smem]^T (TF32 operands) leaving the accumulator rows (TMEM lanes) whose
 // bit is set in off[0..3] (lane i: bit i % 32 of off[i / 32]) untouched.
 __device__ __forceinline__ void mma_tf32_ts_masked(uint32_t d_tmem, uint32_t a_tmem, uint64_t b, uint32_t idesc,
@@ -368,11 +415,8 @@ __global__ void __launch_bounds__(NearTcShape::THREADS, 4) near_tc_kernel(MvmArg
                 // descriptors: the stage base plus byte offsets / 16 in the start-address field
                 // (shared addresses stay below 2^18 bytes, so the 14-bit field cannot carry)
                 const uint64_t d0 = desc0 + (uint64_t)(slot * (kNearChunkBytes >> 4));
-                for (int ks = 0; ks < nks; ++ks) {
-                    const uint64_t bh = d0 + (uint64_t)(ks * (2 * kNearGroupBytes >> 4));
-                    tc::mma3_tf32_ts_masked(tmem, tmem + S::COL_AHI + ks * 8, tmem + S::COL_ALO + ks * 8, bh, bh + 32,
-                                            IDESC, off);
-                }
+                static_assert(2 * kNearGroupBytes / 16 == 136 && 128 * 4 / 16 == 32, "near_chunk_mma offsets");
+                tc::near_chunk_mma(tmem, tmem + S::COL_AHI, tmem + S::COL_ALO, d0, nks, IDESC, off);
                 tc::commit(&mma_done);
                 ++committed;
                 if (ptx::mbar_wait_bounded(&mma_done, (uint32_t)((committed - 1) & 1), kWaitCycles)) waited_mma = committed;
