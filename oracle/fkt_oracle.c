@@ -20,7 +20,8 @@
  * Ytilde_k(u) = L_k^{-1} [C_k^alpha(u . v_i)]_i with G_k = [C_k^alpha(v_i . v_j)] = L_k L_k^T
  * for D_k = |H_k| given unit vectors v_i; it satisfies
  * sum_h Ytilde_kh(u) Ytilde_kh(v) = C_k^alpha(u . v), so Tbar is used without
- * the normalisation Z_k (which the paper never gives).
+ * the normalisation Z_k (which the paper never gives).  In d = 2 (alpha = 0) the zonal
+ * function of degree k is the Chebyshev T_k and the table is built for it.
  *
  * Tree contract (midpoint splits cycling the axes, Sec. 3.1 rules (a), (b)): bounding cube lo = min x, L = max extent;
  * q_a = min(floor((x_a - lo_a) * (2^B / L)), 2^B - 1) with B = floor(63/d);
@@ -157,9 +158,16 @@ static void kernel_derivs(const okernel* k, double r, int n, double* out) {
     }
 }
 
-/* Gegenbauer C_0..C_n at x (Sec. A.1 recurrence). */
+/* Zonal functions of degree 0..n at x: Gegenbauer C_n^alpha (Sec. A.1 recurrence); for
+ * alpha = 0 (d = 2), where C_n^0 vanishes for n >= 1, the Chebyshev T_n, the limit of
+ * C_n^alpha / alpha up to the factor 2/n that the d = 2 coefficient tables absorb. */
 static void gegenbauer(double alpha, int n, double x, double* C) {
     C[0] = 1.0;
+    if (alpha == 0.0) {
+        if (n >= 1) C[1] = x;
+        for (int m = 2; m <= n; ++m) C[m] = 2.0 * x * C[m - 1] - C[m - 2];
+        return;
+    }
     if (n >= 1) C[1] = 2.0 * alpha * x;
     for (int m = 2; m <= n; ++m)
         C[m] = (2.0 * x * (m + alpha - 1.0) * C[m - 1] - (m + 2.0 * alpha - 2.0) * C[m - 2]) / m;
@@ -193,7 +201,7 @@ static double Tb(const obasis* b, int k, int j, int m) {
 
 /* Build the zonal-Gram basis; returns NULL if a Gram matrix is not positive definite. */
 void* orc_basis_new(int d, int p, const double* Tbar, const int* Dk, const double* zonal_pts) {
-    if (d < 3 || d > ORC_MAXD || p < 0 || p > ORC_MAXP) return NULL;
+    if (d < 2 || d > ORC_MAXD || p < 0 || p > ORC_MAXP) return NULL;
     obasis* b = (obasis*)calloc(1, sizeof(obasis));
     b->d = d;
     b->p = p;
@@ -522,7 +530,7 @@ static void build_tree(ofkt* f) {
 
 void* orc_fkt_new(const float* X, int64_t N, int d, const double* kp, int p, int leaf_size,
                   double theta, void* basis) {
-    if (N < 1 || d < 3 || d > ORC_MAXD || leaf_size < 1 || !(theta > 0.0 && theta < 1.0) || !basis) return NULL;
+    if (N < 1 || d < 2 || d > ORC_MAXD || leaf_size < 1 || !(theta > 0.0 && theta < 1.0) || !basis) return NULL;
     ofkt* f = (ofkt*)calloc(1, sizeof(ofkt));
     f->d = d;
     f->p = p;

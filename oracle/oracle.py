@@ -106,11 +106,11 @@ def zonal_points(d: int, p: int, seed: int = 12345):
     """Unit vectors v_{k,i} for the zonal harmonic basis of each degree k <= p.
 
     For degree k, D_k = |H_k| points are picked greedily (pivoted Cholesky of the
-    Gram matrix C_k^alpha(v_i . v_j)) from a seeded random pool so the Gram
+    Gram matrix C_k^alpha(v_i . v_j), T_k(v_i . v_j) for d = 2) from a seeded random pool so the Gram
     matrix is well conditioned.  Any points in general position give a valid
     basis (Sec. A.1 addition theorem); the choice only affects rounding.
     """
-    from scipy.special import eval_gegenbauer
+    from scipy.special import eval_chebyt, eval_gegenbauer
 
     rng = np.random.default_rng(seed)
     a = d / 2.0 - 1.0
@@ -120,7 +120,8 @@ def zonal_points(d: int, p: int, seed: int = 12345):
         npool = 4 * Dk[k] + 16
         pool = rng.normal(size=(npool, d))
         pool /= np.linalg.norm(pool, axis=1, keepdims=True)
-        G = eval_gegenbauer(k, a, np.clip(pool @ pool.T, -1.0, 1.0))
+        cosg = np.clip(pool @ pool.T, -1.0, 1.0)
+        G = eval_chebyt(k, cosg) if d == 2 else eval_gegenbauer(k, a, cosg)  # zonal function of degree k
         diag = G.diagonal().copy()
         chosen = []
         Lrows = np.zeros((Dk[k], npool))

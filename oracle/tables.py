@@ -19,6 +19,11 @@ derivation of the paper (Sec. A.2, "Derivation of the FKT expansion"):
   at m = 1), so the kernel value itself (n = 0 term of eq. taylor) is kept.
 * The printed A_{k,i} denominator "(i-k)/2" is read as ((i-k)/2)!, which makes
   eq. coschange hold for d = 3 and 4.
+* d = 2 (alpha = 0): C_k^0 vanishes for k >= 1, so the zonal functions are the limits
+  C_k^alpha / alpha -> (2/k) T_k (Chebyshev) for k >= 1 and C_0 = T_0 = 1; the expansion is
+  taken in T_k directly: cos^i = sum_k A_{k,i} T_k with A_{k,i} the alpha -> 0 limit of
+  alpha (2/k) A_{k,i}(alpha) (k >= 1) and of A_{0,i}(alpha) (k = 0), and the 2-D addition
+  theorem T_k(cos(phi - phi')) = cos k phi cos k phi' + sin k phi sin k phi'.
 """
 from __future__ import annotations
 
@@ -51,12 +56,18 @@ def double_factorial(n: int) -> int:
 
 @lru_cache(maxsize=None)
 def A(k: int, i: int, d: int) -> Fraction:
-    """cos^i(g) = sum_k A_{k,i} C_k^alpha(cos g)  (eq. coschange).
+    """cos^i(g) = sum_k A_{k,i} C_k^alpha(cos g)  (eq. coschange); for d = 2 the zonal
+    functions are T_k and A_{k,i} is the alpha -> 0 limit stated in the module docstring:
+    2^(1-i) binom(i, (i-k)/2) for k >= 1 and 2^(-i) binom(i, i/2) for k = 0.
 
     Zero unless 0 <= k <= i and k == i (mod 2).
     """
     if k < 0 or k > i or (i - k) % 2:
         return Fraction(0)
+    if d == 2:
+        # limit of alpha (2/k) i! (alpha+k) / (2^i ((i-k)/2)! (alpha)_((i+k)/2+1)), with
+        # (alpha)_n ~ alpha (n-1)! as alpha -> 0
+        return Fraction(factorial(i), 2 ** i * factorial((i - k) // 2) * factorial((i + k) // 2)) * (2 if k else 1)
     a = alpha_of(d)
     num = factorial(i) * (a + k)
     den = Fraction(2) ** i * factorial((i - k) // 2) * rising(a, (i + k) // 2 + 1)
@@ -96,7 +107,7 @@ def Tbar(k: int, j: int, m: int, d: int) -> Fraction:
 
 
 def harmonic_dim(k: int, d: int) -> int:
-    """|H_k| = binom(k+d-1, k) - binom(k+d-3, k-2) (Sec. A.3)."""
+    """|H_k| = binom(k+d-1, k) - binom(k+d-3, k-2) (Sec. A.3); d = 2: 1, 2, 2, ..."""
     return comb(k + d - 1, k) - (comb(k + d - 3, k - 2) if k >= 2 else 0)
 
 
