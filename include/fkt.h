@@ -106,9 +106,13 @@ typedef struct {
 /* Build a plan (Sec. 3.1 tree, far/near sets of Sec. 3.1-3.2, expansion tables of Theorem 3.1).
  *   points     device [N][d] float32, finite
  *   N          1 <= N < 2^31
- *   d          3 or 4
+ *   d          2, 3 or 4.  d = 2 takes the circular harmonics cos k phi, sin k phi with the
+ *              Chebyshev T_k as zonal functions (the alpha = 0 limit of the Gegenbauer form
+ *              of Sec. A.1); its far field runs on the CUDA cores only (far_precision other
+ *              than "fp32" makes fkt_mvm return FKT_ERR_UNSUPPORTED), and the batch entry
+ *              points take d = 3 and 4 only.
  *   kernel     see fkt_kernel; lengthscale > 0 (alpha > 0 for FKT_RATQUAD)
- *   p          truncation order, 0 <= p <= 10 for d = 3, 0 <= p <= 8 for d = 4
+ *   p          truncation order, 0 <= p <= 10 for d = 2 and 3, 0 <= p <= 8 for d = 4
  *   leaf_size  largest number of points in a leaf that may still split, 1 <= leaf_size <= 4096
  *   theta      far-field parameter of eq. accparam, 0 < theta < 1
  *   cuda_stream  cudaStream_t to enqueue on, or NULL for the default stream

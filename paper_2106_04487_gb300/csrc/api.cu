@@ -96,8 +96,8 @@ const char* fkt_error_string(int status) {
 int fkt_plan(const float* points, int64_t N, int d, fkt_kernel kernel, int p, int leaf_size, double theta,
              void* cuda_stream, fkt_plan_t* out) {
     if (out) *out = nullptr;
-    if (!out || !points || N < 1 || N > 0x7fffffffLL || (d != 3 && d != 4) || !valid_kernel(kernel)) return FKT_ERR_INVALID_ARG;
-    if (p < 0 || p > (d == 3 ? fkt::kMaxP3 : fkt::kMaxP4)) return FKT_ERR_INVALID_ARG;
+    if (!out || !points || N < 1 || N > 0x7fffffffLL || d < 2 || d > 4 || !valid_kernel(kernel)) return FKT_ERR_INVALID_ARG;
+    if (p < 0 || p > (d <= 3 ? fkt::kMaxP3 : fkt::kMaxP4)) return FKT_ERR_INVALID_ARG;
     if (leaf_size < 1 || leaf_size > 4096 || !(theta > 0.0 && theta < 1.0)) return FKT_ERR_INVALID_ARG;
     if (!is_device_pointer(points)) return FKT_ERR_INVALID_ARG;
     auto t0 = std::chrono::steady_clock::now();

@@ -17,7 +17,7 @@
 namespace fkt {
 
 // ----------------------------------------------------------------- layout
-// Layout code D of the expansion: 3 or 4 = every radial term j = k, k+2, ..., <= P of each
+// Layout code D of the expansion: 2, 3 or 4 = every radial term j = k, k+2, ..., <= P of each
 // degree k in that dimension; kDiag3 = d = 3 with the j = k term only.  The latter is the radial
 // compression of the Laplace kernel 1/r in d = 3: its degree-k radial part has rank 1 (Table 3),
 // being r'^k / r^(k+1) alone (the Legendre multipole expansion of Sec. 3.3, eq. electro), so the
@@ -29,7 +29,9 @@ __host__ __device__ constexpr bool diag_of(int D) { return D >= 100; }
 template <int D, int P>
 struct Layout {
     static constexpr int nj(int k) { return diag_of(D) ? 1 : (P - k) / 2 + 1; }
-    static constexpr int dk(int k) { return dim_of(D) == 3 ? 2 * k + 1 : (k + 1) * (k + 1); }
+    static constexpr int dk(int k) {
+        return dim_of(D) == 2 ? (k == 0 ? 1 : 2) : dim_of(D) == 3 ? 2 * k + 1 : (k + 1) * (k + 1);
+    }
     // row of the expansion tables (built for the full layout) of radial pair (k, j = k + 2 jj)
     static constexpr int tpair(int k, int jj) {
         int o = 0;
@@ -164,6 +166,8 @@ __device__ __forceinline__ void kernel_jets(const KernelParams& kp, float r, flo
 // ---------------------------------------------------- solid harmonics
 // Calls f(k, h, value) for every normalised solid harmonic St_kh(x) of degree k <= P,
 // in an l-major order.  r2_3 = x0^2 + x1^2 + x2^2, r2 = |x|^2 (r2 = r2_3 when D = 3).
+// D = 2: the circular harmonics Re, Im of (x0 + i x1)^k (1 at k = 0), whose products add up to
+// T_k of the angle between two unit vectors (the 2-D addition theorem).
 // The recurrences are those of Legendre-type polynomials in homogeneous form (no
 // square roots), so the same routine serves s2m (arbitrary x') and m2t (unit x).
 template <int D, int P, class F>
@@ -176,6 +180,15 @@ __device__ __forceinline__ void solid_harmonics(float x0, float x1, float x2, fl
     for (int m = 1; m <= P; ++m) {
         C[m] = x0 * C[m - 1] - x1 * S[m - 1];
         S[m] = x0 * S[m - 1] + x1 * C[m - 1];
+    }
+    if constexpr (dim_of(D) == 2) {
+        f(0, 0, 1.f);
+#pragma unroll
+        for (int k = 1; k <= P; ++k) {
+            f(k, 0, C[k]);
+            f(k, 1, S[k]);
+        }
+        return;
     }
     float pm2[P + 1], pm1[P + 1], cur[P + 1];
 #pragma unroll
@@ -276,8 +289,9 @@ struct Rec {
     static constexpr int WOFF = (D == 3 && NR == 1) ? 3 : 4;                // float index of weight 0
 };
 
-inline int rec_f4(int d, int nrb) { return (d == 3 && nrb == 1) ? 1 : (4 + nrb + 3) / 4; }
-inline int rec_woff(int d, int nrb) { return (d == 3 && nrb == 1) ? 3 : 4; }
+// (d = 2 uses the d = 3 records: its third coordinate is zero)
+inline int rec_f4(int d, int nrb) { return (d <= 3 && nrb == 1) ? 1 : (4 + nrb + 3) / 4; }
+inline int rec_woff(int d, int nrb) { return (d <= 3 && nrb == 1) ? 3 : 4; }
 
 __device__ __forceinline__ bool entry_active(int mask, const uint32_t* __restrict__ masks, int t) {
     return mask < 0 || ((__ldg(&masks[(int64_t)mask * kMaskWords + (t >> 5)]) >> (t & 31)) & 1u);

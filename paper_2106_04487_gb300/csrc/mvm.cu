@@ -26,6 +26,8 @@ FKT_DECL_RANGE(4, 0, 4)
 FKT_DECL_RANGE(4, 5, 6)
 FKT_DECL_RANGE(4, 7, 8)
 #undef FKT_DECL_RANGE
+int launch_s2m_d2_p0_10(int p, int nrb, const FarLaunch& L);
+int launch_far_d2_p0_10(int p, int nrb, const FarLaunch& L);
 int launch_s2m_diag_p0_5(int p, int nrb, const FarLaunch& L);
 int launch_far_diag_p0_5(int p, int nrb, const FarLaunch& L);
 int launch_s2m_diag_p6_10(int p, int nrb, const FarLaunch& L);
@@ -47,8 +49,10 @@ int launch_tc_d3_p7_10(int p, int prec, bool far, const TcLaunch& L);
 int launch_tc_d4_p0_5(int p, int prec, bool far, const TcLaunch& L);
 int launch_tc_d4_p6_8(int p, int prec, bool far, const TcLaunch& L);
 
-// d: the layout code (3, 4, or kDiag3 for the compressed d = 3 layout).
+// d: the layout code (2, 3, 4, or kDiag3 for the compressed d = 3 layout).  The tensor-core
+// far field is built for d = 3 and 4.
 static int launch_tc_any(int d, int p, int prec, bool far, const TcLaunch& L) {
+    if (d == 2) return FKT_ERR_UNSUPPORTED;
     if (d == kDiag3) return p <= 6 ? launch_tc_diag_p0_6(p, prec, far, L) : launch_tc_diag_p7_10(p, prec, far, L);
     if (d == 3) return p <= 6 ? launch_tc_d3_p0_6(p, prec, far, L) : launch_tc_d3_p7_10(p, prec, far, L);
     return p <= 5 ? launch_tc_d4_p0_5(p, prec, far, L) : launch_tc_d4_p6_8(p, prec, far, L);
@@ -63,6 +67,7 @@ static int tc_prec_of(int far_precision) {
 }
 
 static int launch_s2m_any(int d, int p, int nrb, const FarLaunch& L) {
+    if (d == 2) return launch_s2m_d2_p0_10(p, nrb, L);
     if (d == kDiag3) return p <= 5 ? launch_s2m_diag_p0_5(p, nrb, L) : launch_s2m_diag_p6_10(p, nrb, L);
     if (d == 3) {
         if (p <= 4) return launch_s2m_d3_p0_4(p, nrb, L);
@@ -76,6 +81,7 @@ static int launch_s2m_any(int d, int p, int nrb, const FarLaunch& L) {
 }
 
 static int launch_far_any(int d, int p, int nrb, const FarLaunch& L) {
+    if (d == 2) return launch_far_d2_p0_10(p, nrb, L);
     if (d == kDiag3) return p <= 5 ? launch_far_diag_p0_5(p, nrb, L) : launch_far_diag_p6_10(p, nrb, L);
     if (d == 3) {
         if (p <= 4) return launch_far_d3_p0_4(p, nrb, L);
@@ -95,8 +101,10 @@ namespace {
 // operands, tc = 2 FP16 hi/lo operands with double buffering (wmax: 32 words of device scratch for
 // the weights' per-right-hand-side scale), which the 1/r kernel leaves for TF32 (its values are
 // unbounded).
+// d = 2 runs the d = 3 near kernels: its points carry zero third and fourth coordinates.
 void launch_near(int d, int nw, int tpt, int tc, int kind, unsigned grid, cudaStream_t st, const MvmArgs& a,
                  const KernelParams& kp, unsigned* wmax) {
+    if (d == 2) d = 3;
     if (tc && nw == 32) {
         if (tc == 2 && kind != FKT_LAPLACE && wmax) {
             if (d == 3) launch_near_tc2_d3(kind, grid, st, a, kp, wmax);
@@ -125,7 +133,7 @@ void launch_permute_dim(int nw, unsigned grid, cudaStream_t st, int64_t N, const
 
 void launch_permute(int d, int nw, unsigned grid, cudaStream_t st, int64_t N, const int32_t* perm, const float4* xs,
                     const float* w, int nr, float sig, const float* pt_sig, float4* rec) {
-    if (d == 3) launch_permute_dim<3>(nw, grid, st, N, perm, xs, w, nr, sig, pt_sig, rec);
+    if (d <= 3) launch_permute_dim<3>(nw, grid, st, N, perm, xs, w, nr, sig, pt_sig, rec);
     else launch_permute_dim<4>(nw, grid, st, N, perm, xs, w, nr, sig, pt_sig, rec);
 }
 

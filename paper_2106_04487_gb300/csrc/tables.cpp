@@ -12,8 +12,13 @@
 // C_k(cos g) (r'/r)^j J_m gives
 //   That_{k,j,m} = sum_n [e^n] s^m * binom(n, 2n-j) (-2)^(2n-j) A_{k,2n-j}  (= m! Tbar_{k,j,m}).
 //
+// In d = 2 (alpha = 0, where C_k^alpha vanishes for k >= 1) the zonal functions are the
+// Chebyshev T_k instead (the limit C_k^alpha / alpha -> (2/k) T_k, the 2/k folded into the
+// change of basis), found the same way from the monomial coefficients of T_k.
+//
 // The harmonic bases are real solid harmonics normalised so that
-// sum_h Y_kh(u) Y_kh(v) = C_k^alpha(u.v) for unit u, v (addition theorem, Sec. A.1):
+// sum_h Y_kh(u) Y_kh(v) = C_k^alpha(u.v) (T_k(u.v) in d = 2) for unit u, v (addition theorem, Sec. A.1):
+//   d = 2: Re and Im of (x + i y)^k (one function, 1, at k = 0);
 //   d = 3: Pi_l^m(z, r^2) (x + i y)^m with Pi_l^m = N_lm r^(l-m) P_l^(m)(z/r),
 //          N_lm = sqrt((2 - [m=0]) (l-m)! / (l+m)!)   (Schmidt semi-normalised);
 //   d = 4: nu_kl Q_(k-l)^(l+1)(x4, r^2) S^(3)_lm(x1, x2, x3) with the Gegenbauer
@@ -64,13 +69,18 @@ std::vector<std::vector<ld>> sqrt_shift_powers(int P) {
     return pw;  // pw[m][n]
 }
 
-// A[k][i]: x^i = sum_k A[k][i] C_k^alpha(x), by inverting the Gegenbauer coefficient matrix.
-std::vector<std::vector<ld>> cos_power_to_gegenbauer(int P, ld alpha) {
+// A[k][i]: x^i = sum_k A[k][i] C_k^alpha(x), by inverting the Gegenbauer coefficient matrix;
+// with chebyshev set, x^i = sum_k A[k][i] T_k(x) from the Chebyshev coefficient matrix.
+std::vector<std::vector<ld>> cos_power_to_gegenbauer(int P, ld alpha, bool chebyshev = false) {
     std::vector<std::vector<ld>> g(P + 1, std::vector<ld>(P + 1, 0));  // g[k][t]: C_k = sum_t g[k][t] x^t
     g[0][0] = 1;
-    if (P >= 1) g[1][1] = 2 * alpha;
+    if (P >= 1) g[1][1] = chebyshev ? 1 : 2 * alpha;
     for (int k = 2; k <= P; ++k)
         for (int t = 0; t <= k; ++t) {
+            if (chebyshev) {  // T_k = 2 x T_{k-1} - T_{k-2}
+                g[k][t] = -g[k - 2][t] + (t >= 1 ? 2 * g[k - 1][t - 1] : 0);
+                continue;
+            }
             ld v = -(k + 2 * alpha - 2) * g[k - 2][t];
             if (t >= 1) v += 2 * (k + alpha - 1) * g[k - 1][t - 1];
             g[k][t] = v / k;
@@ -94,6 +104,18 @@ ld gegenbauer_norm2(int n, ld lam) {
 // Host mirror of the device harmonics, used only for the self-check below.
 void host_harmonics(int d, int p, const FarTables& T, const double* x, std::vector<double>* out) {
     out->clear();
+    if (d == 2) {
+        double c = 1, s = 0;  // (x + i y)^k
+        out->push_back(1.0);
+        for (int k = 1; k <= p; ++k) {
+            const double cn = x[0] * c - x[1] * s, sn = x[0] * s + x[1] * c;
+            c = cn;
+            s = sn;
+            out->push_back(c);
+            out->push_back(s);
+        }
+        return;
+    }
     double r2_3 = x[0] * x[0] + x[1] * x[1] + x[2] * x[2];
     double r2 = r2_3 + (d == 4 ? x[3] * x[3] : 0.0);
     std::vector<std::vector<double>> Pi(p + 1, std::vector<double>(p + 1, 0));
@@ -136,13 +158,13 @@ void host_harmonics(int d, int p, const FarTables& T, const double* x, std::vect
 }  // namespace
 
 int build_far_tables(int d, int p, FarTables* out) {
-    if (d != 3 && d != 4) return FKT_ERR_INVALID_ARG;
-    if (p < 0 || p > (d == 3 ? kMaxP3 : kMaxP4)) return FKT_ERR_INVALID_ARG;
+    if (d < 2 || d > 4) return FKT_ERR_INVALID_ARG;
+    if (p < 0 || p > (d <= 3 ? kMaxP3 : kMaxP4)) return FKT_ERR_INVALID_ARG;
     memset(out, 0, sizeof(*out));
-    const int P = (d == 3) ? kMaxP3 : kMaxP4;  // fill the whole table; kernels read what they need
+    const int P = (d <= 3) ? kMaxP3 : kMaxP4;  // fill the whole table; kernels read what they need
     const ld alpha = d / 2.0L - 1.0L;
     auto pw = sqrt_shift_powers(P);
-    auto A = cos_power_to_gegenbauer(P, alpha);
+    auto A = cos_power_to_gegenbauer(P, alpha, d == 2);
     int q = 0;
     for (int k = 0; k <= p; ++k)
         for (int j = k; j <= p; j += 2, ++q)
@@ -190,12 +212,14 @@ int build_far_tables(int d, int p, FarTables* out) {
         std::vector<double> Yu, Yv;
         host_harmonics(d, p, *out, u, &Yu);
         host_harmonics(d, p, *out, v, &Yv);
-        double Cm2 = 1, Cm1 = 2 * (double)alpha * uv;
+        double Cm2 = 1, Cm1 = (d == 2) ? uv : 2 * (double)alpha * uv;
         size_t off = 0;
         for (int k = 0; k <= p; ++k) {
-            double Ck = (k == 0) ? 1.0 : (k == 1) ? Cm1 : ((2 * uv * (k + (double)alpha - 1) * Cm1 - (k + 2 * (double)alpha - 2) * Cm2) / k);
+            double Ck = (k == 0) ? 1.0 : (k == 1) ? Cm1
+                      : (d == 2) ? 2 * uv * Cm1 - Cm2
+                                 : ((2 * uv * (k + (double)alpha - 1) * Cm1 - (k + 2 * (double)alpha - 2) * Cm2) / k);
             if (k >= 2) { Cm2 = Cm1; Cm1 = Ck; }
-            size_t D = (d == 3) ? (size_t)(2 * k + 1) : (size_t)((k + 1) * (k + 1));
+            size_t D = (d == 2) ? (size_t)(k == 0 ? 1 : 2) : (d == 3) ? (size_t)(2 * k + 1) : (size_t)((k + 1) * (k + 1));
             double s = 0;
             for (size_t h = 0; h < D; ++h) s += Yu[off + h] * Yv[off + h];
             off += D;

@@ -150,6 +150,7 @@ __global__ void geometry_kernel(const int32_t* __restrict__ begin, const int32_t
     __shared__ double red[32];
     const double lo[4] = {lo0, lo1, lo2, lo3};
     int32_t b = begin[nd], e = end[nd], lev = level[nd];
+    if (threadIdx.x >= d && threadIdx.x < 4) c[threadIdx.x] = 0.0;  // unused axes (d < 4)
     if (threadIdx.x < d) {
         int a = threadIdx.x;
         uint64_t code = codes[b];
