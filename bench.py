@@ -57,6 +57,9 @@ WORKLOADS = {
                      points=lambda n: inputs.gaussian_mixture(n, 3, 10, 0.05), kernel=KERNELS["matern32"],
                      p=6, theta=0.375, leaf=256, nrhs=32, near="tf32x3", far="bf16x3", weights="normal",
                      err_targets=10000),
+    "cauchy2d": dict(desc="d=2 N=20000 uniform square", n=20000, points=lambda n: inputs.uniform_cube(n, 2),
+                     kernel=("cauchy", 0.05, 1.0, 1.0), p=4, theta=0.5, leaf=512, nrhs=1, near="fp32", far="fp32",
+                     weights="normal", err_targets=20000, d=2),
     "gauss20k": dict(desc="d=3 N=20000 uniform cube", n=20000, points=lambda n: inputs.uniform_cube(n, 3),
                      kernel=("gaussian", 0.1, 1.0, 1.0), p=4, theta=0.5, leaf=512, nrhs=1, near="fp32",
                      far="fp32", weights="normal", err_targets=20000),
@@ -107,9 +110,9 @@ def near_kernel_name(kname: str, nw: int, near_precision: str = "fp32") -> str:
     return f"{base}<3,{kname},{nw}>"
 
 
-def far_kernel_name(p: int, far_precision: str, nrhs: int, far_kernel: str = "single") -> str:
+def far_kernel_name(p: int, far_precision: str, nrhs: int, far_kernel: str = "single", d: int = 3) -> str:
     if far_precision == "fp32":
-        return f"far_kernel<3,{p},1>" if nrhs == 1 else f"far_mr_kernel<3,{p}>"
+        return f"far_kernel<{d},{p},1>" if nrhs == 1 else f"far_mr_kernel<{d},{p}>"
     if far_precision == "tf32":
         return f"far_tc_kernel<3,{p},tf32>"
     pairs_ok = p <= (6 if far_precision == "bf16x3" else 9)  # two A buffers fit 256 tensor-memory columns
@@ -118,11 +121,11 @@ def far_kernel_name(p: int, far_precision: str, nrhs: int, far_kernel: str = "si
     return f"far_tc2_kernel<{p},{far_precision}>"
 
 
-def near_pair_cost(kernel: str, nw: int, tensor: bool = False):
+def near_pair_cost(kernel: str, nw: int, tensor: bool = False, d: int = 3):
     """Lower bound on SM work per near-field pair for a pass of nw right-hand sides:
     (FP32-pipe lane-ops, MUFU SM-clocks per lane).
 
-    Per pair the method needs d = 3 subtractions and |x|^2 (1 MUL + 2 FMA), the kernel value and one
+    Per pair the method needs d subtractions and |x|^2 (1 MUL + d - 1 FMA), the kernel value and one
     FMA per right-hand side.  Kernel value: Gaussian 2^-q (ex2); Matern-3/2 sqrt, 1 + u ln2 (FMA),
     2^-u (ex2), product (MUL); Cauchy / rational quadratic 1 + q (ADD), reciprocal (rcp); Laplace
     rsqrt and the r = 0 test.  MUFU rates per operation as measured (MUFU_CLOCKS).  With the
@@ -131,17 +134,20 @@ def near_pair_cost(kernel: str, nw: int, tensor: bool = False):
     extra, mufu = {"gaussian": (0, ["ex2"]), "matern32": (2, ["sqrt", "ex2"]), "cauchy": (1, ["rcp"]),
                    "ratquad": (1, ["rcp"]), "laplace": (1, ["rsqrt"]), "exponential": (0, ["sqrt", "ex2"]),
                    "matern52": (4, ["sqrt", "ex2"])}.get(kernel, (2, ["sqrt", "ex2"]))
-    return 6 + extra + fma, sum(MUFU_CLOCKS[m] for m in mufu)
+    return 2 * d + extra + fma, sum(MUFU_CLOCKS[m] for m in mufu)
 
 
-def far_pair_ops(p: int, diag: bool = False) -> int:
+def far_pair_ops(p: int, diag: bool = False, d: int = 3) -> int:
     """FP32 lane-ops the method needs per (target, far node) pair in d = 3 before the contraction:
     distance and direction (~10), kernel derivatives J_m, m <= p (~3 per order), the radial sums
     R_kj = sum_m That_kjm J_m (j + 1 FMAs per (k, j)), the powers (s/r)^j and G = (s/r)^j R (p + pairs),
     the (p+1)^2 harmonics by recurrence (~3 each) and the products Y_kh G_kj (one per term).
-    diag: the radially compressed expansion of 1/r (only j = k), (p+1)^2 terms."""
+    diag: the radially compressed expansion of 1/r (only j = k), (p+1)^2 terms.  d = 2: distance and
+    direction ~7, the 2p circular harmonics by the complex recurrence (~2 each)."""
     pairs = [(k, j) for k in range(p + 1) for j in range(k, p + 1, 2) if not diag or j == k]
-    nt = (p + 1) ** 2 if diag else nterms(3, p)
+    nt = (p + 1) ** 2 if diag else nterms(d, p)
+    if d == 2:
+        return 7 + 3 * (p + 1) + sum(j + 1 for _, j in pairs) + p + len(pairs) + 4 * p + nt
     return 10 + 3 * (p + 1) + sum(j + 1 for _, j in pairs) + p + len(pairs) + 3 * (p + 1) ** 2 + nt
 
 
@@ -198,6 +204,7 @@ def parse():
         if getattr(a, key) is None:
             setattr(a, key, w[wkey])
     a.kern = w["kernel"]
+    a.d = w.get("d", 3)
     if a.workload == "matern1m" and a.kernel:
         a.kern = KERNELS[a.kernel]
     if a.workload != "matern1m":
@@ -340,7 +347,7 @@ def rooflines(a, stats, head, nsm, peaks, src, kname, passes):
     sm_max = peaks.get("sm_max_mhz", 2070.0)
     nw = 1 if (a.nrhs == 1 and a.far_precision == "fp32") else (8 if a.nrhs <= 8 else 16 if a.nrhs <= 16 else 32)
     near_tc = nw == 32 and a.near_precision in ("tf32x3", "f16x3")
-    fp32_ops, mufu_clk = near_pair_cost(kname, nw, near_tc)
+    fp32_ops, mufu_clk = near_pair_cost(kname, nw, near_tc, getattr(a, "d", 3))
     slots = max(fp32_ops / FP32_LANES, mufu_clk)  # SM clocks per pair
     peak_pairs = nsm * sm_max * 1e6 / slots
     near_pairs = stats["near_pairs"] * passes  # one launch per pass; its kernel value serves the pass
@@ -359,11 +366,11 @@ def rooflines(a, stats, head, nsm, peaks, src, kname, passes):
     roofs = [near_roof]
     if stats["far_pairs"] > 0 and head["far_ms"]:
         diag = stats.get("nterms") == (a.p + 1) ** 2 and a.p > 0 and a.kern[0] == "laplace"
-        nt_used = stats.get("nterms") or nterms(3, a.p)
-        ops = far_pair_ops(a.p, diag)
+        nt_used = stats.get("nterms") or nterms(getattr(a, "d", 3), a.p)
+        ops = far_pair_ops(a.p, diag, getattr(a, "d", 3))
         far_peak = nsm * sm_max * 1e6 * FP32_LANES / ops
         far_ach = stats["far_pairs"] / (head["far_ms"] / 1e3)
-        far_name = far_kernel_name(a.p, a.far_precision, a.nrhs, a.far_kernel)
+        far_name = far_kernel_name(a.p, a.far_precision, a.nrhs, a.far_kernel, getattr(a, "d", 3))
         roof = {"kernel": far_name, "bound": "alu", "achieved": far_ach / 1e9, "peak": far_peak / 1e9,
                 "unit": "Gpair/s", "frac": far_ach / far_peak, "traffic": PROFILED_TRAFFIC.get((far_name,) + key),
                 "traffic_unit": "bytes per launch (ncu dram__bytes_read + write)", "ms_per_step": head["far_ms"],
