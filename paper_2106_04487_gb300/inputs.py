@@ -40,6 +40,15 @@ def unit_ball(n: int, d: int = 3, seed: int = SEED_POINTS) -> np.ndarray:
     return (g * rad[:, None]).astype(np.float32)
 
 
+def unit_sphere(n: int, d: int = 3, seed: int = SEED_POINTS) -> np.ndarray:
+    """Uniform on the unit hypersphere S^(d-1) (normalised Gaussian vectors): the point set of
+    the paper's runtime-versus-N experiment (Sec. 5.1)."""
+    rng = np.random.default_rng(seed)
+    g = rng.standard_normal((n, d))
+    g /= np.linalg.norm(g, axis=1, keepdims=True)
+    return g.astype(np.float32)
+
+
 def uniform_plus_clusters(n: int, d: int = 3, clusters: int = 100, std: float = 0.005,
                           seed: int = SEED_POINTS) -> np.ndarray:
     """Half uniform in the unit cube, half in tight isotropic clusters."""
