@@ -39,30 +39,6 @@ struct NearTcShape {
 
 namespace tc {
 
-// D[tmem] (+)= A[tmem] * B[smem]^T (TF32 operands), issued by one thread.
-__device__ __forceinline__ void mma_tf32_ts(uint32_t d_tmem, uint32_t a_tmem, uint64_t b, uint32_t idesc,
-                                            bool accumulate) {
-    asm volatile(
-        "{\n"
-        ".reg .pred p;\n"
-        "setp.ne.b32 p, %4, 0;\n"
-        "tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, p;\n"
-        "}\n" ::"r"(d_tmem),
-        "r"(a_tmem), "l"(b), "r"(idesc), "r"((uint32_t)accumulate)
-        : "memory");
-}
-
-// 32 consecutive 32-bit columns of this thread's TMEM lane (warp w owns lanes 32(w%4)..+31).
-__device__ __forceinline__ void st32(uint32_t taddr, const uint32_t v[32]) {
-    asm volatile(
-        "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
-        "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31, %32};" ::"r"(taddr),
-        "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7]), "r"(v[8]), "r"(v[9]),
-        "r"(v[10]), "r"(v[11]), "r"(v[12]), "r"(v[13]), "r"(v[14]), "r"(v[15]), "r"(v[16]), "r"(v[17]), "r"(v[18]),
-        "r"(v[19]), "r"(v[20]), "r"(v[21]), "r"(v[22]), "r"(v[23]), "r"(v[24]), "r"(v[25]), "r"(v[26]), "r"(v[27]),
-        "r"(v[28]), "r"(v[29]), "r"(v[30]), "r"(v[31])
-        : "memory");
-}
 // 16 consecutive 32-bit columns of this thread's TMEM lane.
 __device__ __forceinline__ void st16(uint32_t taddr, const uint32_t v[16]) {
     asm volatile(
@@ -92,8 +68,8 @@ __device__ __forceinline__ void st4(uint32_t taddr, const uint32_t v[4]) {
                  "r"(v[2]), "r"(v[3])
                  : "memory");
 }
-// One K-step of the BF16 hi/lo product, D += Ahi Bhi^T + Ahi Blo^T + Alo Bhi^T, in one asm block
-// (operands moved to uniform registers once), rows with a set bit in off[] untouched.
+// One K-step of the BF16 hi/lo product, D += Ahi Bhi^T + Ahi Blo^T + Alo Bhi^T, as one asm block
+// of three MMAs sharing their operands, rows with a set bit in off[] untouched.
 __device__ __forceinline__ void mma3_bf16_ts_masked(uint32_t d_tmem, uint32_t ahi, uint32_t alo, uint64_t bhi,
                                                     uint64_t blo, uint32_t idesc, const uint32_t off[4]) {
     asm volatile(
@@ -124,24 +100,6 @@ __device__ __forceinline__ void st32_zero(uint32_t taddr) {
         : "memory");
 }
 __device__ __forceinline__ void wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
-
-// One K-step of the hi/lo product: D[tmem] += Ahi Bhi^T + Ahi Blo^T + Alo Bhi^T (TF32 operands,
-// A in tensor memory, B in shared memory) in one asm block, so the operands are moved to uniform
-// registers once for the three MMAs; accumulator rows (TMEM lanes) with a set bit in off[0..3]
-// (lane i: bit i % 32 of off[i / 32]) are left untouched.
-__device__ __forceinline__ void mma3_tf32_ts_masked(uint32_t d_tmem, uint32_t ahi, uint32_t alo, uint64_t bhi,
-                                                    uint64_t blo, uint32_t idesc, const uint32_t off[4]) {
-    asm volatile(
-        "{\n"
-        ".reg .pred p;\n"
-        "setp.ne.b32 p, 1, 0;\n"
-        "tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %3, %5, {%6, %7, %8, %9}, p;\n"
-        "tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %4, %5, {%6, %7, %8, %9}, p;\n"
-        "tcgen05.mma.cta_group::1.kind::tf32 [%0], [%2], %3, %5, {%6, %7, %8, %9}, p;\n"
-        "}\n" ::"r"(d_tmem),
-        "r"(ahi), "r"(alo), "l"(bhi), "l"(blo), "r"(idesc), "r"(off[0]), "r"(off[1]), "r"(off[2]), "r"(off[3])
-        : "memory");
-}
 
 // Every K-step of one near chunk (nks = 1..4 steps of 8 sources) in one asm block: for K-step k
 // the hi/lo product D += Ahi_k Bhi_k^T + Ahi_k Blo_k^T + Alo_k Bhi_k^T, with A column offsets 8k
@@ -187,20 +145,6 @@ __device__ __forceinline__ void near_chunk_mma(uint32_t d_tmem, uint32_t ahi, ui
         "@q3 tcgen05.mma.cta_group::1.kind::tf32 [%0], [al3], h3, %5, {%6, %7, %8, %9}, p;\n"
         "}\n" ::"r"(d_tmem),
         "r"(ahi), "r"(alo), "l"(bh), "r"(nks), "r"(idesc), "r"(off[0]), "r"(off[1]), "r"(off[2]), "r"(off[3])
-        : "memory");
-}
-
-// D[tmem] += A[tmem] * B[smem]^T (TF32 operands) leaving the accumulator rows (TMEM lanes) whose
-// bit is set in off[0..3] (lane i: bit i % 32 of off[i / 32]) untouched.
-__device__ __forceinline__ void mma_tf32_ts_masked(uint32_t d_tmem, uint32_t a_tmem, uint64_t b, uint32_t idesc,
-                                                   const uint32_t off[4]) {
-    asm volatile(
-        "{\n"
-        ".reg .pred p;\n"
-        "setp.ne.b32 p, 1, 0;\n"
-        "tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, {%4, %5, %6, %7}, p;\n"
-        "}\n" ::"r"(d_tmem),
-        "r"(a_tmem), "l"(b), "r"(idesc), "r"(off[0]), "r"(off[1]), "r"(off[2]), "r"(off[3])
         : "memory");
 }
 
