@@ -385,9 +385,11 @@ def rooflines(a, stats, head, nsm, peaks, src, kname, passes):
             peak_tf = peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops", 1900.0))
             if a.far_precision == "tf32":
                 peak_tf *= 0.5  # nominal TF32 : BF16 dense ratio
-            roof["tensor"] = {"achieved_tflops": flops / (head["far_ms"] / 1e3) / 1e12, "peak_tflops": peak_tf,
-                              "frac": flops / (head["far_ms"] / 1e3) / 1e12 / peak_tf,
-                              "note": f"{copies} MMA products per term (hi/lo split); {src} sustained bf16 peak"}
+            ach_tf = flops / (head["far_ms"] / 1e3) / 1e12
+            roof["tensor"] = {"achieved_tflops": ach_tf, "peak_tflops": peak_tf, "frac": ach_tf / peak_tf,
+                              "method_frac": ach_tf / copies / peak_tf,
+                              "note": f"{copies} MMA products per term (hi/lo split); method_frac counts the "
+                                      f"method's own contraction once; {src} sustained bf16 peak"}
         roofs.append(roof)
     roofs.sort(key=lambda r: -(r["ms_per_step"] or 0.0))
     return roofs
