@@ -154,3 +154,14 @@ def test_oracle_step_accounting():
     assert 1.2 / (3 * 0.02) < rec["value"] < 1.2 / (3 * 0.0099)
     # full product: s2m 0.004 s + traversal 0.006 s x 10
     assert abs(rec["extrapolated_value"] - 4 / 0.064) < 1e-9
+
+
+def test_two_dimensional_counts():
+    # d = 2: binom(p + 2, 2) terms = 1 + 2 per degree k >= 1, times the radial terms of degree k
+    assert bench.nterms(2, 4) == 15 == sum((1 if k == 0 else 2) * ((4 - k) // 2 + 1) for k in range(5))
+    p = 4
+    pairs = [(k, j) for k in range(p + 1) for j in range(k, p + 1, 2)]
+    assert bench.far_pair_ops(p, d=2) == 7 + 3 * (p + 1) + sum(j + 1 for _, j in pairs) + p + len(pairs) + 4 * p + 15
+    # two coordinate differences and |x|^2 with one MUL + one FMA
+    assert bench.near_pair_cost("cauchy", 1, False, d=2) == pytest.approx((4 + 1 + 1, 1 / 16))
+    assert bench.far_kernel_name(4, "fp32", 1, d=2) == "far_kernel<2,4,1>"
