@@ -82,8 +82,8 @@ GP_SIGMA2 = 1e-2
 # DRAM bytes (read + write) per launch of a kernel from one ncu capture, keyed by kernel and
 # workload (kernel, p, theta, leaf, nrhs, N); see profiles/.  Any other workload reports null.
 PROFILED_TRAFFIC = {
-    ("near_tc_kernel<3,matern32>", "matern32", 6, 0.375, 256, 32, 1_000_000): 2.7388e9 + 0.1295e9,
-    ("far_tc2_kernel<6,bf16x3>", "matern32", 6, 0.375, 256, 32, 1_000_000): 1.4604e9 + 0.1307e9,
+    ("near_tc_kernel<3,matern32>", "matern32", 6, 0.375, 256, 32, 1_000_000): 2.8022e9 + 0.1303e9,
+    ("far_tc2_kernel<6,bf16x3>", "matern32", 6, 0.375, 256, 32, 1_000_000): 1.4582e9 + 0.1308e9,
 }
 
 # Per-SM lane rates of GB300 used by the ALU rooflines, measured by fkt_probe_pipe_rate
