@@ -268,7 +268,7 @@ struct Tc3Shape {
 // runs out (bounded) sets s_fail, which only skips work, and the producer drains what it issued
 // before the CTA frees its tensor memory.
 template <int P, int PREC>
-__global__ void __launch_bounds__(160, 2) far_tc3_kernel(MvmArgs a, KernelParams kp_all,
+__global__ void __launch_bounds__(160, Tc3Shape<P, PREC>::TMEM_COLS <= 128 ? 4 : 2) far_tc3_kernel(MvmArgs a, KernelParams kp_all,
                                                          const __grid_constant__ FarTables2 T,
                                                          const unsigned char* __restrict__ image, int nr_total) {
     using Sh = Tc3Shape<P, PREC>;

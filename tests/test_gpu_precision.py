@@ -58,7 +58,7 @@ def test_precision_modes_d3(fkt, case3, prec, nrhs):
 
 @pytest.mark.parametrize("prec", ["bf16x3", "bf16"])
 @pytest.mark.parametrize("far_kernel", ["pairs", "single", "held"])
-@pytest.mark.parametrize("p,nrhs", [(0, 8), (3, 13), (6, 40), (8, 32)])
+@pytest.mark.parametrize("p,nrhs", [(0, 8), (3, 13), (4, 8), (6, 40), (8, 32)])
 def test_far_kernel_variants_d3(fkt, orc, prec, far_kernel, p, nrhs):
     """Both tensor-core far kernels (two far entries per thread in packed float32 pairs, or one)
     at several orders, including an odd number of entries per block and orders past the paired
