@@ -106,7 +106,7 @@ def near_kernel_name(kname: str, nw: int, near_precision: str = "fp32") -> str:
         return f"near_tc2_kernel<3,{kname}>"
     if nw == 32 and near_precision in ("tf32x3", "f16x3"):
         return f"near_tc_kernel<3,{kname}>"
-    base = "near_kernel" if nw == 1 else "near_wide_kernel" if nw == 8 else "near_tile_kernel"
+    base = "near_kernel" if nw == 1 else "near_wide_kernel" if nw in (4, 8) else "near_tile_kernel"
     return f"{base}<3,{kname},{nw}>"
 
 
@@ -345,7 +345,8 @@ def make_weights(a, n):
 def rooflines(a, stats, head, nsm, peaks, src, kname, passes):
     """Roofline of the near and far kernels of the headline form, dominant first."""
     sm_max = peaks.get("sm_max_mhz", 2070.0)
-    nw = 1 if (a.nrhs == 1 and a.far_precision == "fp32") else (8 if a.nrhs <= 8 else 16 if a.nrhs <= 16 else 32)
+    nw = (1 if (a.nrhs == 1 and a.far_precision == "fp32")
+          else 4 if a.nrhs <= 4 else 8 if a.nrhs <= 8 else 16 if a.nrhs <= 16 else 32)
     near_tc = nw == 32 and a.near_precision in ("tf32x3", "f16x3")
     fp32_ops, mufu_clk = near_pair_cost(kname, nw, near_tc, getattr(a, "d", 3))
     slots = max(fp32_ops / FP32_LANES, mufu_clk)  # SM clocks per pair

@@ -125,6 +125,7 @@ void launch_permute_dim(int nw, unsigned grid, cudaStream_t st, int64_t N, const
                         const float* w, int nr, float sig, const float* pt_sig, float4* rec) {
     switch (nw) {
     case 1: permute_kernel<D, 1><<<grid, 256, 0, st>>>(N, perm, xs, w, nr, sig, pt_sig, rec); break;
+    case 4: permute_kernel<D, 4><<<grid, 256, 0, st>>>(N, perm, xs, w, nr, sig, pt_sig, rec); break;
     case 8: permute_kernel<D, 8><<<grid, 256, 0, st>>>(N, perm, xs, w, nr, sig, pt_sig, rec); break;
     case 16: permute_kernel<D, 16><<<grid, 256, 0, st>>>(N, perm, xs, w, nr, sig, pt_sig, rec); break;
     default: permute_kernel<D, 32><<<grid, 256, 0, st>>>(N, perm, xs, w, nr, sig, pt_sig, rec); break;
@@ -232,7 +233,9 @@ void launch_near_stage(fkt_plan_s* P, MvmArgs& a, int nrb, int tpt, cudaStream_t
 static int rhs_block(const fkt_plan_s* P, int nrhs) { return (nrhs == 1 && P->far_precision == FAR_FP32) ? 1 : 8; }
 
 // Right-hand sides per near-field pass of npass (<= kPass) right-hand sides.
-static int near_width(int nrb, int npass) { return nrb == 1 ? 1 : npass <= 8 ? 8 : npass <= 16 ? 16 : 32; }
+static int near_width(int nrb, int npass) {
+    return nrb == 1 ? 1 : npass <= 4 ? 4 : npass <= 8 ? 8 : npass <= 16 ? 16 : 32;
+}
 
 constexpr int kPass = 32;  // right-hand sides per pass (= the tensor-core far field's N)
 static_assert(kPass == kTcN, "a pass feeds one tensor-core far-field launch");

@@ -111,7 +111,8 @@ s2m_kernel(MvmArgs a, const __grid_constant__ FarTables T) {
         });
 #pragma unroll
         for (int r = 0; r < NR; ++r)
-            wt[lane * NR + r] = ok ? reinterpret_cast<const float*>(a.rec + (int64_t)s * a.rec_f4)[a.woff + r] : 0.f;
+            wt[lane * NR + r] = (ok && r < a.nr) ? reinterpret_cast<const float*>(a.rec + (int64_t)s * a.rec_f4)[a.woff + r]
+                                                 : 0.f;  // records of a narrow pass hold only its nr weights
         __syncwarp();
 #pragma unroll 4
         for (int row = 0; row < 32; ++row) {
@@ -211,7 +212,7 @@ __device__ __forceinline__ float kval(float q, const KernelParams& kp) {
 // T targets per thread (128 / T threads per 128-target block); ST-stage ring of CH-point chunks.
 // Thread tl owns targets tl + (128 / T) j, so the targets of slot j of one warp form one
 // 32-target group -- one word of an entry's mask.  Accumulators hold pairs of right-hand sides
-// (float2, packed FMA) when NR >= 8.  Passes of 16 or 32 right-hand sides (SEL) zero the
+// (float2, packed FMA) when NR >= 4.  Passes of 16 or 32 right-hand sides (SEL) zero the
 // kernel value of a target outside an entry's mask instead of keeping a second set of
 // per-entry accumulators.
 template <int D, int NR, int T>
@@ -221,7 +222,7 @@ struct NearShape {
     static constexpr int CH = F4 == 1 ? 256 : (F4 >= 9 ? 64 : 128);
     static constexpr int ST = T >= 4 ? 2 : 3;
     static constexpr bool SEL = NR >= 16;
-    static constexpr bool PAIRS = NR >= 8;
+    static constexpr bool PAIRS = NR >= 4;
     static constexpr int NA = PAIRS ? NR / 2 : NR;  // accumulators per target
     using Acc = typename std::conditional<PAIRS, float2, float>::type;
     static constexpr int MINB = 1;

@@ -1,5 +1,5 @@
 // Launcher of the near-field kernel for one dimension: kernel kind x right-hand sides per pass
-// (1, 8, 16, 32) x targets per thread.  Instantiated in one translation unit per dimension.
+// (1, 4, 8, 16, 32) x targets per thread.  Instantiated in one translation unit per dimension.
 #pragma once
 
 #include "mvm_kernels.cuh"
@@ -48,7 +48,7 @@ void launch_near_tile_t(int kind, unsigned grid, cudaStream_t st, const MvmArgs&
     }
 }
 
-// nw = right-hand sides of the pass (1, 8, 16 or 32); grid = target blocks to cover; tpt =
+// nw = right-hand sides of the pass (1, 4, 8, 16 or 32); grid = target blocks to cover; tpt =
 // targets per thread of the single-RHS kernel (2 or 4).  Multi-RHS passes use the one-warp
 // near_wide_kernel (two CTAs per target block).
 template <int D>
@@ -59,6 +59,7 @@ void launch_near_dim(int nw, int tpt, int kind, unsigned grid, cudaStream_t st, 
         if (tpt == 4) launch_near_t<D, 1, 4>(kind, grid, st, a, kp);
         else launch_near_t<D, 1, 2>(kind, grid, st, a, kp);
         break;
+    case 4: launch_near_wide_t<D, 4>(kind, grid, st, a, kp); break;
     case 8: launch_near_wide_t<D, 8>(kind, grid, st, a, kp); break;
     case 16: launch_near_tile_t<D, 16>(kind, grid, st, a, kp); break;
     default: launch_near_tile_t<D, 32>(kind, grid, st, a, kp); break;

@@ -132,10 +132,11 @@ def test_orders_d3(fkt, orc, p):
     assert _rel(y, z) < TOL
 
 
-@pytest.mark.parametrize("nrhs", [2, 8, 11, 20, 53])
+@pytest.mark.parametrize("nrhs", [2, 4, 8, 11, 20, 36, 53])
 def test_multi_rhs(fkt, orc, nrhs):
     """Ragged right-hand-side groups and passes (8 per group, 32 per pass; 20 and 53 leave a
-    32-wide near pass with fewer right-hand sides than its width) against the oracle."""
+    32-wide near pass with fewer right-hand sides than its width; 2, 4 and the second pass of
+    36 run the 4-wide near pass, whose records hold only 4 weights) against the oracle."""
     X = inputs.gaussian_mixture(12000, 3, 10, 0.05, seed=8)
     w = inputs.normal_weights(12000, nrhs, seed=9)
     y = _gpu_mvm(_plan(fkt, X, "matern32", 0.2, 6, 256, 0.5), w)
