@@ -261,6 +261,8 @@ struct MvmArgs {
     float* yfar;               // far-field result of this group (tree order), [NR][N]
     const float* nimg;         // near-field image of this pass (32-wide tensor-core passes)
     int nr;                    // right-hand sides actually present in this group (<= NR)
+    int near_split;            // single-RHS near field: CTAs per target block, each taking every
+                               // near_split-th entry and writing its own partial row of ynear
     int* err;                  // device error word: 1 = a bounded wait ran out
     // batches of independent problems (all null for a single problem)
     const KernelParams* kps;   // kernel parameters per problem

@@ -163,6 +163,7 @@ MvmArgs base_args(fkt_plan_s* P) {
     a.blk_list = nullptr;
     a.pt_sig = P->pt_sig;
     a.wait_cycles = P->wait_cycles;
+    a.near_split = 1;
     return a;
 }
 
@@ -212,12 +213,24 @@ static void pack_near_image(fkt_plan_s* P, const MvmArgs& a, int tc, int nw, cud
                       const_cast<float*>(a.nimg), st);
 }
 
+// CTAs per target block of the single-right-hand-side near field of a single problem: small
+// problems have too few target blocks to fill the GPU (152 SMs, ~8 CTAs each), so each block's
+// near entries are dealt to up to 8 CTAs, each writing its own partial row.
+static int near_parts(const fkt_plan_s* P) {
+    if (P->nprob != 0 || P->nblocks <= 0) return 1;
+    const int64_t want = 152 * 8;
+    return (int)std::min<int64_t>(8, std::max<int64_t>(1, (want + P->nblocks - 1) / P->nblocks));
+}
+
 void launch_near_stage(fkt_plan_s* P, MvmArgs& a, int nrb, int tpt, cudaStream_t st, bool exact) {
     const int tc = near_tc_mode(P, exact);
     pack_near_image(P, a, tc, nrb, st);
     if (P->nprob == 0) {
         a.blk_list = nullptr;
-        launch_near(P->d, nrb, tpt, tc, P->kernel.kind, (unsigned)P->nblocks, st, a, P->kp, P->d_wmax);
+        a.near_split = (nrb == 1 && !exact) ? near_parts(P) : 1;
+        launch_near(P->d, nrb, tpt, tc, P->kernel.kind, (unsigned)(P->nblocks * a.near_split), st, a, P->kp,
+                    P->d_wmax);
+        a.near_split = 1;
         return;
     }
     for (size_t i = 0; i < P->kind_list.size(); ++i) {
@@ -247,7 +260,7 @@ void mvm_buffer_floats(const fkt_plan_s* P, int nrhs, size_t out[kMvmBufs]) {
     const size_t N = (size_t)P->N, NT = (size_t)P->nterms;
     const size_t nodes = std::max<int64_t>(P->nnodes, 1), items = std::max<int64_t>(P->n_s2m_items, 1);
     out[0] = round64(N * 4 * (size_t)rec_f4(P->d, nw));  // records of one pass (reused by every pass)
-    out[1] = round64(groups * nrb * N);                  // near result
+    out[1] = round64(groups * nrb * N * (nrb == 1 ? near_parts(P) : 1));  // near result (partial rows)
     out[2] = round64(groups * nrb * NT * nodes);         // multipoles
     out[3] = round64(groups * nrb * NT * items);         // s2m partials
     out[4] = P->far_precision == FAR_FP32 ? 0
@@ -394,8 +407,12 @@ int run_mvm(fkt_plan_s* P, const MvmBuffers& B, const float* w, float* y, int nr
         if (timing) FKT_CUDA_TRY(cudaEventRecord(P->ev[6], st));
         // join, then near + far back to the caller's order
         FKT_CUDA_TRY(cudaStreamWaitEvent(st, P->ev[4], 0));
-        unpermute_kernel<><<<pgrid, 256, 0, st>>>(N, npass, P->perm, B.ynear + (size_t)r0 * N, B.yfar + (size_t)r0 * N,
-                                                   y + (size_t)r0 * N);
+        if (nw == 1 && near_parts(P) > 1) {  // one right-hand side, near field in partial rows
+            unpermute_parts_kernel<><<<pgrid, 256, 0, st>>>(N, near_parts(P), P->perm, B.ynear, B.yfar, y);
+        } else {
+            unpermute_kernel<><<<pgrid, 256, 0, st>>>(N, npass, P->perm, B.ynear + (size_t)r0 * N,
+                                                       B.yfar + (size_t)r0 * N, y + (size_t)r0 * N);
+        }
         FKT_CUDA_TRY(cudaGetLastError());
     }
     if (timing) return finish_timing(P);

@@ -39,6 +39,19 @@ __global__ void permute_kernel(int64_t N, const int32_t* __restrict__ perm, cons
     for (int q = 0; q < R::F4; ++q) rec[i * R::F4 + q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
 }
 
+// y[perm[i]] = sum_{s < parts} ys[s][i] + yadd[i]: one right-hand side whose near field was
+// split over several CTAs per target block (partial rows summed in a fixed order).
+template <int Unused = 0>
+__global__ void unpermute_parts_kernel(int64_t N, int parts, const int32_t* __restrict__ perm,
+                                       const float* __restrict__ ys, const float* __restrict__ yadd,
+                                       float* __restrict__ y) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    float v = ys[i];
+    for (int s = 1; s < parts; ++s) v += ys[s * N + i];
+    y[perm[i]] = v + yadd[i];
+}
+
 // y[r][perm[i]] = ys[r][i] (+ yadd[r][i]): back to the caller's order, adding the far field
 // to the near field when yadd is given.
 template <int Unused = 0>
@@ -360,7 +373,9 @@ __device__ __forceinline__ void near_chunk(const float4* __restrict__ sb, int n,
 
 // Near field of one target block: for each near entry (leaf, mask), every point of the leaf is
 // streamed through shared memory by the bulk-copy engine (ST-stage mbarrier ring, issued by
-// thread 0) and each thread accumulates K(|x_t - x_s|) w_s for its T targets.
+// thread 0) and each thread accumulates K(|x_t - x_s|) w_s for its T targets.  With
+// a.near_split = S > 1 (one right-hand side, small problems) S CTAs share a block: CTA part s
+// takes entries s, s + S, ... and writes its partial sums to row s of ynear.
 template <int D, int KIND, int NR, int T>
 __global__ void __launch_bounds__(NearShape<D, NR, T>::THREADS, NearShape<D, NR, T>::MINB) near_kernel(MvmArgs a, KernelParams kp_all) {
     using R = Rec<D, NR>;
@@ -371,7 +386,9 @@ __global__ void __launch_bounds__(NearShape<D, NR, T>::THREADS, NearShape<D, NR,
     __shared__ __align__(128) float4 buf[ST][CH * F4];
     __shared__ __align__(8) uint64_t full[ST];
     const int tl = threadIdx.x;
-    const int64_t blk = cta_block(a);
+    const int S = NR == 1 ? a.near_split : 1, part = (int)(blockIdx.x % S);
+    const int64_t gi = blockIdx.x / S;
+    const int64_t blk = a.blk_list ? (int64_t)a.blk_list[gi] : gi;
     const KernelParams kp = block_params(a, blk, kp_all);
     const int2 rg = a.blk[blk];
     float tx[T][4];
@@ -391,7 +408,7 @@ __global__ void __launch_bounds__(NearShape<D, NR, T>::THREADS, NearShape<D, NR,
             if constexpr (Sh::PAIRS) acc[j][r] = make_float2(0.f, 0.f);
             else acc[j][r] = 0.f;
         }
-    const int64_t e0 = a.near_off[blk], e1 = a.near_off[blk + 1];
+    const int64_t e0 = a.near_off[blk] + part, e1 = a.near_off[blk + 1];
     bool ok_all = true;
     if (e0 < e1) {
         if (tl == 0) {
@@ -416,13 +433,14 @@ __global__ void __launch_bounds__(NearShape<D, NR, T>::THREADS, NearShape<D, NR,
                     ++issued;
                     return;
                 }
-                if (++pe < e1) pcb = a.nd_begin[a.near_ent[pe].x];
+                pe += S;
+                if (pe < e1) pcb = a.nd_begin[a.near_ent[pe].x];
             }
         };
         if (tl == 0)
             for (int s = 0; s < ST; ++s) issue(s);
         int k = 0;
-        for (int64_t e = e0; e < e1 && ok_all; ++e) {
+        for (int64_t e = e0; e < e1 && ok_all; e += S) {
             const int2 ent = a.near_ent[e];
             bool act[T];
             unsigned jm = 0;  // slots whose 32-target group has an active target (warp-uniform)
@@ -473,7 +491,7 @@ __global__ void __launch_bounds__(NearShape<D, NR, T>::THREADS, NearShape<D, NR,
                 float v;
                 if constexpr (Sh::PAIRS) v = (r & 1) ? acc[j][r / 2].y : acc[j][r / 2].x;
                 else v = acc[j][r];
-                a.ynear[(int64_t)r * a.N + t] = v * kp.scale;
+                a.ynear[(int64_t)(r + part) * a.N + t] = v * kp.scale;  // part > 0 only when NR == 1
             }
         }
     }
