@@ -263,6 +263,7 @@ struct MvmArgs {
     int nr;                    // right-hand sides actually present in this group (<= NR)
     int near_split;            // single-RHS near field: CTAs per target block, each taking every
                                // near_split-th entry and writing its own partial row of ynear
+    int far_split;             // the same for the single-RHS float32 far field (partial rows of yfar)
     int* err;                  // device error word: 1 = a bounded wait ran out
     // batches of independent problems (all null for a single problem)
     const KernelParams* kps;   // kernel parameters per problem

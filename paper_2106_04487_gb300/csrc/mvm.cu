@@ -164,6 +164,7 @@ MvmArgs base_args(fkt_plan_s* P) {
     a.pt_sig = P->pt_sig;
     a.wait_cycles = P->wait_cycles;
     a.near_split = 1;
+    a.far_split = 1;
     return a;
 }
 
@@ -265,7 +266,7 @@ void mvm_buffer_floats(const fkt_plan_s* P, int nrhs, size_t out[kMvmBufs]) {
     out[3] = round64(groups * nrb * NT * items);         // s2m partials
     out[4] = P->far_precision == FAR_FP32 ? 0
              : round64(nodes * (size_t)tc_b_bytes(P->nterms, tc_prec_of(P->far_precision)) / 4);
-    out[5] = round64(groups * nrb * N);                  // far result
+    out[5] = round64(groups * nrb * N * (nrb == 1 ? near_parts(P) : 1));  // far result (partial rows)
     out[6] = near_uses_image(P, near_tc_mode(P, false), nw)  // near-field image of one pass
                  ? round64((size_t)(P->img_pos / 4) * kNearGroupFloats)
                  : 0;
@@ -382,7 +383,8 @@ int run_mvm(fkt_plan_s* P, const MvmBuffers& B, const float* w, float* y, int nr
                 ag.mult = B.mult + (size_t)g * nrb * NT * nodes;
                 ag.yfar = B.yfar + (size_t)g * nrb * N;
                 ag.nr = std::min(nrb, nrhs - g * nrb);
-                FarLaunch L{&ag, &P->kp, &P->tabs, P->nblocks, P->n_s2m_items, P->nnodes, st2, st2};
+                ag.far_split = nrb == 1 ? near_parts(P) : 1;  // partial rows, summed by unpermute
+                FarLaunch L{&ag, &P->kp, &P->tabs, P->nblocks * ag.far_split, P->n_s2m_items, P->nnodes, st2, st2};
                 int rc = launch_far_any(layout_code(P), P->p, nrb, L);
                 if (rc) return rc;
             }

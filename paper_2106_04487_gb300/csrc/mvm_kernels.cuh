@@ -39,17 +39,20 @@ __global__ void permute_kernel(int64_t N, const int32_t* __restrict__ perm, cons
     for (int q = 0; q < R::F4; ++q) rec[i * R::F4 + q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
 }
 
-// y[perm[i]] = sum_{s < parts} ys[s][i] + yadd[i]: one right-hand side whose near field was
-// split over several CTAs per target block (partial rows summed in a fixed order).
+// y[perm[i]] = sum_{s < parts} (ys[s][i] + yadd[s][i]): one right-hand side whose near and far
+// fields were split over several CTAs per target block (partial rows summed in a fixed order).
 template <int Unused = 0>
 __global__ void unpermute_parts_kernel(int64_t N, int parts, const int32_t* __restrict__ perm,
                                        const float* __restrict__ ys, const float* __restrict__ yadd,
                                        float* __restrict__ y) {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= N) return;
-    float v = ys[i];
-    for (int s = 1; s < parts; ++s) v += ys[s * N + i];
-    y[perm[i]] = v + yadd[i];
+    float v = ys[i], f = yadd[i];
+    for (int s = 1; s < parts; ++s) {
+        v += ys[s * N + i];
+        f += yadd[s * N + i];
+    }
+    y[perm[i]] = v + f;
 }
 
 // y[r][perm[i]] = ys[r][i] (+ yadd[r][i]): back to the caller's order, adding the far field
@@ -816,7 +819,11 @@ __global__ void __launch_bounds__(kTB) far_kernel(MvmArgs a, KernelParams kp_all
     __shared__ float4 s_c[FB];
     __shared__ float s_s[FB];
     __shared__ int s_m[FB];
-    const int64_t blk = cta_block(a);
+    // a.far_split = S > 1 (one right-hand side, small problems): S CTAs share a target block, CTA
+    // part s taking entries s, s + S, ... and writing its partial sums to row s of yfar
+    const int S = NR == 1 ? a.far_split : 1, part = (int)(blockIdx.x % S);
+    const int64_t gi = blockIdx.x / S;
+    const int64_t blk = a.blk_list ? (int64_t)a.blk_list[gi] : gi;
     const KernelParams kp = block_params(a, blk, kp_all);
     const int2 rg = a.blk[blk];
     const int tl = threadIdx.x;
@@ -826,17 +833,19 @@ __global__ void __launch_bounds__(kTB) far_kernel(MvmArgs a, KernelParams kp_all
     float acc[NR];
 #pragma unroll
     for (int r = 0; r < NR; ++r) acc[r] = 0.f;
-    const int64_t e0 = a.far_off[blk], e1 = a.far_off[blk + 1];
-    for (int64_t eb = e0; eb < e1; eb += FB) {
-        const int nb = (int)min((int64_t)FB, e1 - eb);
+    const int64_t e0 = a.far_off[blk] + part, nall = a.far_off[blk + 1] - a.far_off[blk];
+    const int64_t nmine = nall > part ? (nall - part + S - 1) / S : 0;  // entries e0 + S k, k < nmine
+    for (int64_t kb = 0; kb < nmine; kb += FB) {
+        const int nb = (int)min((int64_t)FB, nmine - kb);
+        const int64_t eb = e0 + S * kb;
         __syncthreads();
         for (int i = tl; i < nb * NT * NR; i += kTB) {
             const int e = i / (NT * NR), q = i - e * NT * NR;
-            const int node = a.far_ent[eb + e].x;
+            const int node = a.far_ent[eb + (int64_t)S * e].x;
             sM[i] = a.mult[(int64_t)node * NT * NR + q];
         }
         if (tl < nb) {
-            const int2 ent = a.far_ent[eb + tl];
+            const int2 ent = a.far_ent[eb + (int64_t)S * tl];
             s_c[tl] = a.nd_cf[ent.x];
             s_s[tl] = a.nd_scale[ent.x];
             s_m[tl] = ent.y;
@@ -885,7 +894,7 @@ __global__ void __launch_bounds__(kTB) far_kernel(MvmArgs a, KernelParams kp_all
     if (valid) {
 #pragma unroll
         for (int r = 0; r < NR; ++r)
-            if (r < a.nr) a.yfar[(int64_t)r * a.N + t] = acc[r];
+            if (r < a.nr) a.yfar[(int64_t)(r + part) * a.N + t] = acc[r];  // part > 0 only when NR == 1
     }
 }
 
